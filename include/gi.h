@@ -1,0 +1,215 @@
+/*
+ * gi.h -- C ABI of a static GPU index over (key, rowID) pairs, stored in sorted,
+ * Eytzinger (EBS) or k-ary Eytzinger (EKS) order, for NVIDIA GB300 (sm_103a).
+ *
+ * Method: Henneberg & Schuhknecht, "Bigger Is Not Better: The Fastest Static GPU
+ * Index Is Also Lightweight!" (arXiv 2506.01576).
+ *   Problem statement (point and range lookups) ........ Section 1
+ *   Sorted array + binary search (BS) .................. Section 3
+ *   Eytzinger order, EBS lookup ........................ Section 3, Figs 5-6
+ *   One-read-one-write permutation into that order ..... Section 4 (p(t), p'(t))
+ *   Range lookups over Eytzinger order ................. Section 5
+ *   k-ary Eytzinger order and EKS lookup ............... Section 6 (6.1, 6.2)
+ *   Cache pinning of top levels, static scheduling ..... Sections 7.2, 7.3
+ *   Coalescing micro-benchmark ......................... Section 5.1, Fig 9
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Pointers.  Every data pointer may be DEVICE memory (e.g. a torch CUDA
+ *    tensor's data_ptr) or HOST memory (pinned or pageable).  Device pointers are
+ *    used in place and the call is asynchronous on the index's stream.  When any
+ *    input or output of a call is host memory, the library stages it through
+ *    device buffers it owns (pipelined in chunks on internal streams) and the call
+ *    returns only after the host outputs are written.  Device pointers must belong
+ *    to the current device.
+ *  - Ownership.  gi_build copies what it needs: the caller keeps keys/rowids.
+ *    Outputs are always caller-allocated.  The index owns its device arrays and
+ *    internal scratch; gi_destroy frees them.
+ *  - Keys are unsigned 32- or 64-bit integers (GI_KEY_U32 / GI_KEY_U64, OR-ed
+ *    into `layout`); probes and range bounds have the index's key width.
+ *  - rowIDs are uint32; the value GI_MISS is reserved: it is what a point lookup
+ *    that finds nothing reports, and gi_build rejects it as an input rowID.
+ *  - Duplicate keys are allowed.  Ties keep input order (a stable sort): a point
+ *    lookup returns the rowID of the first entry in that order (lower bound), a
+ *    range lookup returns all of them in (key, input position) order.
+ *  - Return codes: GI_OK or a GI_ERR_* code; gi_last_error() then holds a
+ *    message (thread-local, valid until the next call on the same thread).
+ *    Errors found on the device (a bounded wait that gave up) are latched in the
+ *    index and reported by gi_sync or by the next call that synchronises.
+ */
+#ifndef GI_H_
+#define GI_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gi_index gi_index;
+
+/* Layout (low byte of `layout`). */
+#define GI_SORTED         0 /* ascending order; textbook binary search (Section 3)   */
+#define GI_EYTZINGER      1 /* Eytzinger order, 1-based, empty slot 0 (Sections 3-4) */
+#define GI_EYTZINGER_KARY 2 /* k-ary Eytzinger order, k-1 keys per node (Section 6)  */
+/* Key width, OR-ed into `layout`. */
+#define GI_KEY_U32 0x000
+#define GI_KEY_U64 0x100
+
+/* Return codes. */
+#define GI_OK          0
+#define GI_ERR_INVALID 1 /* bad argument (null/misaligned pointer, bad layout/k, reserved rowID) */
+#define GI_ERR_NOMEM   2 /* device or pinned allocation failed                          */
+#define GI_ERR_CUDA    3 /* a CUDA runtime call failed                                  */
+#define GI_ERR_TIMEOUT 4 /* a bounded device-side wait gave up; results are not valid  */
+
+#define GI_MISS 0xFFFFFFFFu
+
+/*
+ * gi_build -- build an index over n (key, rowID) pairs.                (Sections 3, 4, 6.1)
+ *   keys    n keys of the width given in `layout` (device or host memory).
+ *   rowids  n uint32 rowIDs; rowids[j] belongs to keys[j]; none may equal GI_MISS.
+ *   n       number of pairs; 0 is valid (every lookup misses, every range is empty).
+ *   layout  GI_SORTED | GI_EYTZINGER | GI_EYTZINGER_KARY, OR-ed with GI_KEY_U32/U64.
+ *   k       fan-out for GI_EYTZINGER_KARY, 2 <= k <= 33 (nodes of k-1 keys); the
+ *           paper prefers k-1 a power of two (Section 6.1).  Ignored otherwise.
+ *   out     receives the new index.
+ * The pairs are key-value radix sorted (stable) and, for the Eytzinger layouts,
+ * moved into place by the closed-form permutation of Sections 4 and 6.1.  Runs on
+ * the thread's default gi stream (gi_set_stream(NULL, s)); returns after the index
+ * is complete.  The index stores exactly n keys and n rowIDs (plus the empty slot
+ * 0 of GI_EYTZINGER, Section 3).
+ * Errors: GI_ERR_INVALID (bad layout/k/pointer, a rowID equal to GI_MISS),
+ * GI_ERR_NOMEM, GI_ERR_CUDA, GI_ERR_TIMEOUT.  On error *out is set to NULL.
+ */
+int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, uint32_t k,
+             gi_index** out);
+
+/*
+ * gi_point_lookup -- m point lookups.                           (Sections 1, 3, 6.2)
+ *   queries     m probes of the index's key width.
+ *   out_rowids  m uint32: the rowID of the first entry whose key equals
+ *               queries[i], or GI_MISS.  Written in probe order.
+ * SORTED: textbook lower_bound; EYTZINGER: branch-free descent; EYTZINGER_KARY:
+ * a lane group loads one node per level and picks the child by ballot/popc.
+ * Errors: GI_ERR_INVALID (null index/pointer), GI_ERR_CUDA, GI_ERR_NOMEM (staging).
+ */
+int gi_point_lookup(const gi_index* index, const void* queries, uint64_t m,
+                    uint32_t* out_rowids);
+
+/*
+ * gi_range_lookup -- m inclusive range lookups [lo[i], hi[i]] as CSR.    (Sections 1, 5)
+ *   lo, hi       m bounds each, index key width; lo[i] > hi[i] is an empty range.
+ *   out_offsets  m+1 uint64: out_offsets[i] is where range i's rows start,
+ *                out_offsets[m] is the total row count.
+ *   out_rowids   NULL, or room for out_offsets[m] uint32 rowIDs.  Range i's rows
+ *                are in ascending (key, input position) order.
+ * Two-call protocol: call with out_rowids == NULL to get the offsets (and the
+ * total), allocate, call again with the same inputs and out_rowids set.  When
+ * every pointer is device memory and the second call passes the same lo, hi, m
+ * and out_offsets as the first, with no other range lookup on this index in
+ * between, it reuses the first call's counts and runs only the fill pass: the
+ * caller must not change lo, hi or out_offsets between the two calls.
+ * Errors: GI_ERR_INVALID, GI_ERR_CUDA, GI_ERR_NOMEM (scratch or staging).
+ */
+int gi_range_lookup(const gi_index* index, const void* lo, const void* hi, uint64_t m,
+                    uint64_t* out_offsets, uint32_t* out_rowids);
+
+/* gi_destroy -- free the index and everything it owns (waits for its stream). NULL is a no-op. */
+void gi_destroy(gi_index* index);
+
+/*
+ * gi_set_stream -- run the index's work on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  With index == NULL, sets the calling thread's default
+ * stream for later gi_build calls; a built index starts on that stream.
+ */
+int gi_set_stream(gi_index* index, void* stream);
+
+/* gi_sync -- wait for the index's stream; report a latched device-side error. */
+int gi_sync(gi_index* index);
+
+/* gi_last_error -- message of the last failing call on this thread ("" if none). */
+const char* gi_last_error(void);
+
+/* gi_footprint_bytes -- device bytes the index keeps: n*(key+4), + one key for GI_EYTZINGER. */
+uint64_t gi_footprint_bytes(const gi_index* index);
+
+/* Description of a built index.  `keys`/`rowids` are the index's own device arrays
+ * (read-only views, valid until gi_destroy): slot t of the layout is keys[t] and
+ * rowids[t], except GI_EYTZINGER where slot t (0-based) is keys[t+1], rowids[t]. */
+typedef struct gi_info {
+  uint64_t n;
+  int32_t layout;        /* GI_SORTED / GI_EYTZINGER / GI_EYTZINGER_KARY */
+  uint32_t k;            /* fan-out: 2 for GI_EYTZINGER, k for KARY, 0 for SORTED */
+  uint32_t key_bytes;    /* 4 or 8 */
+  uint32_t unique;       /* 1 if no two keys are equal */
+  uint32_t levels;       /* tree levels (SORTED: ceil(log2(n+1))) */
+  uint32_t reserved;
+  const void* keys;
+  const uint32_t* rowids;
+  uint64_t footprint_bytes;
+} gi_info;
+int gi_get_info(const gi_index* index, gi_info* out);
+
+/*
+ * gi_copy_layout -- copy the index's arrays in layout order: keys_out[t] and
+ * rowids_out[t] for slot t = 0..n-1 (for GI_EYTZINGER the 0-based slots, i.e.
+ * without the empty slot 0).  Either output may be NULL; each may be device or
+ * host memory.  Returns after the copy is complete.  Lets a caller inspect or
+ * save the built order (Sections 3, 4, 6.1).
+ */
+int gi_copy_layout(const gi_index* index, void* keys_out, uint32_t* rowids_out);
+
+/*
+ * Tuning knobs (Sections 7.2, 7.3 and the EKS group size of Section 6.2).  A value
+ * of -1 restores the automatic choice.  Values outside the supported set return
+ * GI_ERR_INVALID.
+ *   GI_OPT_GROUP        lanes per lookup for EYTZINGER_KARY (1 = one thread per
+ *                       lookup, "EKS (single)"; up to 32; must be supported for k).
+ *   GI_OPT_PER_THREAD   independent lookups interleaved per thread/group: 1, 2, 4.
+ *   GI_OPT_SMEM_LEVELS  top tree levels pinned in shared memory (0 = none).
+ *   GI_OPT_BLOCK        threads per block: 128, 256, 512, 1024.
+ *   GI_OPT_BLOCKS_PER_SM  0 = one thread (group) per work item; >0 = persistent grid
+ *                       of that many blocks per SM with a static schedule.
+ *   GI_OPT_PREFETCH     EYTZINGER prefetch distance in levels: 0, 2, 3, 4.
+ *   GI_OPT_EARLY_EXIT   stop a point lookup at an equal pivot: 0 or 1 (only honoured
+ *                       when the keys are unique).
+ */
+#define GI_OPT_GROUP         1
+#define GI_OPT_PER_THREAD    2
+#define GI_OPT_SMEM_LEVELS   3
+#define GI_OPT_BLOCK         4
+#define GI_OPT_BLOCKS_PER_SM 5
+#define GI_OPT_PREFETCH      6
+#define GI_OPT_EARLY_EXIT    7
+int gi_set_option(gi_index* index, int option, int64_t value);
+int gi_get_option(const gi_index* index, int option, int64_t* value);
+
+/*
+ * gi_probe_random_sectors -- roofline probe: `loads` loads of `chunk_bytes`
+ * (16, 32, 64, 128 or 256) contiguous bytes each from uniformly random
+ * chunk-aligned offsets of the device buffer `buf` (`bytes` long, 256-byte
+ * aligned), many in flight per warp.  With buf much larger than L2 it measures
+ * the random-access throughput of HBM.  The XOR of everything loaded goes to
+ * *sink (device).  Asynchronous on `stream`.                     (Section 5.1)
+ */
+int gi_probe_random_sectors(const void* buf, uint64_t bytes, uint32_t chunk_bytes,
+                            uint64_t loads, uint64_t seed, uint64_t* sink, void* stream);
+
+/*
+ * gi_coalescing_probe -- the micro-benchmark of Section 5.1 / Fig 9: `threads`
+ * threads in groups of `group` neighbours; for `steps` steps each group draws a
+ * random position p in the uint32 array `buf` (`entries` long) and thread i of the
+ * group loads entry p+i.  The XOR of the loads goes to *sink.  Asynchronous.
+ */
+int gi_coalescing_probe(const uint32_t* buf, uint64_t entries, uint32_t threads,
+                        uint32_t group, uint32_t steps, uint64_t seed, uint64_t* sink,
+                        void* stream);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t gi_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GI_H_ */

@@ -1,0 +1,241 @@
+"""Python binding of libgi (include/gi.h): a static GPU index over (key, rowID)
+pairs in sorted, Eytzinger or k-ary Eytzinger order, for GB300 (sm_103a).
+
+The functions keep the C names and only marshal arguments: buffers may be torch
+tensors (CUDA or CPU) or numpy arrays; their data pointers go straight to the C
+library, which runs every step on the GPU.  There is no CPU fallback: if
+libgi.so is missing or fails to load, importing the binding's entry points
+raises.
+
+    idx = gi_build(keys, rowids, GI_EYTZINGER_KARY | GI_KEY_U64, 9)
+    gi_point_lookup(idx, probes, out)          # out: uint32 rowIDs or GI_MISS
+    gi_range_lookup(idx, lo, hi, offsets)       # offsets: m+1 uint64
+    gi_range_lookup(idx, lo, hi, offsets, rows) # rows: offsets[m] uint32
+    gi_destroy(idx)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = [
+    "GI_SORTED", "GI_EYTZINGER", "GI_EYTZINGER_KARY", "GI_KEY_U32", "GI_KEY_U64", "GI_MISS",
+    "GI_OK", "GI_ERR_INVALID", "GI_ERR_NOMEM", "GI_ERR_CUDA", "GI_ERR_TIMEOUT",
+    "GI_OPT_GROUP", "GI_OPT_PER_THREAD", "GI_OPT_SMEM_LEVELS", "GI_OPT_BLOCK",
+    "GI_OPT_BLOCKS_PER_SM", "GI_OPT_PREFETCH", "GI_OPT_EARLY_EXIT",
+    "GIError", "Index", "gi_info", "lib_path", "load",
+    "gi_build", "gi_point_lookup", "gi_range_lookup", "gi_destroy", "gi_set_stream", "gi_sync",
+    "gi_last_error", "gi_footprint_bytes", "gi_get_info", "gi_copy_layout", "gi_set_option", "gi_get_option",
+    "gi_probe_random_sectors", "gi_coalescing_probe", "gi_launch_count",
+]
+
+GI_SORTED, GI_EYTZINGER, GI_EYTZINGER_KARY = 0, 1, 2
+GI_KEY_U32, GI_KEY_U64 = 0x000, 0x100
+GI_OK, GI_ERR_INVALID, GI_ERR_NOMEM, GI_ERR_CUDA, GI_ERR_TIMEOUT = 0, 1, 2, 3, 4
+GI_MISS = 0xFFFFFFFF
+(GI_OPT_GROUP, GI_OPT_PER_THREAD, GI_OPT_SMEM_LEVELS, GI_OPT_BLOCK, GI_OPT_BLOCKS_PER_SM,
+ GI_OPT_PREFETCH, GI_OPT_EARLY_EXIT) = range(1, 8)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(_HERE, "libgi.so")
+_lib = None
+
+
+class GIError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("gi error %d: %s" % (code, msg))
+        self.code = code
+
+
+class gi_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("layout", ctypes.c_int32), ("k", ctypes.c_uint32),
+                ("key_bytes", ctypes.c_uint32), ("unique", ctypes.c_uint32),
+                ("levels", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("keys", ctypes.c_void_p), ("rowids", ctypes.c_void_p),
+                ("footprint_bytes", ctypes.c_uint64)]
+
+
+def load(build_if_missing: bool = False):
+    """Load libgi.so (optionally compiling it first).  Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        from . import _build
+        _build.build()
+    if not os.path.exists(lib_path):
+        raise ImportError("libgi.so is not built (%s); run __graft_entry__.build()" % lib_path)
+    lib = ctypes.CDLL(lib_path)
+    P, U64, U32, I, I64 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int64
+    sig = {
+        "gi_build": (I, [P, P, U64, I, U32, ctypes.POINTER(P)]),
+        "gi_point_lookup": (I, [P, P, U64, P]),
+        "gi_range_lookup": (I, [P, P, P, U64, P, P]),
+        "gi_destroy": (None, [P]),
+        "gi_set_stream": (I, [P, P]),
+        "gi_sync": (I, [P]),
+        "gi_last_error": (ctypes.c_char_p, []),
+        "gi_footprint_bytes": (U64, [P]),
+        "gi_get_info": (I, [P, ctypes.POINTER(gi_info)]),
+        "gi_copy_layout": (I, [P, P, P]),
+        "gi_set_option": (I, [P, I, I64]),
+        "gi_get_option": (I, [P, I, ctypes.POINTER(I64)]),
+        "gi_probe_random_sectors": (I, [P, U64, U32, U64, U64, P, P]),
+        "gi_coalescing_probe": (I, [P, U64, U32, U32, U32, U64, P, P]),
+        "gi_launch_count": (U64, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != GI_OK:
+        raise GIError(rc, load().gi_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor / numpy array (contiguous), an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):  # torch.Tensor
+        if not x.is_contiguous():
+            raise ValueError("buffers must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "__array_interface__"):  # numpy
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffers must be contiguous")
+        return x.__array_interface__["data"][0]
+    raise TypeError("unsupported buffer type %r" % type(x))
+
+
+def _len(x) -> int:
+    if hasattr(x, "numel"):
+        return int(x.numel())
+    return int(len(x))
+
+
+def _stream_handle(stream):
+    if stream is None or isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+class Index:
+    """Handle of a built index (owns the C gi_index*)."""
+
+    def __init__(self, handle: int, keepalive=None):
+        self._h = handle
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise GIError(GI_ERR_INVALID, "index was destroyed")
+        return self._h
+
+    def info(self) -> gi_info:
+        return gi_get_info(self)
+
+    def close(self):
+        if self._h:
+            load().gi_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gi_build(keys, rowids, layout: int, k: int = 0) -> Index:
+    lib = load()
+    n = _len(keys)
+    if _len(rowids) != n:
+        raise ValueError("keys and rowids differ in length")
+    out = ctypes.c_void_p()
+    _check(lib.gi_build(_ptr(keys), _ptr(rowids), n, layout, k, ctypes.byref(out)))
+    return Index(out.value)
+
+
+def gi_point_lookup(index: Index, queries, out_rowids) -> None:
+    m = _len(queries)
+    if _len(out_rowids) < m:
+        raise ValueError("out_rowids too small")
+    _check(load().gi_point_lookup(index.handle, _ptr(queries), m, _ptr(out_rowids)))
+
+
+def gi_range_lookup(index: Index, lo, hi, out_offsets, out_rowids=None) -> None:
+    m = _len(lo)
+    if _len(hi) != m or _len(out_offsets) < m + 1:
+        raise ValueError("lo/hi lengths differ or out_offsets is shorter than m+1")
+    _check(load().gi_range_lookup(index.handle, _ptr(lo), _ptr(hi), m, _ptr(out_offsets),
+                                  _ptr(out_rowids)))
+
+
+def gi_destroy(index: Index) -> None:
+    index.close()
+
+
+def gi_set_stream(index, stream) -> None:
+    _check(load().gi_set_stream(index.handle if index is not None else None,
+                                _stream_handle(stream)))
+
+
+def gi_sync(index: Index) -> None:
+    _check(load().gi_sync(index.handle))
+
+
+def gi_last_error() -> str:
+    return load().gi_last_error().decode(errors="replace")
+
+
+def gi_footprint_bytes(index: Index) -> int:
+    return int(load().gi_footprint_bytes(index.handle))
+
+
+def gi_get_info(index: Index) -> gi_info:
+    inf = gi_info()
+    _check(load().gi_get_info(index.handle, ctypes.byref(inf)))
+    return inf
+
+
+def gi_copy_layout(index: Index, keys_out=None, rowids_out=None) -> None:
+    _check(load().gi_copy_layout(index.handle, _ptr(keys_out), _ptr(rowids_out)))
+
+
+def gi_set_option(index: Index, option: int, value: int) -> None:
+    _check(load().gi_set_option(index.handle, option, value))
+
+
+def gi_get_option(index: Index, option: int) -> int:
+    v = ctypes.c_int64()
+    _check(load().gi_get_option(index.handle, option, ctypes.byref(v)))
+    return int(v.value)
+
+
+def gi_probe_random_sectors(buf, chunk_bytes: int, loads: int, seed: int, sink, stream=None) -> None:
+    nbytes = buf.numel() * buf.element_size()
+    _check(load().gi_probe_random_sectors(_ptr(buf), nbytes, chunk_bytes, loads, seed, _ptr(sink),
+                                          _stream_handle(stream)))
+
+
+def gi_coalescing_probe(buf, threads: int, group: int, steps: int, seed: int, sink,
+                        stream=None) -> None:
+    _check(load().gi_coalescing_probe(_ptr(buf), _len(buf), threads, group, steps, seed,
+                                      _ptr(sink), _stream_handle(stream)))
+
+
+def gi_launch_count() -> int:
+    return int(load().gi_launch_count())

@@ -1,0 +1,749 @@
+// The C ABI of include/gi.h: argument checks, the index object, device memory,
+// host-memory staging, and the choice of kernel configuration.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gi_internal.cuh"
+
+// ---------------------------------------------------------------- the index object
+struct GiStaging {
+  cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev = nullptr;
+  void* q[3] = {nullptr, nullptr, nullptr};
+  uint32_t* out[3] = {nullptr, nullptr, nullptr};
+  uint64_t chunk = 0;  // probes per chunk
+};
+
+struct gi_index {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  uint64_t n = 0;
+  int layout = 0;
+  uint32_t k = 0;
+  int key_bytes = 4;
+  bool unique = true;
+  void* keys = nullptr;        // EYTZINGER: slot t at keys[t+1]
+  uint32_t* rows = nullptr;
+  uint32_t* dflags = nullptr;  // device status word
+  gi::Geom geom{};
+  int64_t opt[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  // range-lookup scratch and the state of the two-call protocol
+  void* rscratch = nullptr;
+  size_t rscratch_bytes = 0;
+  const void* last_lo = nullptr;
+  const void* last_hi = nullptr;
+  uint64_t last_m = 0;
+  const uint64_t* last_off = nullptr;
+  bool counts_valid = false;
+  GiStaging* stage = nullptr;
+  uint32_t latched = 0;  // device status seen by the host
+};
+
+namespace {
+
+thread_local std::string t_err;
+thread_local cudaStream_t t_default_stream = nullptr;
+std::atomic<uint64_t> g_launches{0};
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky-free error
+  if (e == cudaErrorMemoryAllocation) return fail(GI_ERR_NOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(GI_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define GI_CUDA(call, what)                     \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// Makes the index's device current for the scope of a call, then restores.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+enum PtrKind { kDevice, kHost, kBad };
+
+PtrKind pointer_kind(const void* p) {
+  if (!p) return kBad;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return kHost;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return kDevice;
+  return kHost;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// key arrays carry room for the empty slot and for whole-node vector reads past n
+size_t key_alloc_bytes(uint64_t n, int key_bytes) { return round256((n + 1 + 64) * key_bytes + 64); }
+size_t row_alloc_bytes(uint64_t n) { return round256((n + 64) * 4); }
+
+cudaError_t dalloc(void** p, size_t bytes, cudaStream_t s) { return cudaMallocAsync(p, bytes, s); }
+void dfree(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+int read_flags(gi_index* idx) {
+  uint32_t f = 0;
+  cudaError_t e = cudaMemcpyAsync(&f, idx->dflags, sizeof f, cudaMemcpyDeviceToHost, idx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(idx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading device status");
+  idx->latched |= f;
+  return GI_OK;
+}
+
+int check_latched(gi_index* idx) {
+  if (idx->latched & gi::kFlagTimeout)
+    return fail(GI_ERR_TIMEOUT, "a bounded device-side wait gave up; results are not valid");
+  return GI_OK;
+}
+
+gi::LookupCfg resolve_cfg(const gi_index* idx) {
+  gi::LookupCfg c;
+  c.layout = idx->layout;
+  c.key_bytes = idx->key_bytes;
+  const int64_t* o = idx->opt;
+  c.group = o[GI_OPT_GROUP] >= 0 ? (int)o[GI_OPT_GROUP]
+                                  : (idx->layout == GI_EYTZINGER_KARY
+                                         ? gi::eks_default_group(idx->k, idx->key_bytes)
+                                         : 1);
+  int def_pt = 1;
+  if (idx->layout == GI_EYTZINGER) def_pt = 2;
+  if (idx->layout == GI_EYTZINGER_KARY) def_pt = 2;
+  c.per_thread = o[GI_OPT_PER_THREAD] >= 0 ? (int)o[GI_OPT_PER_THREAD] : def_pt;
+  c.smem_levels = o[GI_OPT_SMEM_LEVELS] >= 0 ? (int)o[GI_OPT_SMEM_LEVELS] : 0;
+  c.block = o[GI_OPT_BLOCK] >= 0 ? (int)o[GI_OPT_BLOCK] : 256;
+  c.blocks_per_sm = o[GI_OPT_BLOCKS_PER_SM] >= 0 ? (int)o[GI_OPT_BLOCKS_PER_SM] : 0;
+  c.prefetch = o[GI_OPT_PREFETCH] >= 0 ? (int)o[GI_OPT_PREFETCH] : 0;
+  const int ee = o[GI_OPT_EARLY_EXIT] >= 0 ? (int)o[GI_OPT_EARLY_EXIT] : 1;
+  c.early_exit = (ee && idx->unique) ? 1 : 0;
+  if (c.layout == GI_SORTED) c.per_thread = 1;
+  return c;
+}
+
+cudaError_t launch_point(const gi_index* idx, const gi::LookupCfg& c, const void* q, uint64_t m,
+                         uint32_t* out, cudaStream_t s) {
+  if (idx->key_bytes == 4)
+    return gi::point_lookup_u32(idx->keys, idx->rows, idx->geom, c, q, m, out, idx->dflags, s);
+  return gi::point_lookup_u64(idx->keys, idx->rows, idx->geom, c, q, m, out, idx->dflags, s);
+}
+
+int ensure_staging(gi_index* idx, uint64_t chunk) {
+  if (idx->stage && idx->stage->chunk >= chunk) return GI_OK;
+  if (idx->stage) {
+    cudaStreamSynchronize(idx->stream);
+    for (int i = 0; i < 3; ++i) {
+      if (idx->stage->st[i]) cudaStreamSynchronize(idx->stage->st[i]);
+      cudaFree(idx->stage->q[i]);
+      cudaFree(idx->stage->out[i]);
+      if (idx->stage->st[i]) cudaStreamDestroy(idx->stage->st[i]);
+    }
+    if (idx->stage->ev) cudaEventDestroy(idx->stage->ev);
+    delete idx->stage;
+    idx->stage = nullptr;
+  }
+  GiStaging* st = new GiStaging();
+  st->chunk = chunk;
+  idx->stage = st;
+  for (int i = 0; i < 3; ++i) {
+    GI_CUDA(cudaStreamCreateWithFlags(&st->st[i], cudaStreamNonBlocking), "staging stream");
+    GI_CUDA(cudaMalloc(&st->q[i], chunk * idx->key_bytes), "staging buffer");
+    GI_CUDA(cudaMalloc((void**)&st->out[i], chunk * 4), "staging buffer");
+  }
+  GI_CUDA(cudaEventCreateWithFlags(&st->ev, cudaEventDisableTiming), "staging event");
+  return GI_OK;
+}
+
+int ensure_range_scratch(gi_index* idx, uint64_t m) {
+  const size_t need = gi::range_scratch_bytes(m);
+  if (idx->rscratch_bytes >= need) return GI_OK;
+  dfree(idx->rscratch, idx->stream);
+  idx->rscratch = nullptr;
+  idx->rscratch_bytes = 0;
+  idx->counts_valid = false;
+  GI_CUDA(dalloc(&idx->rscratch, need, idx->stream), "range scratch");
+  idx->rscratch_bytes = need;
+  return GI_OK;
+}
+
+}  // namespace
+
+namespace gi {
+
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int sm_count() {
+  static int cached[64];
+  static std::once_flag once[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  std::call_once(once[dev], [&] {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 1;
+  });
+  return cached[dev];
+}
+
+int device_max_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+Geom make_geom(uint64_t n, uint32_t k) {
+  Geom g{};
+  g.n = n;
+  g.k = k;
+  g.log2k = ((k & (k - 1)) == 0) ? ilog2_const(k) : 0;
+  if (n == 0) return g;
+  uint32_t m = 0;
+  uint64_t p = 1;
+  while (p <= n / k) {
+    p *= k;
+    ++m;
+  }
+  g.m = m;
+  g.top = p - 1;
+  g.b = n - g.top;
+  g.levels = m + 1;
+  return g;
+}
+
+size_t range_scratch_bytes(uint64_t m) {
+  const uint64_t nb = (m + 2047) / 2048;
+  return round256(sizeof(uint64_t) * (m ? m : 1)) + round256(sizeof(uint64_t) * (nb + 1));
+}
+
+bool eks_group_supported(uint32_t k, int group) {
+  static const int pairs[][2] = {{3, 1},  {3, 2},  {4, 1},  {4, 4},  {5, 1},  {5, 2},  {5, 4},
+                                 {8, 1},  {8, 8},  {9, 1},  {9, 2},  {9, 4},  {9, 8},  {16, 1},
+                                 {16, 8}, {16, 16}, {17, 1}, {17, 4}, {17, 8}, {17, 16}, {32, 1},
+                                 {32, 16}, {32, 32}, {33, 1}, {33, 8}, {33, 16}, {33, 32}};
+  for (auto& p : pairs)
+    if ((uint32_t)p[0] == k && p[1] == group) return true;
+  return false;
+}
+
+int eks_default_group(uint32_t k, int key_bytes) {
+  // one 16-byte vector per lane where the node splits that way, else one key per lane
+  const int node_bytes = (int)(k - 1) * key_bytes;
+  if (node_bytes % 16 == 0 && eks_group_supported(k, node_bytes / 16)) return node_bytes / 16;
+  for (int g = 32; g >= 1; g >>= 1)
+    if (eks_group_supported(k, g) && g <= (int)(k - 1)) return g;
+  if (eks_group_supported(k, 1)) return 1;
+  return 1;  // generic kernel
+}
+
+uint64_t smem_slots_for_levels(int layout, const Geom& g, int levels, int key_bytes) {
+  (void)key_bytes;
+  if (levels <= 0 || g.n == 0 || layout == GI_SORTED) return 0;
+  if (layout == GI_EYTZINGER) {
+    const uint64_t s = levels >= 40 ? (1ull << 40) : (1ull << levels);  // slots 0 .. 2^d - 1
+    return std::min<uint64_t>(s, g.n + 1);
+  }
+  uint64_t top = 1;
+  for (int i = 0; i < levels && top <= g.n; ++i) top *= g.k;
+  top -= 1;  // k^d - 1 slots: d whole levels
+  const uint64_t node = g.k - 1;
+  const uint64_t whole = (g.n + node - 1) / node * node;  // round n up to whole nodes
+  return std::min<uint64_t>(top, whole);
+}
+
+}  // namespace gi
+
+// ================================================================= C ABI
+extern "C" {
+
+const char* gi_last_error(void) { return t_err.c_str(); }
+
+uint64_t gi_launch_count(void) { return g_launches.load(); }
+
+int gi_set_stream(gi_index* idx, void* stream) {
+  t_err.clear();
+  if (!idx) {
+    t_default_stream = (cudaStream_t)stream;
+    return GI_OK;
+  }
+  idx->stream = (cudaStream_t)stream;
+  return GI_OK;
+}
+
+static void destroy_impl(gi_index* idx) {
+  if (!idx) return;
+  DeviceScope ds(idx->device);
+  cudaStreamSynchronize(idx->stream);
+  if (idx->stage) {
+    for (int i = 0; i < 3; ++i) {
+      if (idx->stage->st[i]) cudaStreamSynchronize(idx->stage->st[i]);
+      cudaFree(idx->stage->q[i]);
+      cudaFree(idx->stage->out[i]);
+      if (idx->stage->st[i]) cudaStreamDestroy(idx->stage->st[i]);
+    }
+    if (idx->stage->ev) cudaEventDestroy(idx->stage->ev);
+    delete idx->stage;
+  }
+  dfree(idx->keys, idx->stream);
+  dfree(idx->rows, idx->stream);
+  dfree(idx->dflags, idx->stream);
+  dfree(idx->rscratch, idx->stream);
+  cudaStreamSynchronize(idx->stream);
+  cudaGetLastError();
+  delete idx;
+}
+
+void gi_destroy(gi_index* idx) { destroy_impl(idx); }
+
+int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, uint32_t k,
+             gi_index** out) {
+  t_err.clear();
+  if (!out) return fail(GI_ERR_INVALID, "gi_build: out is NULL");
+  *out = nullptr;
+  const int lay = layout & 0xFF;
+  const int kw = layout & ~0xFF;
+  if (kw != GI_KEY_U32 && kw != GI_KEY_U64) return fail(GI_ERR_INVALID, "gi_build: bad key width bits 0x%x", kw);
+  if (lay != GI_SORTED && lay != GI_EYTZINGER && lay != GI_EYTZINGER_KARY)
+    return fail(GI_ERR_INVALID, "gi_build: unknown layout %d", lay);
+  if (lay == GI_EYTZINGER_KARY && (k < 2 || k > 33))
+    return fail(GI_ERR_INVALID, "gi_build: k must be in [2, 33], got %u", k);
+  if (n > 0 && (!keys || !rowids)) return fail(GI_ERR_INVALID, "gi_build: NULL keys or rowids");
+  if (n >= (1ull << 40)) return fail(GI_ERR_INVALID, "gi_build: n too large");
+  const int kb = kw == GI_KEY_U64 ? 8 : 4;
+
+  gi_index* idx = new gi_index();
+  idx->stream = t_default_stream;
+  cudaGetDevice(&idx->device);
+  idx->n = n;
+  idx->layout = lay;
+  idx->k = lay == GI_SORTED ? 0 : (lay == GI_EYTZINGER ? 2 : k);
+  idx->key_bytes = kb;
+  idx->geom = gi::make_geom(n, lay == GI_SORTED ? 2 : idx->k);
+  cudaStream_t s = idx->stream;
+
+  auto bail = [&](int rc) {
+    destroy_impl(idx);
+    return rc;
+  };
+  int rc = GI_OK;
+#define GI_TRY(call, what)                      \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return bail(cuda_fail(e_, what)); \
+  } while (0)
+
+  GI_TRY(dalloc((void**)&idx->dflags, 256, s), "status word");
+  GI_TRY(cudaMemsetAsync(idx->dflags, 0, 256, s), "status word");
+  const size_t kbytes = key_alloc_bytes(n, kb), rbytes = row_alloc_bytes(n);
+  if (n == 0) {
+    GI_TRY(dalloc(&idx->keys, kbytes, s), "index keys");
+    GI_TRY(dalloc((void**)&idx->rows, rbytes, s), "index rows");
+    GI_TRY(cudaMemsetAsync(idx->keys, 0, kbytes, s), "index keys");
+    GI_TRY(cudaStreamSynchronize(s), "gi_build");
+    *out = idx;
+    return GI_OK;
+  }
+  const PtrKind kk = pointer_kind(keys), rk = pointer_kind(rowids);
+  void* bk[2] = {nullptr, nullptr};
+  uint32_t* bv[2] = {nullptr, nullptr};
+  void* scratch = nullptr;
+  auto free_tmp = [&]() {
+    for (int i = 0; i < 2; ++i) {
+      if (bk[i] != idx->keys) dfree(bk[i], s);
+      if (bv[i] != idx->rows) dfree(bv[i], s);
+    }
+    dfree(scratch, s);
+  };
+  auto bail_tmp = [&](int code) {
+    free_tmp();
+    return bail(code);
+  };
+#define GI_TRY2(call, what)                     \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return bail_tmp(cuda_fail(e_, what)); \
+  } while (0)
+  for (int i = 0; i < 2; ++i) {
+    GI_TRY2(dalloc(&bk[i], kbytes, s), "sort buffer");
+    GI_TRY2(dalloc((void**)&bv[i], rbytes, s), "sort buffer");
+  }
+  const void* src_k = keys;
+  const uint32_t* src_v = rowids;
+  bool staged = false;
+  if (kk == kHost) {
+    GI_TRY2(cudaMemcpyAsync(bk[0], keys, n * kb, cudaMemcpyHostToDevice, s), "copying keys");
+    src_k = bk[0];
+    staged = true;
+  }
+  if (rk == kHost) {
+    GI_TRY2(cudaMemcpyAsync(bv[0], rowids, n * 4, cudaMemcpyHostToDevice, s), "copying rowids");
+    src_v = bv[0];
+    staged = true;
+  }
+  const size_t sbytes = gi::sort_scratch_bytes(n, kb);
+  GI_TRY2(dalloc(&scratch, sbytes, s), "sort scratch");
+  uint32_t trivial = 0;
+  GI_TRY2(gi::sort_prepare(src_k, src_v, n, kb, scratch, idx->dflags, s, &trivial), "histogram");
+  // Ping-pong between the two buffers; the first pass writes the buffer that does
+  // not hold a staged copy of the input.
+  const void* ck = src_k;
+  const uint32_t* cv = src_v;
+  int cur = -1;  // -1: the data is still the (caller's or staged) input
+  int next_dst = staged ? 1 : 0;
+  for (int p = 0; p < kb; ++p) {
+    if (trivial & (1u << p)) continue;  // every key has the same digit here
+    const int dst = next_dst;
+    GI_TRY2(gi::sort_pass(ck, cv, bk[dst], bv[dst], n, kb, p, scratch, idx->dflags, s), "radix pass");
+    ck = bk[dst];
+    cv = bv[dst];
+    cur = dst;
+    next_dst = 1 - dst;
+  }
+  if (lay == GI_SORTED) {
+    if (cur < 0) {  // no pass ran (all keys equal): the input order is the sorted order
+      cur = next_dst;
+      GI_TRY2(cudaMemcpyAsync(bk[cur], ck, n * kb, cudaMemcpyDefault, s), "copy");
+      GI_TRY2(cudaMemcpyAsync(bv[cur], cv, n * 4, cudaMemcpyDefault, s), "copy");
+    }
+    idx->keys = bk[cur];
+    idx->rows = bv[cur];
+    GI_TRY2(gi::check_sorted_dups(idx->keys, n, kb, idx->dflags, s), "duplicate check");
+  } else {
+    const int dst = cur >= 0 ? 1 - cur : next_dst;
+    GI_TRY2(gi::layout_gather(ck, cv, bk[dst], bv[dst], idx->geom, kb,
+                              lay == GI_EYTZINGER ? 1u : 0u, idx->dflags, s),
+            "layout permutation");
+    idx->keys = bk[dst];
+    idx->rows = bv[dst];
+  }
+  free_tmp();
+  rc = read_flags(idx);
+  if (rc != GI_OK) return bail(rc);
+  if (idx->latched & gi::kFlagReservedRowid)
+    return bail(fail(GI_ERR_INVALID, "gi_build: a rowID equals the reserved value GI_MISS"));
+  if (idx->latched & gi::kFlagTimeout)
+    return bail(fail(GI_ERR_TIMEOUT, "gi_build: a bounded device-side wait gave up"));
+  idx->unique = !(idx->latched & gi::kFlagDuplicate);
+  idx->latched = 0;
+  GI_TRY(cudaMemsetAsync(idx->dflags, 0, 256, s), "status word");
+  *out = idx;
+  return GI_OK;
+#undef GI_TRY
+#undef GI_TRY2
+}
+
+int gi_point_lookup(const gi_index* cidx, const void* queries, uint64_t m, uint32_t* out_rowids) {
+  t_err.clear();
+  gi_index* idx = const_cast<gi_index*>(cidx);
+  if (!idx) return fail(GI_ERR_INVALID, "gi_point_lookup: NULL index");
+  if (m == 0) return GI_OK;
+  if (!queries || !out_rowids) return fail(GI_ERR_INVALID, "gi_point_lookup: NULL pointer");
+  DeviceScope ds(idx->device);
+  const gi::LookupCfg c = resolve_cfg(idx);
+  const PtrKind qk = pointer_kind(queries), ok = pointer_kind(out_rowids);
+  if (qk == kDevice && ok == kDevice) {
+    GI_CUDA(launch_point(idx, c, queries, m, out_rowids, idx->stream), "point lookup");
+    return GI_OK;
+  }
+  // host memory: pipelined chunks on three internal streams
+  const uint64_t chunk = std::min<uint64_t>(m, 1ull << 22);
+  int rc = ensure_staging(idx, chunk);
+  if (rc != GI_OK) return rc;
+  GiStaging* st = idx->stage;
+  GI_CUDA(cudaEventRecord(st->ev, idx->stream), "staging event");
+  for (int i = 0; i < 3; ++i) GI_CUDA(cudaStreamWaitEvent(st->st[i], st->ev, 0), "staging wait");
+  const int kb = idx->key_bytes;
+  uint64_t ci = 0;
+  for (uint64_t off = 0; off < m; off += chunk, ++ci) {
+    const uint64_t len = std::min<uint64_t>(chunk, m - off);
+    const int b = (int)(ci % 3);
+    cudaStream_t s = st->st[b];
+    const void* qd = (const char*)queries + off * kb;
+    if (qk == kHost) {
+      GI_CUDA(cudaMemcpyAsync(st->q[b], qd, len * kb, cudaMemcpyHostToDevice, s), "copying probes");
+      qd = st->q[b];
+    }
+    uint32_t* od = ok == kHost ? st->out[b] : out_rowids + off;
+    GI_CUDA(launch_point(idx, c, qd, len, od, s), "point lookup");
+    if (ok == kHost)
+      GI_CUDA(cudaMemcpyAsync(out_rowids + off, od, len * 4, cudaMemcpyDeviceToHost, s), "copying results");
+  }
+  for (int i = 0; i < 3; ++i) GI_CUDA(cudaStreamSynchronize(st->st[i]), "point lookup");
+  rc = read_flags(idx);
+  if (rc != GI_OK) return rc;
+  return check_latched(idx);
+}
+
+int gi_range_lookup(const gi_index* cidx, const void* lo, const void* hi, uint64_t m,
+                    uint64_t* out_offsets, uint32_t* out_rowids) {
+  t_err.clear();
+  gi_index* idx = const_cast<gi_index*>(cidx);
+  if (!idx) return fail(GI_ERR_INVALID, "gi_range_lookup: NULL index");
+  if (!out_offsets) return fail(GI_ERR_INVALID, "gi_range_lookup: NULL out_offsets");
+  if (m > 0 && (!lo || !hi)) return fail(GI_ERR_INVALID, "gi_range_lookup: NULL bounds");
+  DeviceScope ds(idx->device);
+  const gi::LookupCfg c = resolve_cfg(idx);
+  const int kb = idx->key_bytes;
+  cudaStream_t s = idx->stream;
+  const PtrKind lk = m ? pointer_kind(lo) : kDevice, hk = m ? pointer_kind(hi) : kDevice;
+  const PtrKind ofk = pointer_kind(out_offsets);
+  const PtrKind rk = out_rowids ? pointer_kind(out_rowids) : kDevice;
+  auto run = [&](const void* dlo, const void* dhi, uint64_t* doff, uint32_t* drows,
+                 bool ready) -> cudaError_t {
+    if (kb == 4)
+      return gi::range_lookup_u32(idx->keys, idx->rows, idx->geom, c, dlo, dhi, m, doff, drows,
+                                  idx->rscratch, ready, s);
+    return gi::range_lookup_u64(idx->keys, idx->rows, idx->geom, c, dlo, dhi, m, doff, drows,
+                                idx->rscratch, ready, s);
+  };
+  int rc = ensure_range_scratch(idx, m);
+  if (rc != GI_OK) return rc;
+  if (lk == kDevice && hk == kDevice && ofk == kDevice && rk == kDevice) {
+    const bool ready = out_rowids && idx->counts_valid && idx->last_lo == lo &&
+                       idx->last_hi == hi && idx->last_m == m && idx->last_off == out_offsets;
+    GI_CUDA(run(lo, hi, out_offsets, out_rowids, ready), "range lookup");
+    idx->counts_valid = out_rowids == nullptr;
+    idx->last_lo = lo;
+    idx->last_hi = hi;
+    idx->last_m = m;
+    idx->last_off = out_offsets;
+    return GI_OK;
+  }
+  // host memory somewhere: stage everything through temporary device buffers
+  idx->counts_valid = false;
+  void *dlo = nullptr, *dhi = nullptr;
+  uint64_t* doff = nullptr;
+  uint32_t* drows = nullptr;
+  auto cleanup = [&]() {
+    if (lk == kHost) dfree(dlo, s);
+    if (hk == kHost) dfree(dhi, s);
+    if (ofk == kHost) dfree(doff, s);
+    if (out_rowids && rk == kHost) dfree(drows, s);
+    cudaStreamSynchronize(s);
+  };
+  auto stage_fail = [&](cudaError_t e, const char* what) {
+    cleanup();
+    return cuda_fail(e, what);
+  };
+#define GI_TRY3(call, what)                          \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return stage_fail(e_, what); \
+  } while (0)
+  const size_t bb = (m ? m : 1) * kb;
+  if (lk == kHost) {
+    GI_TRY3(dalloc(&dlo, bb, s), "staging");
+    GI_TRY3(cudaMemcpyAsync(dlo, lo, m * kb, cudaMemcpyHostToDevice, s), "copying bounds");
+  } else {
+    dlo = const_cast<void*>(lo);
+  }
+  if (hk == kHost) {
+    GI_TRY3(dalloc(&dhi, bb, s), "staging");
+    GI_TRY3(cudaMemcpyAsync(dhi, hi, m * kb, cudaMemcpyHostToDevice, s), "copying bounds");
+  } else {
+    dhi = const_cast<void*>(hi);
+  }
+  if (ofk == kHost) {
+    GI_TRY3(dalloc((void**)&doff, (m + 1) * 8, s), "staging");
+  } else {
+    doff = out_offsets;
+  }
+  GI_TRY3(run(dlo, dhi, doff, nullptr, false), "range lookup");
+  if (out_rowids) {
+    uint64_t total = 0;
+    GI_TRY3(cudaMemcpyAsync(&total, doff + m, 8, cudaMemcpyDeviceToHost, s), "reading total");
+    GI_TRY3(cudaStreamSynchronize(s), "range lookup");
+    if (rk == kHost) {
+      GI_TRY3(dalloc((void**)&drows, (total ? total : 1) * 4, s), "staging");
+    } else {
+      drows = out_rowids;
+    }
+    GI_TRY3(run(dlo, dhi, doff, drows, true), "range fill");
+    if (rk == kHost && total)
+      GI_TRY3(cudaMemcpyAsync(out_rowids, drows, total * 4, cudaMemcpyDeviceToHost, s), "copying rows");
+  }
+  if (ofk == kHost)
+    GI_TRY3(cudaMemcpyAsync(out_offsets, doff, (m + 1) * 8, cudaMemcpyDeviceToHost, s), "copying offsets");
+  cleanup();
+  GI_CUDA(cudaGetLastError(), "range lookup");
+  rc = read_flags(idx);
+  if (rc != GI_OK) return rc;
+  return check_latched(idx);
+#undef GI_TRY3
+}
+
+int gi_sync(gi_index* idx) {
+  t_err.clear();
+  if (!idx) return fail(GI_ERR_INVALID, "gi_sync: NULL index");
+  DeviceScope ds(idx->device);
+  int rc = read_flags(idx);
+  if (rc != GI_OK) return rc;
+  return check_latched(idx);
+}
+
+uint64_t gi_footprint_bytes(const gi_index* idx) {
+  if (!idx) return 0;
+  return idx->n * (uint64_t)(idx->key_bytes + 4) + (idx->layout == GI_EYTZINGER ? idx->key_bytes : 0);
+}
+
+int gi_get_info(const gi_index* idx, gi_info* out) {
+  t_err.clear();
+  if (!idx || !out) return fail(GI_ERR_INVALID, "gi_get_info: NULL argument");
+  memset(out, 0, sizeof *out);
+  out->n = idx->n;
+  out->layout = idx->layout;
+  out->k = idx->k;
+  out->key_bytes = idx->key_bytes;
+  out->unique = idx->unique ? 1 : 0;
+  if (idx->layout == GI_SORTED) {
+    uint32_t l = 0;
+    while (l < 64 && (1ull << l) <= idx->n) ++l;
+    out->levels = l;
+  } else {
+    out->levels = idx->geom.levels;
+  }
+  out->keys = idx->keys;
+  out->rowids = idx->rows;
+  out->footprint_bytes = gi_footprint_bytes(idx);
+  return GI_OK;
+}
+
+int gi_copy_layout(const gi_index* cidx, void* keys_out, uint32_t* rowids_out) {
+  t_err.clear();
+  gi_index* idx = const_cast<gi_index*>(cidx);
+  if (!idx) return fail(GI_ERR_INVALID, "gi_copy_layout: NULL index");
+  DeviceScope ds(idx->device);
+  const char* src = (const char*)idx->keys + (idx->layout == GI_EYTZINGER ? idx->key_bytes : 0);
+  if (keys_out && idx->n)
+    GI_CUDA(cudaMemcpyAsync(keys_out, src, idx->n * idx->key_bytes, cudaMemcpyDefault, idx->stream),
+            "copying keys");
+  if (rowids_out && idx->n)
+    GI_CUDA(cudaMemcpyAsync(rowids_out, idx->rows, idx->n * 4, cudaMemcpyDefault, idx->stream),
+            "copying rowids");
+  GI_CUDA(cudaStreamSynchronize(idx->stream), "gi_copy_layout");
+  return GI_OK;
+}
+
+int gi_set_option(gi_index* idx, int option, int64_t v) {
+  t_err.clear();
+  if (!idx) return fail(GI_ERR_INVALID, "gi_set_option: NULL index");
+  if (option < 1 || option > 7) return fail(GI_ERR_INVALID, "gi_set_option: unknown option %d", option);
+  if (v == -1) {
+    idx->opt[option] = -1;
+    return GI_OK;
+  }
+  switch (option) {
+    case GI_OPT_GROUP:
+      if (idx->layout != GI_EYTZINGER_KARY || !gi::eks_group_supported(idx->k, (int)v))
+        return fail(GI_ERR_INVALID, "gi_set_option: group %lld not available for this index", (long long)v);
+      break;
+    case GI_OPT_PER_THREAD:
+      if (v != 1 && v != 2 && v != 4) return fail(GI_ERR_INVALID, "gi_set_option: per-thread must be 1, 2 or 4");
+      break;
+    case GI_OPT_SMEM_LEVELS: {
+      if (v < 0 || v > 40) return fail(GI_ERR_INVALID, "gi_set_option: smem levels out of range");
+      DeviceScope ds(idx->device);
+      const uint64_t slots = gi::smem_slots_for_levels(idx->layout, idx->geom, (int)v, idx->key_bytes);
+      const uint64_t bytes = (slots * idx->key_bytes + 15) & ~15ull;
+      if (bytes > (uint64_t)gi::device_max_smem_optin() - 1024)
+        return fail(GI_ERR_INVALID, "gi_set_option: %lld levels need %llu bytes of shared memory",
+                    (long long)v, (unsigned long long)bytes);
+      break;
+    }
+    case GI_OPT_BLOCK:
+      if (v != 64 && v != 128 && v != 256 && v != 512)
+        return fail(GI_ERR_INVALID, "gi_set_option: block must be 64, 128, 256 or 512");
+      break;
+    case GI_OPT_BLOCKS_PER_SM:
+      if (v < 0 || v > 32) return fail(GI_ERR_INVALID, "gi_set_option: blocks per SM out of range");
+      break;
+    case GI_OPT_PREFETCH:
+      if (v != 0 && v != 2 && v != 3 && v != 4) return fail(GI_ERR_INVALID, "gi_set_option: prefetch must be 0, 2, 3 or 4");
+      break;
+    case GI_OPT_EARLY_EXIT:
+      if (v != 0 && v != 1) return fail(GI_ERR_INVALID, "gi_set_option: early exit must be 0 or 1");
+      break;
+  }
+  idx->opt[option] = v;
+  return GI_OK;
+}
+
+int gi_get_option(const gi_index* idx, int option, int64_t* v) {
+  t_err.clear();
+  if (!idx || !v) return fail(GI_ERR_INVALID, "gi_get_option: NULL argument");
+  if (option < 1 || option > 7) return fail(GI_ERR_INVALID, "gi_get_option: unknown option %d", option);
+  const gi::LookupCfg c = resolve_cfg(idx);
+  switch (option) {
+    case GI_OPT_GROUP: *v = c.group; break;
+    case GI_OPT_PER_THREAD: *v = c.per_thread; break;
+    case GI_OPT_SMEM_LEVELS: *v = c.smem_levels; break;
+    case GI_OPT_BLOCK: *v = c.block; break;
+    case GI_OPT_BLOCKS_PER_SM: *v = c.blocks_per_sm; break;
+    case GI_OPT_PREFETCH: *v = c.prefetch; break;
+    case GI_OPT_EARLY_EXIT: *v = c.early_exit; break;
+  }
+  return GI_OK;
+}
+
+int gi_probe_random_sectors(const void* buf, uint64_t bytes, uint32_t chunk_bytes, uint64_t loads,
+                            uint64_t seed, uint64_t* sink, void* stream) {
+  t_err.clear();
+  if (!buf || !sink) return fail(GI_ERR_INVALID, "gi_probe_random_sectors: NULL pointer");
+  if (chunk_bytes != 16 && chunk_bytes != 32 && chunk_bytes != 64 && chunk_bytes != 128 &&
+      chunk_bytes != 256)
+    return fail(GI_ERR_INVALID, "gi_probe_random_sectors: chunk must be 16..256 bytes, a power of two");
+  if (((uintptr_t)buf & 255) || bytes < chunk_bytes)
+    return fail(GI_ERR_INVALID, "gi_probe_random_sectors: buffer must be 256-byte aligned and hold a chunk");
+  if (pointer_kind(buf) != kDevice || pointer_kind(sink) != kDevice)
+    return fail(GI_ERR_INVALID, "gi_probe_random_sectors: buffers must be device memory");
+  GI_CUDA(gi::probe_random_sectors(buf, bytes, chunk_bytes, loads, seed, sink, (cudaStream_t)stream),
+          "probe");
+  return GI_OK;
+}
+
+int gi_coalescing_probe(const uint32_t* buf, uint64_t entries, uint32_t threads, uint32_t group,
+                        uint32_t steps, uint64_t seed, uint64_t* sink, void* stream) {
+  t_err.clear();
+  if (!buf || !sink) return fail(GI_ERR_INVALID, "gi_coalescing_probe: NULL pointer");
+  if (group == 0 || group > threads || group > entries || threads == 0)
+    return fail(GI_ERR_INVALID, "gi_coalescing_probe: need 0 < group <= threads, group <= entries");
+  if (pointer_kind(buf) != kDevice || pointer_kind(sink) != kDevice)
+    return fail(GI_ERR_INVALID, "gi_coalescing_probe: buffers must be device memory");
+  GI_CUDA(gi::coalescing_probe(buf, entries, threads, group, steps, seed, sink, (cudaStream_t)stream),
+          "probe");
+  return GI_OK;
+}
+
+}  // extern "C"

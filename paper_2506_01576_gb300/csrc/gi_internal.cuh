@@ -1,0 +1,186 @@
+// Internal declarations shared by the CUDA translation units of libgi.
+//
+// Index geometry and the two closed-form maps between a slot of the
+// (k-ary) Eytzinger array and the rank (sorted position) of the key it holds:
+//   slot -> rank : p'(t) of Section 6.1 (k = 2: Section 4), read with the bottom
+//                  level at t >= k^m - 1 and the level of slot t as
+//                  floor(log_k(t + 1));
+//   rank -> slot : its inverse, derived from the same level structure.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gi.h"
+
+namespace gi {
+
+// ---------------------------------------------------------------- device status bits
+enum : uint32_t {
+  kFlagReservedRowid = 1u << 0,  // an input rowID equals GI_MISS
+  kFlagDuplicate = 1u << 1,      // two equal keys were found (index not unique)
+  kFlagTimeout = 1u << 2,        // a bounded spin gave up
+};
+
+// Spin limit for every device-side wait (each iteration sleeps ~100 ns or more).
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+  uint64_t n;          // keys
+  uint64_t top;        // k^m - 1: keys in the full levels 0..m-1
+  uint64_t b;          // n - top: keys in the (partial) bottom level m, 1 <= b
+  uint32_t k;          // fan-out (2 = Eytzinger)
+  uint32_t m;          // floor(log_k n)
+  uint32_t levels;     // m + 1 for n >= 1, 0 for n == 0
+  uint32_t log2k;      // log2(k) if k is a power of two, else 0
+};
+
+Geom make_geom(uint64_t n, uint32_t k);  // host
+
+__host__ __device__ constexpr uint32_t ilog2_const(uint32_t v) {
+  return v <= 1 ? 0 : 1 + ilog2_const(v >> 1);
+}
+
+// k^e (e small; the caller guarantees no overflow)
+template <int KF>
+__host__ __device__ __forceinline__ uint64_t kpow(uint32_t e, const Geom& g) {
+  const uint32_t k = KF ? KF : g.k;
+  if ((k & (k - 1)) == 0) return 1ull << (e * (KF ? ilog2_const(KF) : g.log2k));
+  uint64_t p = 1;
+  for (uint32_t i = 0; i < e; ++i) p *= k;
+  return p;
+}
+
+// floor(log_k(x)) for 1 <= x
+template <int KF>
+__host__ __device__ __forceinline__ uint32_t floor_log_k(uint64_t x, const Geom& g) {
+  const uint32_t k = KF ? KF : g.k;
+  if ((k & (k - 1)) == 0) {
+    const uint32_t s = KF ? ilog2_const(KF) : g.log2k;
+#ifdef __CUDA_ARCH__
+    const uint32_t lg = 63 - __clzll((long long)x);
+#else
+    const uint32_t lg = 63 - __builtin_clzll(x);
+#endif
+    return lg / s;
+  }
+  uint32_t l = 0;
+  uint64_t p = k;
+  while (p <= x) {
+    ++l;
+    if (p > x / k) break;
+    p *= k;
+  }
+  return l;
+}
+
+// Slot t (0-based) -> rank of the key it holds (Section 6.1, Section 4 for k = 2).
+template <int KF>
+__host__ __device__ __forceinline__ uint64_t slot_to_rank(uint64_t t, const Geom& g) {
+  const uint64_t k = KF ? (uint64_t)KF : (uint64_t)g.k;
+  const uint64_t km1 = k - 1;
+  if (t >= g.top) {  // bottom level: node-major, one rank skipped after each node
+    const uint64_t i = t - g.top;
+    return i + i / km1;
+  }
+  const uint32_t l = floor_log_k<KF>(t + 1, g);
+  const uint64_t i = t - (kpow<KF>(l, g) - 1);
+  const uint64_t p = kpow<KF>(g.m - l - 1, g) * (1 + i + i / km1) - 1;  // rank in the perfect tree
+  const uint64_t corr = km1 * (p + 1);                                   // bottom keys to its left
+  return p + (g.b < corr ? g.b : corr);
+}
+
+// Rank r -> slot holding it (inverse of slot_to_rank).
+template <int KF>
+__host__ __device__ __forceinline__ uint64_t rank_to_slot(uint64_t r, const Geom& g) {
+  const uint64_t k = KF ? (uint64_t)KF : (uint64_t)g.k;
+  const uint64_t km1 = k - 1;
+  const uint64_t c = r / k, o = r - c * k;
+  if (o < km1 && c * km1 + o < g.b) return g.top + c * km1 + o;  // bottom-level key
+  const uint64_t below = c * km1 + o;
+  const uint64_t q = r - (g.b < below ? g.b : below);  // rank among the upper-level keys
+  uint64_t x = q + 1;
+  uint32_t z = 0;
+  while (x % k == 0) {
+    x /= k;
+    ++z;
+  }
+  const uint32_t l = g.m - 1 - z;
+  const uint64_t xd = x / k;
+  return (kpow<KF>(l, g) - 1) + xd * km1 + (x - xd * k) - 1;
+}
+
+// ---------------------------------------------------------------- launch bookkeeping
+void count_launch(uint64_t n = 1);
+int sm_count();
+int device_max_smem_optin();
+
+// ---------------------------------------------------------------- kernel entry points (host side)
+// Radix sort + layout (gi_sort.cu).  Returns cudaError_t.
+struct SortBuffers {
+  void* keys[2];
+  uint32_t* vals[2];
+  void* scratch;          // histogram + status + counters
+  size_t scratch_bytes;
+};
+size_t sort_scratch_bytes(uint64_t n, int key_bytes);
+// Histogram all digits, check rowIDs; fills hist scan on device; host reads trivial mask.
+cudaError_t sort_prepare(const void* keys, const uint32_t* vals, uint64_t n, int key_bytes,
+                         void* scratch, uint32_t* dflags, cudaStream_t s,
+                         uint32_t* host_trivial_mask /* pinned or pageable, sync inside */);
+cudaError_t sort_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
+                      uint64_t n, int key_bytes, int pass, void* scratch, uint32_t* dflags,
+                      cudaStream_t s);
+cudaError_t layout_gather(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
+                          const Geom& g, int key_bytes, uint32_t key_off, uint32_t* dflags,
+                          cudaStream_t s);
+cudaError_t check_sorted_dups(const void* sk, uint64_t n, int key_bytes, uint32_t* dflags,
+                              cudaStream_t s);
+
+// Point lookups (gi_point.cu).
+struct LookupCfg {
+  int layout;         // GI_SORTED / GI_EYTZINGER / GI_EYTZINGER_KARY
+  int key_bytes;
+  int group;          // lanes per lookup (EKS)
+  int per_thread;     // lookups interleaved per thread / group
+  int smem_levels;    // top levels staged in shared memory
+  int block;          // threads per block
+  int blocks_per_sm;  // 0: one thread (group) per work item
+  int prefetch;       // EBS prefetch distance
+  int early_exit;     // stop on an equal pivot (unique keys only)
+};
+cudaError_t point_lookup_u32(const void* keys, const uint32_t* rows, const Geom& g,
+                             const LookupCfg& c, const void* q, uint64_t m, uint32_t* out,
+                             uint32_t* dflags, cudaStream_t s);
+cudaError_t point_lookup_u64(const void* keys, const uint32_t* rows, const Geom& g,
+                             const LookupCfg& c, const void* q, uint64_t m, uint32_t* out,
+                             uint32_t* dflags, cudaStream_t s);
+// (k, group) pairs the lane-group kernel is compiled for
+bool eks_group_supported(uint32_t k, int group);
+int eks_default_group(uint32_t k, int key_bytes);
+// slots staged in shared memory for `levels` top levels (0 = none)
+uint64_t smem_slots_for_levels(int layout, const Geom& g, int levels, int key_bytes);
+
+// Range lookups (gi_lookup_u32/u64.cu).  scratch: range_scratch_bytes(m) bytes.
+// counts_ready: `offsets` already holds the scanned offsets of these ranges and
+// scratch their lower ranks (the first call of the two-call protocol).
+size_t range_scratch_bytes(uint64_t m);
+cudaError_t range_lookup_u32(const void* keys, const uint32_t* rows, const Geom& g,
+                             const LookupCfg& c, const void* lo, const void* hi, uint64_t m,
+                             uint64_t* offsets, uint32_t* out_rows, void* scratch,
+                             bool counts_ready, cudaStream_t s);
+cudaError_t range_lookup_u64(const void* keys, const uint32_t* rows, const Geom& g,
+                             const LookupCfg& c, const void* lo, const void* hi, uint64_t m,
+                             uint64_t* offsets, uint32_t* out_rows, void* scratch,
+                             bool counts_ready, cudaStream_t s);
+
+// Probes (gi_probe.cu).
+cudaError_t probe_random_sectors(const void* buf, uint64_t bytes, uint32_t chunk_bytes,
+                                 uint64_t loads, uint64_t seed, uint64_t* sink,
+                                 cudaStream_t s);
+cudaError_t coalescing_probe(const uint32_t* buf, uint64_t entries, uint32_t threads,
+                             uint32_t group, uint32_t steps, uint64_t seed, uint64_t* sink,
+                             cudaStream_t s);
+
+}  // namespace gi

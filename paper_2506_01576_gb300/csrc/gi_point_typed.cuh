@@ -1,0 +1,115 @@
+// Launch logic of the point-lookup kernels for one key type (included by
+// gi_point_u32.cu / gi_point_u64.cu).
+#pragma once
+
+#include "gi_point_impl.cuh"
+
+namespace gi {
+namespace pt {
+
+// Every (k, group) pair instantiated for the lane-group kernel.  G = 1 is the
+// single-thread variant.  The list is the same for both key types.
+#define GI_EKS_PAIRS(X) \
+  X(3, 1) X(3, 2)                        \
+  X(4, 1) X(4, 4)                        \
+  X(5, 1) X(5, 2) X(5, 4)                \
+  X(8, 1) X(8, 8)                        \
+  X(9, 1) X(9, 2) X(9, 4) X(9, 8)        \
+  X(16, 1) X(16, 8) X(16, 16)            \
+  X(17, 1) X(17, 4) X(17, 8) X(17, 16)   \
+  X(32, 1) X(32, 16) X(32, 32)           \
+  X(33, 1) X(33, 8) X(33, 16) X(33, 32)
+
+inline bool eks_pair_listed(uint32_t k, int g) {
+#define GI_X(KF, G) if (k == KF && g == G) return true;
+  GI_EKS_PAIRS(GI_X)
+#undef GI_X
+  return false;
+}
+
+template <class Kern>
+inline cudaError_t set_smem(Kern kern, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+inline unsigned grid_size(uint64_t threads_needed, int block, int blocks_per_sm) {
+  if (blocks_per_sm > 0) return (unsigned)(sm_count() * blocks_per_sm);
+  uint64_t g = (threads_needed + block - 1) / block;
+  if (g == 0) g = 1;
+  if (g > 0x7fffffffull) g = 0x7fffffffull;
+  return (unsigned)g;
+}
+
+template <class K>
+cudaError_t point_lookup_typed(const K* keys, const uint32_t* rows, const Geom& g,
+                               const LookupCfg& c, const K* q, uint64_t m, uint32_t* out,
+                               uint32_t* dflags, cudaStream_t s) {
+  const int block = c.block;
+  const int R = c.per_thread;
+  if (c.layout == GI_SORTED) {
+    const unsigned grid = grid_size(m, block, c.blocks_per_sm);
+    k_bs_point<K><<<grid, block, 0, s>>>(keys, rows, g.n, q, m, out);
+    count_launch();
+    return cudaGetLastError();
+  }
+  const uint64_t slots = smem_slots_for_levels(c.layout, g, c.smem_levels, sizeof(K));
+  const size_t smem = (size_t)((slots * sizeof(K) + 15) & ~15ull);
+  if (c.layout == GI_EYTZINGER) {
+    const unsigned grid = grid_size((m + R - 1) / R, block, c.blocks_per_sm);
+    cudaError_t e = cudaErrorInvalidValue;
+#define GI_EBS(RR, PFF)                                                                        \
+  if (R == RR && c.prefetch == PFF) {                                                          \
+    auto kern = k_ebs_point<K, RR, PFF>;                                                       \
+    e = set_smem(kern, smem);                                                                  \
+    if (e != cudaSuccess) return e;                                                            \
+    kern<<<grid, block, smem, s>>>(keys, rows, g.n, g.levels, q, m, out, (uint32_t)slots,      \
+                                   dflags);                                                    \
+    count_launch();                                                                            \
+    return cudaGetLastError();                                                                 \
+  }
+    GI_EBS(1, 0) GI_EBS(1, 2) GI_EBS(1, 3) GI_EBS(1, 4)
+    GI_EBS(2, 0) GI_EBS(2, 2) GI_EBS(2, 3) GI_EBS(2, 4)
+    GI_EBS(4, 0) GI_EBS(4, 2) GI_EBS(4, 3) GI_EBS(4, 4)
+#undef GI_EBS
+    return e;
+  }
+  // k-ary Eytzinger
+  const int G = c.group;
+  const uint32_t k = g.k;
+  const unsigned grid = grid_size((m + R - 1) / R * (uint64_t)G, block, c.blocks_per_sm);
+#define GI_X(KF, GG)                                                                          \
+  if (k == KF && G == GG) {                                                                   \
+    if (R == 1) {                                                                             \
+      auto kern = k_eks_point<K, KF, GG, 1>;                                                  \
+      cudaError_t e = set_smem(kern, smem);                                                   \
+      if (e != cudaSuccess) return e;                                                         \
+      kern<<<grid, block, smem, s>>>(keys, rows, g.n, g.levels, q, m, out, (uint32_t)slots,   \
+                                     c.early_exit, dflags);                                   \
+    } else if (R == 2) {                                                                      \
+      auto kern = k_eks_point<K, KF, GG, 2>;                                                  \
+      cudaError_t e = set_smem(kern, smem);                                                   \
+      if (e != cudaSuccess) return e;                                                         \
+      kern<<<grid, block, smem, s>>>(keys, rows, g.n, g.levels, q, m, out, (uint32_t)slots,   \
+                                     c.early_exit, dflags);                                   \
+    } else {                                                                                  \
+      auto kern = k_eks_point<K, KF, GG, 4>;                                                  \
+      cudaError_t e = set_smem(kern, smem);                                                   \
+      if (e != cudaSuccess) return e;                                                         \
+      kern<<<grid, block, smem, s>>>(keys, rows, g.n, g.levels, q, m, out, (uint32_t)slots,   \
+                                     c.early_exit, dflags);                                   \
+    }                                                                                         \
+    count_launch();                                                                           \
+    return cudaGetLastError();                                                                \
+  }
+  GI_EKS_PAIRS(GI_X)
+#undef GI_X
+  // any other k: one thread per lookup
+  const unsigned ggrid = grid_size(m, block, c.blocks_per_sm);
+  k_eks_generic<K><<<ggrid, block, 0, s>>>(keys, rows, g.n, k, q, m, out, c.early_exit);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace pt
+}  // namespace gi

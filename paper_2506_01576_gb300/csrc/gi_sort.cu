@@ -1,0 +1,439 @@
+// Build path: stable LSD radix sort of (key, rowID) pairs, then the closed-form
+// permutation into Eytzinger / k-ary Eytzinger order.
+//
+// The paper builds the sorted array with a library key-value sort (Section 3)
+// and moves it into Eytzinger order with one thread per target slot, each
+// computing the source position p'(t) in closed form and copying one entry
+// (Section 4, generalised to k in Section 6.1).  Here the sort is our own:
+//
+//   1. sort_prepare: one read of the keys computes the 256-bin histogram of
+//      every 8-bit digit at once, checks the rowIDs for the reserved value, and
+//      scans each histogram into global digit offsets.  Passes whose digit is
+//      the same for every key are skipped.
+//   2. sort_pass (one per remaining digit): a single-pass "onesweep" scatter.
+//      Each CTA takes the next tile in launch order, ranks its keys stably by
+//      digit with warp ballots, publishes its per-digit counts and finds its
+//      global offsets by decoupled look-back over earlier tiles (a bounded wait),
+//      then writes keys and rowIDs through shared memory so that each digit's
+//      run leaves the SM as consecutive addresses.
+//   3. layout_gather: slot t <- sorted[p'(t)], one read and one write per entry,
+//      fused with the duplicate-key check.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gi_internal.cuh"
+
+namespace gi {
+
+namespace {
+
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+
+template <class K>
+struct SortTile;
+template <>
+struct SortTile<uint32_t> {
+  static constexpr int kItems = 16;
+};
+template <>
+struct SortTile<uint64_t> {
+  static constexpr int kItems = 12;
+};
+
+// Status word of the look-back: [63:62] flag, [61:40] epoch, [39:0] count.
+constexpr uint64_t kStatAggregate = 1ull << 62;
+constexpr uint64_t kStatInclusive = 2ull << 62;
+constexpr uint64_t kValueMask = (1ull << 40) - 1;
+
+__device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_volatile_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Scratch layout (bytes, each region 256-aligned):
+//   hist    [passes][256] u64   digit counts
+//   offs    [passes][256] u64   exclusive digit offsets
+//   trivial [passes]      u32   1 if one digit holds every key
+//   counter [passes]      u32   tile tickets
+//   status  [tiles][256]  u64   look-back words (epoch = pass + 1)
+struct ScratchView {
+  unsigned long long* hist;
+  unsigned long long* offs;
+  uint32_t* trivial;
+  uint32_t* counter;
+  uint64_t* status;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+inline uint64_t tiles_for(uint64_t n, int key_bytes) {
+  const uint64_t tile = (uint64_t)kSortThreads *
+                        (key_bytes == 4 ? SortTile<uint32_t>::kItems : SortTile<uint64_t>::kItems);
+  return (n + tile - 1) / tile;
+}
+
+inline ScratchView view(void* scratch, int key_bytes) {
+  const int passes = key_bytes;  // 8-bit digits
+  char* p = (char*)scratch;
+  ScratchView v;
+  v.hist = (unsigned long long*)p;
+  p += align256(sizeof(uint64_t) * passes * kRadix);
+  v.offs = (unsigned long long*)p;
+  p += align256(sizeof(uint64_t) * passes * kRadix);
+  v.trivial = (uint32_t*)p;
+  p += align256(sizeof(uint32_t) * passes);
+  v.counter = (uint32_t*)p;
+  p += align256(sizeof(uint32_t) * passes);
+  v.status = (uint64_t*)p;
+  return v;
+}
+
+inline size_t header_bytes(int key_bytes) {
+  const int passes = key_bytes;
+  return 2 * align256(sizeof(uint64_t) * passes * kRadix) + 2 * align256(sizeof(uint32_t) * passes);
+}
+
+// ---------------------------------------------------------------- histogram
+template <class K>
+__global__ void __launch_bounds__(256) k_histogram(const K* __restrict__ keys,
+                                                   const uint32_t* __restrict__ rows, uint64_t n,
+                                                   unsigned long long* __restrict__ hist,
+                                                   uint32_t* __restrict__ flags) {
+  constexpr int P = sizeof(K);
+  __shared__ uint32_t sh[P][kRadix];
+  for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  bool bad = false;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const K key = keys[i];
+#pragma unroll
+    for (int p = 0; p < P; ++p) atomicAdd(&sh[p][(uint32_t)(key >> (8 * p)) & 0xFF], 1u);
+    bad |= rows[i] == GI_MISS;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagReservedRowid);
+  __syncthreads();
+  for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) {
+    const uint32_t c = (&sh[0][0])[i];
+    if (c) atomicAdd(&hist[i], (unsigned long long)c);
+  }
+}
+
+// One block per pass: exclusive scan of the 256 digit counts.
+__global__ void __launch_bounds__(256) k_scan_hist(const unsigned long long* __restrict__ hist,
+                                                   unsigned long long* __restrict__ offs,
+                                                   uint32_t* __restrict__ trivial, uint64_t n) {
+  __shared__ unsigned long long warp_tot[8];
+  __shared__ uint32_t any_full;
+  const int p = blockIdx.x, d = threadIdx.x, lane = d & 31, w = d >> 5;
+  if (d == 0) any_full = 0;
+  __syncthreads();
+  const unsigned long long c = hist[p * kRadix + d];
+  if (c == n) atomicOr(&any_full, 1u);
+  unsigned long long x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  unsigned long long base = 0;
+  for (int i = 0; i < w; ++i) base += warp_tot[i];
+  offs[p * kRadix + d] = base + x - c;
+  __syncthreads();
+  if (d == 0) trivial[p] = any_full;
+}
+
+// ---------------------------------------------------------------- one onesweep pass
+template <class K>
+__global__ void __launch_bounds__(kSortThreads) k_sort_pass(
+    const K* __restrict__ src_k, const uint32_t* __restrict__ src_v, K* __restrict__ dst_k,
+    uint32_t* __restrict__ dst_v, uint64_t n, uint32_t shift,
+    const unsigned long long* __restrict__ digit_off, uint64_t* __restrict__ status,
+    uint32_t* __restrict__ tile_counter, uint32_t epoch, uint32_t* __restrict__ flags) {
+  constexpr int ITEMS = SortTile<K>::kItems;
+  constexpr int TILE = kSortThreads * ITEMS;
+  struct WarpHist {
+    uint32_t h[kSortWarps][kRadix];
+  };
+  union Exchange {
+    WarpHist wh;
+    K keys[TILE];
+    uint32_t vals[TILE];
+  };
+  __shared__ Exchange ex;
+  __shared__ uint32_t s_start[kRadix];          // tile-local start of each digit's run
+  __shared__ unsigned long long s_gbase[kRadix];  // global position of local position 0 per digit
+  __shared__ uint32_t s_warp_tot[kSortWarps];
+  __shared__ uint32_t s_tile;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+  for (int i = lane; i < kRadix; i += 32) ex.wh.h[warp][i] = 0;
+  __syncthreads();
+  const uint64_t tile = s_tile;
+  const uint64_t tile_base = tile * TILE;
+  const uint32_t valid = (uint32_t)((n - tile_base) < (uint64_t)TILE ? (n - tile_base) : TILE);
+
+  // Warp-striped ownership: item i of lane l in warp w is tile element
+  // w*32*ITEMS + i*32 + l, so tile order is (warp, item, lane).
+  K key[ITEMS];
+  uint32_t dig[ITEMS];
+  uint32_t rnk[ITEMS];
+  const uint64_t wbase = tile_base + (uint64_t)warp * 32 * ITEMS + lane;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint64_t idx = wbase + (uint64_t)i * 32;
+    key[i] = idx < n ? src_k[idx] : ~K(0);  // padding sorts last (digit 255, after real keys)
+    dig[i] = (uint32_t)(key[i] >> shift) & 0xFF;
+  }
+  const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t d = dig[i];
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      const uint32_t bit = (d >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bal : ~bal;
+    }
+    const uint32_t before = __popc(peers & lt_mask);
+    const uint32_t leader = 31 - __clz(peers);
+    const uint32_t base = ex.wh.h[warp][d];
+    __syncwarp();
+    if (lane == leader) ex.wh.h[warp][d] = base + __popc(peers);
+    __syncwarp();
+    rnk[i] = base + before;
+  }
+  __syncthreads();
+
+  // Thread d owns digit d: exclusive prefix over warps, tile count.
+  const uint32_t d = tid;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) {
+    const uint32_t c = ex.wh.h[w][d];
+    ex.wh.h[w][d] = cnt;
+    cnt += c;
+  }
+  const uint32_t cnt_valid = (d == kRadix - 1) ? cnt - (TILE - valid) : cnt;
+  uint64_t* my_status = status + tile * kRadix + d;
+  const uint64_t ep = (uint64_t)epoch << 40;
+  st_volatile_u64(my_status, (tile == 0 ? kStatInclusive : kStatAggregate) | ep | cnt_valid);
+
+  // Block-wide exclusive scan of the per-digit tile counts -> run starts.
+  uint32_t x = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp_tot[warp] = x;
+  __syncthreads();
+  uint32_t wpre = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) wpre += (w < warp) ? s_warp_tot[w] : 0u;
+  const uint32_t start = wpre + x - cnt;
+  s_start[d] = start;
+
+  // Decoupled look-back over earlier tiles for digit d (bounded wait).
+  uint64_t excl = 0;
+  if (tile > 0) {
+    int64_t j = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+      const uint64_t s = ld_volatile_u64(status + (uint64_t)j * kRadix + d);
+      const bool ready = ((s >> 40) & 0x3FFFFF) == epoch && (s >> 62) != 0;
+      if (ready) {
+        excl += s & kValueMask;
+        if ((s >> 62) == 2) break;
+        --j;
+      } else {
+        if (++spins > kSpinLimit) {
+          atomicOr(flags, kFlagTimeout);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    st_volatile_u64(my_status, kStatInclusive | ep | (excl + cnt_valid));
+  }
+  s_gbase[d] = digit_off[d] + excl - start;
+  __syncthreads();
+
+  uint32_t pos[ITEMS];
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) pos[i] = s_start[dig[i]] + ex.wh.h[warp][dig[i]] + rnk[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) ex.keys[pos[i]] = key[i];
+  __syncthreads();
+
+  // Consecutive threads take consecutive local positions: each digit run is
+  // written to consecutive global addresses.
+  uint64_t dst[ITEMS];
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    const uint32_t j = tid + r * kSortThreads;
+    const K kk = ex.keys[j];
+    dst[r] = s_gbase[(uint32_t)(kk >> shift) & 0xFF] + j;
+    if (j < valid && dst[r] < n) dst_k[dst[r]] = kk;  // the bound only guards a failed wait
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint64_t idx = wbase + (uint64_t)i * 32;
+    ex.vals[pos[i]] = idx < n ? src_v[idx] : 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    const uint32_t j = tid + r * kSortThreads;
+    if (j < valid && dst[r] < n) dst_v[dst[r]] = ex.vals[j];
+  }
+}
+
+// ---------------------------------------------------------------- layout permutation
+// Slot t <- sorted[p'(t)] (Sections 4, 6.1).  key_off = 1 for Eytzinger order,
+// whose slot 0 is the empty slot.  Also flags equal neighbours in sorted order.
+template <class K, int KF>
+__global__ void __launch_bounds__(256) k_layout_gather(const K* __restrict__ sk,
+                                                       const uint32_t* __restrict__ sv,
+                                                       K* __restrict__ dk, uint32_t* __restrict__ dv,
+                                                       Geom g, uint32_t key_off,
+                                                       uint32_t* __restrict__ flags) {
+  bool dup = false;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < g.n; t += stride) {
+    const uint64_t r = slot_to_rank<KF>(t, g);
+    const K key = sk[r];
+    dk[t + key_off] = key;
+    dv[t] = sv[r];
+    if (r > 0) dup |= sk[r - 1] == key;
+  }
+  if (key_off && blockIdx.x == 0 && threadIdx.x == 0) dk[0] = K(0);
+  if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagDuplicate);
+}
+
+template <class K>
+__global__ void __launch_bounds__(256) k_sorted_dups(const K* __restrict__ sk, uint64_t n,
+                                                     uint32_t* __restrict__ flags) {
+  bool dup = false;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n; i += stride)
+    dup |= sk[i - 1] == sk[i];
+  if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagDuplicate);
+}
+
+inline int grid_for(uint64_t work, int block, int per_sm = 8) {
+  const uint64_t want = (work + block - 1) / block;
+  const uint64_t cap = (uint64_t)sm_count() * per_sm;
+  return (int)(want < cap ? (want ? want : 1) : cap);
+}
+
+}  // namespace
+
+size_t sort_scratch_bytes(uint64_t n, int key_bytes) {
+  return header_bytes(key_bytes) + align256(sizeof(uint64_t) * kRadix * (tiles_for(n, key_bytes) + 1));
+}
+
+cudaError_t sort_prepare(const void* keys, const uint32_t* vals, uint64_t n, int key_bytes,
+                         void* scratch, uint32_t* dflags, cudaStream_t s,
+                         uint32_t* host_trivial_mask) {
+  ScratchView v = view(scratch, key_bytes);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, key_bytes), s);
+  if (e != cudaSuccess) return e;
+  const int grid = grid_for(n, 256, 4);
+  if (key_bytes == 4)
+    k_histogram<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)keys, vals, n, v.hist, dflags);
+  else
+    k_histogram<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)keys, vals, n, v.hist, dflags);
+  k_scan_hist<<<key_bytes, 256, 0, s>>>(v.hist, v.offs, v.trivial, n);
+  count_launch(2);
+  uint32_t triv[8] = {0};
+  e = cudaMemcpyAsync(triv, v.trivial, sizeof(uint32_t) * key_bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  uint32_t mask = 0;
+  for (int p = 0; p < key_bytes; ++p)
+    if (triv[p]) mask |= 1u << p;
+  *host_trivial_mask = mask;
+  return cudaGetLastError();
+}
+
+cudaError_t sort_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
+                      uint64_t n, int key_bytes, int pass, void* scratch, uint32_t* dflags,
+                      cudaStream_t s) {
+  ScratchView v = view(scratch, key_bytes);
+  const uint64_t tiles = tiles_for(n, key_bytes);
+  if (tiles == 0) return cudaSuccess;
+  if (tiles > 0x7fffffffull) return cudaErrorInvalidValue;
+  // every pass reuses the status array; the epoch (pass + 1) tells its words apart
+  if (key_bytes == 4)
+    k_sort_pass<uint32_t><<<(unsigned)tiles, kSortThreads, 0, s>>>(
+        (const uint32_t*)src_k, src_v, (uint32_t*)dst_k, dst_v, n, 8u * pass,
+        v.offs + pass * kRadix, v.status, v.counter + pass, (uint32_t)pass + 1, dflags);
+  else
+    k_sort_pass<uint64_t><<<(unsigned)tiles, kSortThreads, 0, s>>>(
+        (const uint64_t*)src_k, src_v, (uint64_t*)dst_k, dst_v, n, 8u * pass,
+        v.offs + pass * kRadix, v.status, v.counter + pass, (uint32_t)pass + 1, dflags);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <class K>
+static void launch_gather(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
+                          const Geom& g, uint32_t key_off, uint32_t* dflags, cudaStream_t s) {
+  const int grid = grid_for(g.n, 256, 16);
+  const K* a = (const K*)sk;
+  K* b = (K*)dk;
+  switch (g.k) {
+    case 2: k_layout_gather<K, 2><<<grid, 256, 0, s>>>(a, sv, b, dv, g, key_off, dflags); break;
+    case 3: k_layout_gather<K, 3><<<grid, 256, 0, s>>>(a, sv, b, dv, g, key_off, dflags); break;
+    case 4: k_layout_gather<K, 4><<<grid, 256, 0, s>>>(a, sv, b, dv, g, key_off, dflags); break;
+    case 5: k_layout_gather<K, 5><<<grid, 256, 0, s>>>(a, sv, b, dv, g, key_off, dflags); break;
+    case 8: k_layout_gather<K, 8><<<grid, 256, 0, s>>>(a, sv, b, dv, g, key_off, dflags); break;
+    case 9: k_layout_gather<K, 9><<<grid, 256, 0, s>>>(a, sv, b, dv, g, key_off, dflags); break;
+    case 16: k_layout_gather<K, 16><<<grid, 256, 0, s>>>(a, sv, b, dv, g, key_off, dflags); break;
+    case 17: k_layout_gather<K, 17><<<grid, 256, 0, s>>>(a, sv, b, dv, g, key_off, dflags); break;
+    case 32: k_layout_gather<K, 32><<<grid, 256, 0, s>>>(a, sv, b, dv, g, key_off, dflags); break;
+    case 33: k_layout_gather<K, 33><<<grid, 256, 0, s>>>(a, sv, b, dv, g, key_off, dflags); break;
+    default: k_layout_gather<K, 0><<<grid, 256, 0, s>>>(a, sv, b, dv, g, key_off, dflags); break;
+  }
+  count_launch();
+}
+
+cudaError_t layout_gather(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
+                          const Geom& g, int key_bytes, uint32_t key_off, uint32_t* dflags,
+                          cudaStream_t s) {
+  if (g.n == 0) return cudaSuccess;
+  if (key_bytes == 4)
+    launch_gather<uint32_t>(sk, sv, dk, dv, g, key_off, dflags, s);
+  else
+    launch_gather<uint64_t>(sk, sv, dk, dv, g, key_off, dflags, s);
+  return cudaGetLastError();
+}
+
+cudaError_t check_sorted_dups(const void* sk, uint64_t n, int key_bytes, uint32_t* dflags,
+                              cudaStream_t s) {
+  if (n < 2) return cudaSuccess;
+  const int grid = grid_for(n, 256, 8);
+  if (key_bytes == 4)
+    k_sorted_dups<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)sk, n, dflags);
+  else
+    k_sorted_dups<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)sk, n, dflags);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace gi

@@ -1,0 +1,256 @@
+"""GPU path vs CPU oracle, element by element, through the C ABI.
+
+Every output is integer: results must be bit-identical (rowIDs, CSR offsets,
+CSR rows and their order), and the built layout must equal the oracle's
+in-order fill slot by slot.  Sizes span several radix tiles (4096 u32 / 3072 u64
+keys per tile) with ragged tails, every fan-out the library compiles plus two it
+does not (generic kernel), unique and duplicate-heavy key sets, and the edge
+cases: empty index, one key, probes at 0 and at the key maximum, empty and
+inverted ranges, ranges covering everything.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2506_01576_gb300 as gi
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+from gpu_util import DEV, build, layout_arrays, point, ranges, to_dev  # noqa: E402
+
+LAYOUTS = [(gi.GI_SORTED, 0), (gi.GI_EYTZINGER, 2)] + [
+    (gi.GI_EYTZINGER_KARY, k) for k in (3, 4, 5, 8, 9, 16, 17, 32, 33, 2, 6)]
+SIZES = [0, 1, 2, 3, 7, 31, 100, 1000, 3071, 3072, 4097, 12289, 50000]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2506_01576_gb300 import _build
+    _build.build()
+    gi.load()
+    torch.cuda.set_device(DEV)
+
+
+def _oracle_layout(keys, rows, layout, k):
+    return oracle.layout_arrays(keys, rows, {gi.GI_SORTED: oracle.SORTED, gi.GI_EYTZINGER: oracle.EYTZINGER,
+                                             gi.GI_EYTZINGER_KARY: oracle.EYTZINGER_KARY}[layout], k)
+
+
+def _probe_set(keys, dtype, rng):
+    top = np.iinfo(dtype).max
+    extra = np.array([0, 1, top, top - 1], dtype=dtype)
+    rnd = rng.integers(0, top, size=2000, dtype=dtype, endpoint=True)
+    near = (keys[: 500] + dtype(1)) if len(keys) else np.zeros(0, dtype)
+    return np.concatenate([keys, extra, rnd, near]).astype(dtype)
+
+
+def _range_set(keys, dtype, rng):
+    top = np.iinfo(dtype).max
+    sk = np.sort(keys)
+    m = 600
+    a = rng.integers(0, top, size=m, dtype=dtype, endpoint=True)
+    w = rng.integers(0, 2 ** (8 * np.dtype(dtype).itemsize - 6), size=m, dtype=dtype)
+    with np.errstate(over="ignore"):
+        b = a + w  # wraps on overflow
+    b = np.where(b < a, top, b).astype(dtype)
+    lo = [a]
+    hi = [b]
+    if len(sk):
+        i = rng.integers(0, len(sk), size=200)
+        j = np.minimum(i + rng.integers(0, 40, size=200), len(sk) - 1)
+        lo.append(sk[i]); hi.append(sk[j])               # exact key bounds
+        lo.append(sk[j]); hi.append(sk[i])               # inverted (empty unless equal)
+    lo.append(np.array([0, top, 0, 5, top], dtype=dtype))
+    hi.append(np.array([top, top, 0, 4, 0], dtype=dtype))  # everything, max only, min only, empty, inverted
+    return np.concatenate(lo).astype(dtype), np.concatenate(hi).astype(dtype)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+@pytest.mark.parametrize("layout,k", LAYOUTS)
+def test_unique_keys_all_sizes(dtype, layout, k):
+    bits = 8 * np.dtype(dtype).itemsize
+    rng = np.random.default_rng(1234 + k)
+    for n in SIZES:
+        keys = W.unique_keys(n, bits, W.seed_for(7, n % 64, k))
+        rows = rng.permutation(n).astype(np.uint32)
+        idx = build(keys, rows, layout, k)
+        inf = gi.gi_get_info(idx)
+        assert inf.n == n and inf.unique == 1
+        assert gi.gi_footprint_bytes(idx) == n * (np.dtype(dtype).itemsize + 4) + (
+            np.dtype(dtype).itemsize if layout == gi.GI_EYTZINGER else 0)
+        lk, lr = layout_arrays(idx, n, dtype)
+        ok, orr = _oracle_layout(keys, rows, layout, k)
+        assert np.array_equal(lk, ok) and np.array_equal(lr, orr), ("layout", n)
+        sk, sr = oracle.sort_pairs(keys, rows)
+        q = _probe_set(keys, dtype, rng)
+        assert np.array_equal(point(idx, q), oracle.point_lookup(sk, sr, q)), ("point", n)
+        lo, hi = _range_set(keys, dtype, rng)
+        off, rr = ranges(idx, lo, hi)
+        woff, wrr = oracle.range_lookup(sk, sr, lo, hi)
+        assert np.array_equal(off, woff), ("offsets", n)
+        assert np.array_equal(rr, wrr), ("rows", n)
+        gi.gi_destroy(idx)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+@pytest.mark.parametrize("layout,k", [(gi.GI_SORTED, 0), (gi.GI_EYTZINGER, 2),
+                                      (gi.GI_EYTZINGER_KARY, 3), (gi.GI_EYTZINGER_KARY, 9),
+                                      (gi.GI_EYTZINGER_KARY, 16), (gi.GI_EYTZINGER_KARY, 33),
+                                      (gi.GI_EYTZINGER_KARY, 7)])
+def test_duplicate_keys(dtype, layout, k):
+    # duplicates: first entry in input order wins a point lookup; ranges list all of
+    # them in (key, input position) order (Section 8.11)
+    rng = np.random.default_rng(99)
+    top = np.iinfo(dtype).max
+    for n, alphabet in [(50, 3), (1000, 37), (9000, 500), (20000, 20000)]:
+        vals = np.unique(rng.integers(0, top, size=alphabet, dtype=dtype, endpoint=True))
+        vals[0] = 0
+        keys = vals[rng.integers(0, len(vals), size=n)]
+        rows = rng.permutation(n).astype(np.uint32)
+        idx = build(keys, rows, layout, k)
+        assert gi.gi_get_info(idx).unique == (1 if len(np.unique(keys)) == n else 0)
+        lk, lr = layout_arrays(idx, n, dtype)
+        ok, orr = _oracle_layout(keys, rows, layout, k)
+        assert np.array_equal(lk, ok) and np.array_equal(lr, orr)
+        sk, sr = oracle.sort_pairs(keys, rows)
+        q = np.concatenate([vals, _probe_set(keys[:100], dtype, rng)]).astype(dtype)
+        assert np.array_equal(point(idx, q), oracle.point_lookup(sk, sr, q))
+        lo, hi = _range_set(keys, dtype, rng)
+        lo = np.concatenate([lo, vals[:50]]).astype(dtype)
+        hi = np.concatenate([hi, vals[:50]]).astype(dtype)
+        off, rr = ranges(idx, lo, hi)
+        woff, wrr = oracle.range_lookup(sk, sr, lo, hi)
+        assert np.array_equal(off, woff) and np.array_equal(rr, wrr)
+        gi.gi_destroy(idx)
+
+
+def test_all_equal_keys_skip_every_radix_pass():
+    # every digit trivial: no radix pass runs, the input order is the sorted order
+    for dtype in (np.uint32, np.uint64):
+        keys = np.full(5000, 12345, dtype=dtype)
+        rows = np.arange(5000, dtype=np.uint32)[::-1].copy()
+        for layout, k in [(gi.GI_SORTED, 0), (gi.GI_EYTZINGER, 2), (gi.GI_EYTZINGER_KARY, 9)]:
+            idx = build(keys, rows, layout, k)
+            lk, lr = layout_arrays(idx, 5000, dtype)
+            ok, orr = _oracle_layout(keys, rows, layout, k)
+            assert np.array_equal(lk, ok) and np.array_equal(lr, orr)
+            assert point(idx, np.array([12345, 1], dtype=dtype)).tolist() == [4999, gi.GI_MISS]
+            gi.gi_destroy(idx)
+
+
+@pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER, 2), (gi.GI_EYTZINGER_KARY, 9),
+                                      (gi.GI_EYTZINGER_KARY, 17), (gi.GI_EYTZINGER_KARY, 5)])
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_every_knob_gives_identical_results(layout, k, dtype):
+    # group size, interleaving, shared-memory pinning, block size, persistent grid,
+    # prefetch and early exit change the schedule, never the answer (Sections 6.2, 7)
+    bits = 8 * np.dtype(dtype).itemsize
+    n = 70001
+    keys = W.unique_keys(n, bits, 5)
+    rows = np.arange(n, dtype=np.uint32)
+    q = W.point_probes(keys, 100000, 0.5, bits, 5, 6)
+    sk, sr = oracle.sort_pairs(keys, rows)
+    want = oracle.point_lookup(sk, sr, q)
+    idx = build(keys, rows, layout, k)
+    groups = [g for g in (1, 2, 4, 8, 16, 32) if layout == gi.GI_EYTZINGER_KARY
+              and _supported(idx, g)] or [None]
+    configs = []
+    for g in groups:
+        for pt in (1, 2, 4):
+            configs.append(dict(group=g, pt=pt, smem=0, block=256, bpsm=0, pf=0, ee=1))
+    configs += [dict(group=groups[-1], pt=2, smem=3, block=256, bpsm=2, pf=0, ee=1),
+                dict(group=groups[0], pt=1, smem=4, block=512, bpsm=1, pf=0, ee=0),
+                dict(group=groups[-1], pt=4, smem=2, block=128, bpsm=0, pf=0, ee=1),
+                dict(group=groups[0], pt=2, smem=0, block=64, bpsm=4, pf=0, ee=0)]
+    if layout == gi.GI_EYTZINGER:
+        configs += [dict(group=None, pt=p, smem=s, block=256, bpsm=b, pf=f, ee=1)
+                    for f in (2, 3, 4) for p in (1, 4) for (s, b) in ((0, 0), (8, 2))]
+    for c in configs:
+        if c["group"] is not None:
+            gi.gi_set_option(idx, gi.GI_OPT_GROUP, c["group"])
+        gi.gi_set_option(idx, gi.GI_OPT_PER_THREAD, c["pt"])
+        try:
+            gi.gi_set_option(idx, gi.GI_OPT_SMEM_LEVELS, c["smem"])
+        except gi.GIError:  # that many levels do not fit in shared memory
+            gi.gi_set_option(idx, gi.GI_OPT_SMEM_LEVELS, 2)
+        gi.gi_set_option(idx, gi.GI_OPT_BLOCK, c["block"])
+        gi.gi_set_option(idx, gi.GI_OPT_BLOCKS_PER_SM, c["bpsm"])
+        gi.gi_set_option(idx, gi.GI_OPT_PREFETCH, c["pf"])
+        gi.gi_set_option(idx, gi.GI_OPT_EARLY_EXIT, c["ee"])
+        assert np.array_equal(point(idx, q), want), c
+    gi.gi_sync(idx)
+    gi.gi_destroy(idx)
+
+
+def _supported(idx, g):
+    try:
+        gi.gi_set_option(idx, gi.GI_OPT_GROUP, g)
+        return True
+    except gi.GIError:
+        return False
+
+
+def test_host_buffers_equal_device_buffers():
+    # the staged host-memory path (pinned and pageable) returns what the device path does
+    n, m = 200003, 3 * (1 << 22) + 77  # several staging chunks with a ragged tail
+    keys = W.unique_keys(n, 64, 11)
+    rows = np.arange(n, dtype=np.uint32)
+    q = W.point_probes(keys, m, 0.5, 64, 11, 12)
+    sk, sr = oracle.sort_pairs(keys, rows)
+    want = oracle.point_lookup(sk, sr, q, threads=oracle.hardware_threads())
+    idx = gi.gi_build(keys, rows, gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 9)  # host inputs
+    out = np.empty(m, dtype=np.uint32)
+    gi.gi_point_lookup(idx, q, out)  # pageable host memory
+    assert np.array_equal(out, want)
+    qp = torch.from_numpy(q.view(np.int64)).pin_memory()
+    op = torch.empty(m, dtype=torch.int32).pin_memory()
+    gi.gi_point_lookup(idx, qp, op)
+    assert np.array_equal(op.numpy().view(np.uint32), want)
+    lo = q[:5000]
+    hi = lo + np.uint64(1 << 48)
+    woff, wrr = oracle.range_lookup(sk, sr, lo, hi)
+    off = np.empty(len(lo) + 1, dtype=np.uint64)
+    gi.gi_range_lookup(idx, lo, hi, off)
+    rr = np.empty(int(off[-1]), dtype=np.uint32)
+    gi.gi_range_lookup(idx, lo, hi, off, rr)
+    assert np.array_equal(off, woff) and np.array_equal(rr, wrr)
+    gi.gi_destroy(idx)
+
+
+def test_reserved_rowid_rejected_and_streams():
+    keys = np.arange(100, dtype=np.uint32)
+    rows = np.arange(100, dtype=np.uint32)
+    rows[57] = gi.GI_MISS
+    with pytest.raises(gi.GIError) as e:
+        build(keys, rows, gi.GI_EYTZINGER)
+    assert e.value.code == gi.GI_ERR_INVALID
+    # a built index follows the thread's default stream and can be moved to another
+    s = torch.cuda.Stream()
+    gi.gi_set_stream(None, s)
+    try:
+        rows[57] = 57
+        idx = build(keys, rows, gi.GI_EYTZINGER_KARY, 9)
+        with torch.cuda.stream(s):
+            out = torch.empty(100, dtype=torch.int32, device=DEV)
+            gi.gi_point_lookup(idx, to_dev(keys), out)
+        s.synchronize()
+        assert out.cpu().numpy().tolist() == list(range(100))
+        gi.gi_set_stream(idx, None)
+        assert point(idx, keys).tolist() == list(range(100))
+        gi.gi_destroy(idx)
+    finally:
+        gi.gi_set_stream(None, None)
+
+
+def test_probes_roofline_kernels_run():
+    buf = torch.zeros(1 << 24, dtype=torch.int32, device=DEV)
+    sink = torch.zeros(1, dtype=torch.int64, device=DEV)
+    for c in (16, 32, 64, 128, 256):
+        gi.gi_probe_random_sectors(buf, c, 1 << 20, 7, sink)
+    for g in (1, 2, 16, 32, 64):
+        gi.gi_coalescing_probe(buf, 1 << 16, g, 64, 3, sink)
+    torch.cuda.synchronize()
+    with pytest.raises(gi.GIError):
+        gi.gi_probe_random_sectors(buf, 48, 10, 1, sink)

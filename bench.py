@@ -1,0 +1,470 @@
+"""Benchmark: point lookups/s on a static index of 2^26 uint64 keys (EKS vs BS).
+
+One step is one pass of the whole hot path over one batch of synthetic input:
+  build    gi_build of 2^26 unique uint64 keys (uniform in [0, 2^63), rowIDs
+           0..n-1): radix sort + k-ary Eytzinger permutation;
+  point    gi_point_lookup of 2^27 uint64 probes, hit rate 0.5, uniform;
+  range    gi_range_lookup of 2^22 inclusive ranges with 16 expected rows each
+           (count + scan + fill into CSR).
+value = point lookups in the step / step time (device clock, CUDA events, max
+over ranks).  Inputs (0.5 GiB keys, 1 GiB probes) are larger than L2, so no
+extra flush is needed between steps.
+
+Extra fields: lookup-only throughput of EKS and of textbook BS on the same
+index keys (the "EKS vs BS" of the metric), the roofline of the lookup kernel
+against the measured HBM copy bandwidth and against a random-access probe run
+in the same process, an end-to-end number through the C ABI with host buffers,
+and the CPU oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "point lookups/s @2^26 u64 keys, EKS vs textbook BS; % of HBM sector roofline"
+UNIT = "lookups/s"
+
+
+# ---------------------------------------------------------------- helpers
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-log", type=int, default=26)
+    ap.add_argument("--m-log", type=int, default=27)
+    ap.add_argument("--ranges-log", type=int, default=22)
+    ap.add_argument("--range-rows", type=float, default=16.0)
+    ap.add_argument("--k", type=int, default=5, help="EKS fan-out")
+    ap.add_argument("--group", type=int, default=-1)
+    ap.add_argument("--per-thread", type=int, default=-1)
+    ap.add_argument("--smem-levels", type=int, default=-1)
+    ap.add_argument("--blocks-per-sm", type=int, default=-1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def kary_level_sizes(n: int, k: int):
+    """Keys per level of the complete k-ary tree of n keys (last level partial)."""
+    if n == 0:
+        return []
+    m, p = 0, 1
+    while p <= n // k:
+        p *= k
+        m += 1
+    sizes = [(k - 1) * k ** l for l in range(m)]
+    sizes.append(n - (p - 1))
+    return sizes
+
+
+def eks_bytes_per_lookup(n: int, k: int, key_bytes: int, hit_rate: float, l2_bytes: int):
+    """Algorithmic DRAM bytes of one k-ary lookup, and the random requests by size.
+
+    Levels whose cumulative key bytes fit in L2 are counted as resident.  Every
+    lookup visits all full levels; it reaches the partial bottom level iff its
+    gap borders a bottom key: (b + bottom nodes) of the n + 1 gaps.  Each visited
+    level reads one node (k-1 keys, rounded up to 32-byte sectors).  A hit reads
+    one rowID sector.  Probe and result stream once (key + 4 bytes).
+    """
+    sizes = kary_level_sizes(n, k)
+    node = math.ceil((k - 1) * key_bytes / 32) * 32
+    cum, reqs = 0, {}
+    for l, sz in enumerate(sizes):
+        cum += sz * key_bytes
+        if cum <= l2_bytes:
+            continue
+        if l < len(sizes) - 1:
+            p = 1.0
+        else:
+            b = sz
+            p = (b + math.ceil(b / (k - 1))) / (n + 1)
+        reqs[node] = reqs.get(node, 0.0) + p
+    reqs[32] = reqs.get(32, 0.0) + hit_rate
+    nbytes = sum(sz * c for sz, c in reqs.items()) + key_bytes + 4
+    return nbytes, reqs
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2506_01576_gb300 as gi
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    gi.load()
+    n, m, mr = 1 << a.n_log, 1 << a.m_log, 1 << a.ranges_log
+    seed = W.seed_for(1, a.n_log, rank)
+    keys = W.unique_keys(n, 64, seed)
+    rows = np.arange(n, dtype=np.uint32)
+    q = W.point_probes(keys, m, 0.5, 64, seed, seed + 1)
+    lo, hi, w = W.ranges_with_expected_rows(n, mr, a.range_rows, 64, seed + 2)
+    dv = lambda x: torch.from_numpy(x.view(np.int64) if x.dtype == np.uint64 else x.view(np.int32)).to(dev)
+    kd, rd, qd, lod, hid = dv(keys), dv(rows), dv(q), dv(lo), dv(hi)
+    out = torch.empty(m, dtype=torch.int32, device=dev)
+    off = torch.empty(mr + 1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    gi.gi_set_stream(None, stream)
+    layout = gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64
+
+    def configure(idx):
+        for opt, v in ((gi.GI_OPT_GROUP, a.group), (gi.GI_OPT_PER_THREAD, a.per_thread),
+                       (gi.GI_OPT_SMEM_LEVELS, a.smem_levels),
+                       (gi.GI_OPT_BLOCKS_PER_SM, a.blocks_per_sm)):
+            gi.gi_set_option(idx, opt, v)
+
+    # size the range output once (the same ranges every step)
+    idx = gi.gi_build(kd, rd, layout, a.k)
+    gi.gi_range_lookup(idx, lod, hid, off)
+    total_rows = int(off[-1].item())
+    rout = torch.empty(max(total_rows, 1), dtype=torch.int32, device=dev)
+    gi.gi_destroy(idx)
+
+    ev_pt = []
+
+    def step(timed):
+        idx = gi.gi_build(kd, rd, layout, a.k)
+        configure(idx)
+        if timed:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        gi.gi_point_lookup(idx, qd, out)
+        if timed:
+            e1.record(stream)
+            ev_pt.append((e0, e1))
+        gi.gi_range_lookup(idx, lod, hid, off, rout)  # single call: count + scan + fill
+        gi.gi_destroy(idx)  # waits for the stream
+
+    for _ in range(a.warmup):
+        step(False)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = gi.gi_launch_count()
+    with ClockSampler(local) as clk:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(a.steps):
+            step(True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    launches = gi.gi_launch_count() - l0
+    if world > 1:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_step = ms / a.steps
+    value = m * world * a.steps / (ms / 1e3)
+    pt_ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev_pt]))
+
+    # parity spot check of the timed configuration (results are integers: exact)
+    res = {}
+    if rank == 0:
+        res = extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, layout,
+                     total_rows)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "build 2^%d unique u64 keys (EKS k=%d) + 2^%d point probes (hit 0.5, "
+                               "uniform) + 2^%d ranges (%.0f expected rows) per step"
+                               % (a.n_log, a.k, a.m_log, a.ranges_log, a.range_rows),
+                   "n_keys": n, "point_probes": m, "ranges": mr, "range_rows_total": total_rows,
+                   "layout": "EKS", "k": a.k, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": clk.summary(), "gpu_launches": int(launches),
+    }
+    line.update(res)
+    print(json.dumps(line), flush=True)
+
+
+def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, layout, total_rows):
+    """Lookup-only rates, roofline, e2e through host buffers, CPU oracle."""
+    import oracle
+    stream = torch.cuda.current_stream()
+
+    def ev_time(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    res = {}
+    # ---- lookup-only: EKS (timed configuration), textbook BS, EBS
+    idx = gi.gi_build(kd, rd, layout, a.k)
+    configure(idx)
+    eks_ms = ev_time(lambda: gi.gi_point_lookup(idx, qd, out))
+    opts = {name: gi.gi_get_option(idx, o) for name, o in
+            (("group", gi.GI_OPT_GROUP), ("per_thread", gi.GI_OPT_PER_THREAD),
+             ("smem_levels", gi.GI_OPT_SMEM_LEVELS), ("block", gi.GI_OPT_BLOCK),
+             ("blocks_per_sm", gi.GI_OPT_BLOCKS_PER_SM))}
+    gi.gi_point_lookup(idx, qd, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32)
+    gi.gi_destroy(idx)
+    bs = gi.gi_build(kd, rd, gi.GI_SORTED | gi.GI_KEY_U64, 0)
+    bs_ms = ev_time(lambda: gi.gi_point_lookup(bs, qd, out))
+    gi.gi_destroy(bs)
+    eb = gi.gi_build(kd, rd, gi.GI_EYTZINGER | gi.GI_KEY_U64, 0)
+    gi.gi_set_option(eb, gi.GI_OPT_PER_THREAD, 4)
+    ebs_ms = ev_time(lambda: gi.gi_point_lookup(eb, qd, out))
+    gi.gi_destroy(eb)
+    # sampled parity: probes whose rowID is known without the oracle
+    rng = np.random.default_rng(0)
+    samp = rng.choice(m, size=1 << 16, replace=False)
+    sk_idx = np.argsort(keys, kind="stable")
+    sk = keys[sk_idx]
+    r = np.searchsorted(sk, q[samp])
+    hit = (r < n) & (sk[np.minimum(r, n - 1)] == q[samp])
+    want = np.where(hit, sk_idx[np.minimum(r, n - 1)].astype(np.uint32), np.uint32(0xFFFFFFFF))
+    parity_ok = bool(np.array_equal(got[samp], want))
+    res["lookup_only"] = {
+        "eks_lookups_per_s": m / (eks_ms / 1e3), "eks_ms": eks_ms, "eks_kernel_ms_in_step": pt_ms,
+        "bs_lookups_per_s": m / (bs_ms / 1e3), "bs_ms": bs_ms,
+        "ebs_lookups_per_s": m / (ebs_ms / 1e3), "ebs_ms": ebs_ms,
+        "speedup_eks_vs_bs": bs_ms / eks_ms, "eks_config": opts,
+        "sampled_parity_65536": parity_ok,
+    }
+    # ---- roofline of the dominant kernel (EKS point lookup)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    bpl, reqs = eks_bytes_per_lookup(n, a.k, 8, 0.5, l2)
+    achieved = bpl * m / (pt_ms / 1e3) / 1e9
+    res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                       "frac": achieved / hbm, "traffic": None,
+                       "peak_source": "measured" if peaks else "fallback",
+                       "kernel": "k_eks_point", "algorithmic_bytes_per_lookup": bpl,
+                       "random_requests_per_lookup": reqs, "l2_bytes": l2}
+    if not a.no_probe:
+        buf = torch.empty(16 << 30, dtype=torch.uint8, device=dev)
+        sink = torch.zeros(1, dtype=torch.int64, device=dev)
+        rate = {}
+        for c in sorted(set(list(reqs.keys()) + [32])):
+            loads = 1 << 28
+            t = ev_time(lambda: gi.gi_probe_random_sectors(buf, c, loads, 7, sink, stream), reps=3)
+            rate[c] = loads / (t / 1e3)
+        del buf
+        torch.cuda.empty_cache()
+        t_per = sum(cnt / rate[c] for c, cnt in reqs.items())
+        bound = 1.0 / t_per
+        res["roofline"]["random_access"] = {
+            "probe_chunks_per_s": {str(c): v for c, v in rate.items()},
+            "bound_lookups_per_s": bound, "frac": (m / (pt_ms / 1e3)) / bound,
+            "note": "bound = 1 / sum(requests_of_size_s / measured random-chunk rate at s)"}
+    # ---- e2e through the C ABI with pinned host buffers
+    if not a.no_e2e:
+        nk = len(keys)
+        hk = torch.from_numpy(keys.view(np.int64)).pin_memory()
+        hr = torch.arange(nk, dtype=torch.int32).pin_memory()
+        hq = torch.from_numpy(q.view(np.int64)).pin_memory()
+        ho = torch.empty(m, dtype=torch.int32).pin_memory()
+        mr = 1 << a.ranges_log
+        lo, hi, _ = W.ranges_with_expected_rows(n, mr, a.range_rows, 64, W.seed_for(1, a.n_log, 0) + 2)
+        hlo = torch.from_numpy(lo.view(np.int64)).pin_memory()
+        hhi = torch.from_numpy(hi.view(np.int64)).pin_memory()
+        hoff = torch.empty(mr + 1, dtype=torch.int64).pin_memory()
+        hrows = torch.empty(max(total_rows, 1), dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            idx = gi.gi_build(hk, hr, layout, a.k)
+            configure(idx)
+            gi.gi_point_lookup(idx, hq, ho)
+            gi.gi_range_lookup(idx, hlo, hhi, hoff, hrows)  # count + scan + fill, staged
+            gi.gi_destroy(idx)
+            return int(hoff[-1])
+
+        e2e_step()
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            total = e2e_step()
+        dt = (time.perf_counter() - t0) / reps
+        res["e2e"] = {"value": m / dt, "unit": UNIT,
+                      "h2d_bytes_per_step": nk * 8 + nk * 4 + m * 8 + 2 * mr * 8,
+                      "d2h_bytes_per_step": m * 4 + (mr + 1) * 8 + total * 4,
+                      "ms_per_step": dt * 1e3, "host_buffers": "pinned"}
+    # ---- CPU oracle on the host cores (bounded sample)
+    if not a.no_cpu:
+        res["cpu_baseline"] = cpu_oracle_sample(keys, q, n, m, a)
+    return res
+
+
+def cpu_oracle_sample(keys, q, n, m, a, sort_sample=1 << 22, point_sample=1 << 21):
+    """The oracle as it stands on the host cores: a sample of the step, scaled.
+
+    Sort: std::sort of `sort_sample` pairs (single thread), scaled to n by
+    n log n.  Point lookups: std::lower_bound of `point_sample` probes over the
+    full sorted index on all cores, scaled to m.  Ranges are not timed (the
+    point-lookup metric's step is dominated by the two parts above).
+    """
+    import oracle
+    threads = oracle.hardware_threads()
+    rows = np.arange(n, dtype=np.uint32)
+    t0 = time.perf_counter()
+    oracle.sort_pairs(keys[:sort_sample], rows[:sort_sample])
+    t_sort = time.perf_counter() - t0
+    sk, sr = oracle.sort_pairs(keys, rows)  # full index, untimed
+    qs = q[:point_sample]
+    t0 = time.perf_counter()
+    oracle.point_lookup(sk, sr, qs, threads)
+    t_pt = time.perf_counter() - t0
+    est = t_sort * (n / sort_sample) * (math.log2(n) / math.log2(sort_sample)) + t_pt * (m / point_sample)
+    return {"value": m / est, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "std::sort of 2^%d pairs (1 thread, scaled n log n to 2^%d) + "
+                      "std::lower_bound of 2^%d probes on %d threads (scaled to 2^%d)"
+                      % (int(math.log2(sort_sample)), int(math.log2(n)),
+                         int(math.log2(point_sample)), threads, int(math.log2(m))),
+            "est_step_s": est}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(a):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n, m = 1 << a.n_log, 1 << a.m_log
+    seed = W.seed_for(1, a.n_log, 0)
+    keys = W.unique_keys(n, 64, seed)
+    q = W.point_probes(keys, m, 0.5, 64, seed, seed + 1)
+    rows = np.arange(n, dtype=np.uint32)
+    threads = oracle.hardware_threads()
+    sk, sr = oracle.sort_pairs(keys, rows)
+    sort_sample, point_sample = 1 << 21, 1 << 20
+    rng = np.random.default_rng(1)
+
+    def step():
+        j = int(rng.integers(0, n - sort_sample))
+        t0 = time.perf_counter()
+        oracle.sort_pairs(keys[j:j + sort_sample], rows[j:j + sort_sample])
+        t_sort = time.perf_counter() - t0
+        i = int(rng.integers(0, m - point_sample))
+        t0 = time.perf_counter()
+        oracle.point_lookup(sk, sr, q[i:i + point_sample], threads)
+        t_pt = time.perf_counter() - t0
+        return t_sort * (n / sort_sample) * (math.log2(n) / math.log2(sort_sample)) + t_pt * (m / point_sample)
+
+    for _ in range(a.warmup):
+        step()
+    ests = [step() for _ in range(a.steps)]
+    est = float(np.mean(ests))
+    value = m / est
+    sample = ("per step: std::sort of 2^21 pairs (1 thread, scaled n log n to 2^%d) + "
+              "std::lower_bound of 2^20 probes on %d threads (scaled to 2^%d)" % (a.n_log, threads, a.m_log))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "build 2^%d unique u64 keys + 2^%d point probes (hit 0.5, uniform) "
+                                   "per step, estimated from a timed sample" % (a.n_log, a.m_log),
+                       "n_keys": n, "point_probes": m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

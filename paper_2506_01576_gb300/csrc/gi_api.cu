@@ -139,8 +139,7 @@ gi::LookupCfg resolve_cfg(const gi_index* idx) {
                                          ? gi::eks_default_group(idx->k, idx->key_bytes)
                                          : 1);
   int def_pt = 1;
-  if (idx->layout == GI_EYTZINGER) def_pt = 2;
-  if (idx->layout == GI_EYTZINGER_KARY) def_pt = 2;
+  if (idx->layout == GI_EYTZINGER) def_pt = 4;
   c.per_thread = o[GI_OPT_PER_THREAD] >= 0 ? (int)o[GI_OPT_PER_THREAD] : def_pt;
   c.smem_levels = o[GI_OPT_SMEM_LEVELS] >= 0 ? (int)o[GI_OPT_SMEM_LEVELS] : 0;
   c.block = o[GI_OPT_BLOCK] >= 0 ? (int)o[GI_OPT_BLOCK] : 256;
@@ -248,23 +247,27 @@ size_t range_scratch_bytes(uint64_t m) {
   return round256(sizeof(uint64_t) * (m ? m : 1)) + round256(sizeof(uint64_t) * (nb + 1));
 }
 
-bool eks_group_supported(uint32_t k, int group) {
-  static const int pairs[][2] = {{3, 1},  {3, 2},  {4, 1},  {4, 4},  {5, 1},  {5, 2},  {5, 4},
-                                 {8, 1},  {8, 8},  {9, 1},  {9, 2},  {9, 4},  {9, 8},  {16, 1},
-                                 {16, 8}, {16, 16}, {17, 1}, {17, 4}, {17, 8}, {17, 16}, {32, 1},
-                                 {32, 16}, {32, 32}, {33, 1}, {33, 8}, {33, 16}, {33, 32}};
-  for (auto& p : pairs)
-    if ((uint32_t)p[0] == k && p[1] == group) return true;
+bool eks_group_supported(uint32_t k, int key_bytes, int group) {
+#define GI_X(KF, G) \
+  if (k == KF && group == G) return true;
+  if (key_bytes == 8) {
+    GI_EKS_PAIRS_U64(GI_X)
+  } else {
+    GI_EKS_PAIRS_U32(GI_X)
+  }
+#undef GI_X
   return false;
 }
 
 int eks_default_group(uint32_t k, int key_bytes) {
-  // one 16-byte vector per lane where the node splits that way, else one key per lane
+  // One thread per lookup reading its whole node with vector loads measured
+  // fastest beyond L2 (fewest instructions per level); nodes wider than 64
+  // bytes are split over lanes in 16-byte pieces.
   const int node_bytes = (int)(k - 1) * key_bytes;
-  if (node_bytes % 16 == 0 && eks_group_supported(k, node_bytes / 16)) return node_bytes / 16;
+  if (node_bytes <= 64 && eks_group_supported(k, key_bytes, 1)) return 1;
+  if (node_bytes % 16 == 0 && eks_group_supported(k, key_bytes, node_bytes / 16)) return node_bytes / 16;
   for (int g = 32; g >= 1; g >>= 1)
-    if (eks_group_supported(k, g) && g <= (int)(k - 1)) return g;
-  if (eks_group_supported(k, 1)) return 1;
+    if (eks_group_supported(k, key_bytes, g)) return g;
   return 1;  // generic kernel
 }
 
@@ -370,7 +373,7 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   if (n == 0) {
     GI_TRY(dalloc(&idx->keys, kbytes, s), "index keys");
     GI_TRY(dalloc((void**)&idx->rows, rbytes, s), "index rows");
-    GI_TRY(cudaMemsetAsync(idx->keys, 0, kbytes, s), "index keys");
+    GI_TRY(cudaMemsetAsync(idx->keys, 0xFF, kbytes, s), "index keys");
     GI_TRY(cudaStreamSynchronize(s), "gi_build");
     *out = idx;
     return GI_OK;
@@ -447,6 +450,11 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
             "layout permutation");
     idx->keys = bk[dst];
     idx->rows = bv[dst];
+  }
+  {
+    // slots past the last key hold the maximum key: whole-node reads need no bounds checks
+    const size_t used = (n + (lay == GI_EYTZINGER ? 1 : 0)) * kb;
+    GI_TRY2(cudaMemsetAsync((char*)idx->keys + used, 0xFF, kbytes - used, s), "key padding");
   }
   free_tmp();
   rc = read_flags(idx);
@@ -666,7 +674,7 @@ int gi_set_option(gi_index* idx, int option, int64_t v) {
   }
   switch (option) {
     case GI_OPT_GROUP:
-      if (idx->layout != GI_EYTZINGER_KARY || !gi::eks_group_supported(idx->k, (int)v))
+      if (idx->layout != GI_EYTZINGER_KARY || !gi::eks_group_supported(idx->k, idx->key_bytes, (int)v))
         return fail(GI_ERR_INVALID, "gi_set_option: group %lld not available for this index", (long long)v);
       break;
     case GI_OPT_PER_THREAD:

@@ -156,8 +156,30 @@ cudaError_t point_lookup_u32(const void* keys, const uint32_t* rows, const Geom&
 cudaError_t point_lookup_u64(const void* keys, const uint32_t* rows, const Geom& g,
                              const LookupCfg& c, const void* q, uint64_t m, uint32_t* out,
                              uint32_t* dflags, cudaStream_t s);
-// (k, group) pairs the lane-group kernel is compiled for
-bool eks_group_supported(uint32_t k, int group);
+// (k, lanes per lookup) pairs the k-ary lookup kernel is compiled for, per key
+// width.  Lanes hold 8/16/32-byte vectors of a node where it splits evenly;
+// otherwise one key per lane (or the whole node in one lane, G = 1).
+#define GI_EKS_PAIRS_U64(X)                         \
+  X(3, 1) X(3, 2)                                   \
+  X(4, 1) X(4, 4)                                   \
+  X(5, 1) X(5, 2) X(5, 4)                           \
+  X(8, 1) X(8, 8)                                   \
+  X(9, 1) X(9, 2) X(9, 4) X(9, 8)                   \
+  X(16, 1) X(16, 16)                                \
+  X(17, 1) X(17, 4) X(17, 8) X(17, 16)              \
+  X(32, 32)                                         \
+  X(33, 8) X(33, 16) X(33, 32)
+#define GI_EKS_PAIRS_U32(X)                         \
+  X(3, 1) X(3, 2)                                   \
+  X(4, 1) X(4, 4)                                   \
+  X(5, 1) X(5, 2) X(5, 4)                           \
+  X(8, 1) X(8, 8)                                   \
+  X(9, 1) X(9, 2) X(9, 4) X(9, 8)                   \
+  X(16, 1) X(16, 16)                                \
+  X(17, 1) X(17, 2) X(17, 4) X(17, 8) X(17, 16)     \
+  X(32, 32)                                         \
+  X(33, 4) X(33, 8) X(33, 16) X(33, 32)
+bool eks_group_supported(uint32_t k, int key_bytes, int group);
 int eks_default_group(uint32_t k, int key_bytes);
 // slots staged in shared memory for `levels` top levels (0 = none)
 uint64_t smem_slots_for_levels(int layout, const Geom& g, int levels, int key_bytes);

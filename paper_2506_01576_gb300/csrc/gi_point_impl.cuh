@@ -166,7 +166,27 @@ __global__ void __launch_bounds__(512) k_ebs_point(const K* __restrict__ keys,
 }
 
 // ---------------------------------------------------------------- k-ary Eytzinger, lane groups
-// P contiguous keys (8 bytes, or a multiple of 16 bytes) with vector loads.
+// P contiguous keys (8, 16, 32 or 64 bytes...) with the widest vector loads:
+// 32-byte loads (ld.global.nc.v4.u64 / .v8.u32, sm_100+) where they fit.
+template <class K>
+__device__ __forceinline__ void ld32(const K* p, K* v) {
+  if constexpr (sizeof(K) == 8) {
+    unsigned long long a, b, c, d;
+    asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
+                 : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
+                 : "l"(p));
+    v[0] = a; v[1] = b; v[2] = c; v[3] = d;
+  } else {
+    uint32_t a[8];
+    asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]),
+                   "=r"(a[6]), "=r"(a[7])
+                 : "l"(p));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = a[i];
+  }
+}
+
 template <class K, int P>
 __device__ __forceinline__ void vec_load(const K* p, K* v) {
   constexpr int BYTES = P * (int)sizeof(K);
@@ -178,42 +198,49 @@ __device__ __forceinline__ void vec_load(const K* p, K* v) {
     } else {
       v[0] = ((uint64_t)t.y << 32) | t.x;
     }
-  } else {
-#pragma unroll
-    for (int i = 0; i < BYTES / 16; ++i) {
-      if constexpr (sizeof(K) == 4) {
-        const uint4 t = __ldg((const uint4*)p + i);
-        v[4 * i + 0] = t.x;
-        v[4 * i + 1] = t.y;
-        v[4 * i + 2] = t.z;
-        v[4 * i + 3] = t.w;
-      } else {
-        const ulonglong2 t = __ldg((const ulonglong2*)p + i);
-        v[2 * i + 0] = t.x;
-        v[2 * i + 1] = t.y;
-      }
+  } else if constexpr (BYTES == 16) {
+    if constexpr (sizeof(K) == 4) {
+      const uint4 t = __ldg((const uint4*)p);
+      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+      const ulonglong2 t = __ldg((const ulonglong2*)p);
+      v[0] = t.x; v[1] = t.y;
     }
+  } else {
+    constexpr int PER = 32 / (int)sizeof(K);
+#pragma unroll
+    for (int i = 0; i < BYTES / 32; ++i) ld32<K>(p + i * PER, v + i * PER);
   }
 }
 
 template <class K, int KF, int G>
 struct EksShape {
-  static constexpr int N = KF - 1;                 // pivots per node
-  static constexpr int P = (N + G - 1) / G;        // pivots per lane
-  // contiguous vector per lane when the node splits evenly into 8/16/32/64-byte pieces
-  static constexpr bool VEC = (N % G == 0) && (P >= 2) && (P * sizeof(K) >= 8) &&
-                              (P * sizeof(K) <= 64) && ((P & (P - 1)) == 0);
+  static constexpr int N = KF - 1;           // pivots per node
+  static constexpr int P = (N + G - 1) / G;  // pivots per lane
+  // one contiguous vector per lane when the node splits evenly into 8-byte or
+  // 16-byte pieces or whole 32-byte loads
+  static constexpr int BYTES = P * (int)sizeof(K);
+  static constexpr bool VEC = (N % G == 0) && (P >= 2 || sizeof(K) == 8) && ((P & (P - 1)) == 0) &&
+                              (BYTES == 8 || BYTES == 16 || BYTES % 32 == 0);
 };
 
-template <class K, int KF, int G, int R>
+// The lookup loop (Section 6.2).  Each group of G lanes owns R lookups at a
+// time and walks all tree levels in lock step, so every warp is at the same
+// level and the shared-memory / global choice is warp-uniform.  Slots past n
+// hold the maximum key (written at build), so a node needs no per-pivot bounds
+// check: c = #{pivots < x}; the lower-bound candidate is slot s+c if it exists;
+// the next node starts at s*k + (c+1)*(k-1).  Equality is resolved once at the
+// end with one load of the candidate key.
+template <class K, int KF, int G, int R, class IDX>
 __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
-                                                   const uint32_t* __restrict__ rows, uint64_t n,
+                                                   const uint32_t* __restrict__ rows, IDX n,
                                                    uint32_t levels, const K* __restrict__ q,
                                                    uint64_t m, uint32_t* __restrict__ out,
-                                                   uint32_t smem_slots, int early_exit,
+                                                   uint32_t smem_levels, uint32_t smem_slots,
                                                    uint32_t* flags) {
   using S = EksShape<K, KF, G>;
   constexpr int N = S::N, P = S::P;
+  constexpr IDX kNoCand = ~IDX(0);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t mbar;
   const K* sm = (const K*)smem_raw;
@@ -226,75 +253,82 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
   const uint32_t gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
   const uint64_t groups = ((uint64_t)gridDim.x * blockDim.x) / G;
   const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const IDX lane_off = S::VEC ? (IDX)(gl * P) : (IDX)gl;
 
   for (uint64_t first = gid; first < m; first += groups * R) {
     K x[R];
-    uint64_t s[R], cand[R];
-    bool act[R], eqf[R];
+    IDX s[R], cand[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint64_t i = first + r * groups;
-      act[r] = i < m && n > 0;
       x[r] = i < m ? q[i] : K(0);
-      s[r] = 0;
-      cand[r] = kNone;
-      eqf[r] = false;
+      s[r] = i < m ? IDX(0) : n;  // s >= n: nothing (more) to do
+      cand[r] = kNoCand;
     }
     for (uint32_t lv = 0; lv < levels; ++lv) {
       K piv[R][P];
+      const bool from_smem = lv < smem_levels;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        if (act[r]) {
-          if (S::VEC) {
-            const uint64_t at = s[r] + (uint64_t)gl * P;
-            if (s[r] < smem_slots) {
+        if (s[r] < n) {
+          const IDX at = s[r] + lane_off;
+          if (from_smem) {
+            if constexpr (S::VEC && S::BYTES >= 16) {
+              // 16-byte shared loads (the staged region is 16-byte aligned)
+              constexpr int PER = 16 / (int)sizeof(K);
 #pragma unroll
-              for (int p = 0; p < P; ++p) piv[r][p] = sm[at + p];
+              for (int i = 0; i < P / PER; ++i) {
+                const uint4 t = *reinterpret_cast<const uint4*>(sm + at + i * PER);
+                if constexpr (sizeof(K) == 8) {
+                  piv[r][i * 2] = ((uint64_t)t.y << 32) | t.x;
+                  piv[r][i * 2 + 1] = ((uint64_t)t.w << 32) | t.z;
+                } else {
+                  piv[r][i * 4] = t.x; piv[r][i * 4 + 1] = t.y;
+                  piv[r][i * 4 + 2] = t.z; piv[r][i * 4 + 3] = t.w;
+                }
+              }
             } else {
-              vec_load<K, P>(keys + at, piv[r]);
+#pragma unroll
+              for (int p = 0; p < P; ++p) {
+                const int j = S::VEC ? gl * P + p : gl + p * G;
+                piv[r][p] = j < N ? sm[s[r] + j] : K(0);
+              }
             }
+          } else if constexpr (S::VEC) {
+            vec_load<K, P>(keys + at, piv[r]);
           } else {
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-              const uint64_t at = s[r] + gl + (uint64_t)p * G;
-              const bool ok = (gl + p * G < N) && at < n;
-              piv[r][p] = ok ? (s[r] < smem_slots ? sm[at] : ldg(keys + at)) : K(0);
+              const int j = gl + p * G;
+              piv[r][p] = j < N ? ldg(keys + at + p * G) : K(0);
             }
           }
         }
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        if (act[r]) {
+        if (s[r] < n) {
+          // pivots < x held by this lane, then summed over the group (butterfly)
           uint32_t c = 0;
-          bool any_eq = false;
 #pragma unroll
           for (int p = 0; p < P; ++p) {
-            const int j = S::VEC ? gl * P + p : gl + p * G;  // position in the node
-            const bool ok = j < N && s[r] + j < n;
-            const bool lt = ok && piv[r][p] < x[r];
-            any_eq |= ok && piv[r][p] == x[r];
-            c += __popc(__ballot_sync(gmask, lt) & gmask);
+            const int j = S::VEC ? gl * P + p : gl + p * G;  // pivot position in the node
+            c += (j < N && piv[r][p] < x[r]) ? 1u : 0u;
           }
-          any_eq = __any_sync(gmask, any_eq);
-          if (c < (uint32_t)N && s[r] + c < n) {
-            cand[r] = s[r] + c;
-            eqf[r] = any_eq;
-          }
-          if (early_exit && any_eq) {
-            act[r] = false;
-          } else {
-            s[r] = s[r] * KF + (uint64_t)(c + 1) * N;
-            if (s[r] >= n) act[r] = false;
-          }
+#pragma unroll
+          for (int o = 1; o < G; o <<= 1) c += __shfl_xor_sync(gmask, c, o);
+          if (c < (uint32_t)N && s[r] + c < n) cand[r] = s[r] + c;
+          s[r] = s[r] * KF + (IDX)((c + 1) * N);
         }
       }
     }
-    if (gl == 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const uint64_t i = first + r * groups;
-        if (i < m) out[i] = eqf[r] ? ldg(rows + cand[r]) : GI_MISS;
+    for (int r = 0; r < R; ++r) {
+      const uint64_t i = first + r * groups;
+      if (i < m && gl == r % G) {
+        uint32_t res = GI_MISS;
+        if (cand[r] != kNoCand && ldg(keys + cand[r]) == x[r]) res = ldg(rows + cand[r]);
+        out[i] = res;
       }
     }
   }

@@ -7,25 +7,16 @@
 namespace gi {
 namespace pt {
 
-// Every (k, group) pair instantiated for the lane-group kernel.  G = 1 is the
-// single-thread variant.  The list is the same for both key types.
-#define GI_EKS_PAIRS(X) \
-  X(3, 1) X(3, 2)                        \
-  X(4, 1) X(4, 4)                        \
-  X(5, 1) X(5, 2) X(5, 4)                \
-  X(8, 1) X(8, 8)                        \
-  X(9, 1) X(9, 2) X(9, 4) X(9, 8)        \
-  X(16, 1) X(16, 8) X(16, 16)            \
-  X(17, 1) X(17, 4) X(17, 8) X(17, 16)   \
-  X(32, 1) X(32, 16) X(32, 32)           \
-  X(33, 1) X(33, 8) X(33, 16) X(33, 32)
-
-inline bool eks_pair_listed(uint32_t k, int g) {
-#define GI_X(KF, G) if (k == KF && g == G) return true;
-  GI_EKS_PAIRS(GI_X)
-#undef GI_X
-  return false;
-}
+// Lane-group k-ary lookups, instantiated in gi_eks_{u32,u64}_{a,b}.cu; each sets
+// *handled when it owns the requested (k, group) pair.
+#define GI_EKS_DECL(NAME)                                                                      \
+  cudaError_t NAME(const void* keys, const uint32_t* rows, const Geom& g, const LookupCfg& c, \
+                   const void* q, uint64_t m, uint32_t* out, uint32_t* dflags, cudaStream_t s, \
+                   bool* handled);
+GI_EKS_DECL(eks_point_u64_a)
+GI_EKS_DECL(eks_point_u64_b)
+GI_EKS_DECL(eks_point_u32_a)
+GI_EKS_DECL(eks_point_u32_b)
 
 template <class Kern>
 inline cudaError_t set_smem(Kern kern, size_t bytes) {
@@ -74,37 +65,19 @@ cudaError_t point_lookup_typed(const K* keys, const uint32_t* rows, const Geom& 
 #undef GI_EBS
     return e;
   }
-  // k-ary Eytzinger
-  const int G = c.group;
-  const uint32_t k = g.k;
-  const unsigned grid = grid_size((m + R - 1) / R * (uint64_t)G, block, c.blocks_per_sm);
-#define GI_X(KF, GG)                                                                          \
-  if (k == KF && G == GG) {                                                                   \
-    if (R == 1) {                                                                             \
-      auto kern = k_eks_point<K, KF, GG, 1>;                                                  \
-      cudaError_t e = set_smem(kern, smem);                                                   \
-      if (e != cudaSuccess) return e;                                                         \
-      kern<<<grid, block, smem, s>>>(keys, rows, g.n, g.levels, q, m, out, (uint32_t)slots,   \
-                                     c.early_exit, dflags);                                   \
-    } else if (R == 2) {                                                                      \
-      auto kern = k_eks_point<K, KF, GG, 2>;                                                  \
-      cudaError_t e = set_smem(kern, smem);                                                   \
-      if (e != cudaSuccess) return e;                                                         \
-      kern<<<grid, block, smem, s>>>(keys, rows, g.n, g.levels, q, m, out, (uint32_t)slots,   \
-                                     c.early_exit, dflags);                                   \
-    } else {                                                                                  \
-      auto kern = k_eks_point<K, KF, GG, 4>;                                                  \
-      cudaError_t e = set_smem(kern, smem);                                                   \
-      if (e != cudaSuccess) return e;                                                         \
-      kern<<<grid, block, smem, s>>>(keys, rows, g.n, g.levels, q, m, out, (uint32_t)slots,   \
-                                     c.early_exit, dflags);                                   \
-    }                                                                                         \
-    count_launch();                                                                           \
-    return cudaGetLastError();                                                                \
+  // k-ary Eytzinger: the compiled (k, group) pairs live in gi_eks_*.cu
+  {
+    bool handled = false;
+    cudaError_t e = sizeof(K) == 8
+        ? eks_point_u64_a(keys, rows, g, c, q, m, out, dflags, s, &handled)
+        : eks_point_u32_a(keys, rows, g, c, q, m, out, dflags, s, &handled);
+    if (handled) return e;
+    e = sizeof(K) == 8 ? eks_point_u64_b(keys, rows, g, c, q, m, out, dflags, s, &handled)
+                       : eks_point_u32_b(keys, rows, g, c, q, m, out, dflags, s, &handled);
+    if (handled) return e;
   }
-  GI_EKS_PAIRS(GI_X)
-#undef GI_X
-  // any other k: one thread per lookup
+  // any other k (or group): one thread per lookup
+  const uint32_t k = g.k;
   const unsigned ggrid = grid_size(m, block, c.blocks_per_sm);
   k_eks_generic<K><<<ggrid, block, 0, s>>>(keys, rows, g.n, k, q, m, out, c.early_exit);
   count_launch();

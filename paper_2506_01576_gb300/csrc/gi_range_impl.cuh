@@ -67,7 +67,8 @@ __device__ __forceinline__ void ebs_bounds(const K* __restrict__ keys, const Geo
   ru = b ? slot_to_rank<2>(b - 1, g) : g.n;
 }
 
-// k-ary: a group of G lanes, both descents interleaved.
+// k-ary: a group of G lanes (one key per lane), both descents interleaved.
+// Slots past n hold the maximum key, so only lanes past the node end are masked.
 template <class K, int KF, int G>
 __device__ __forceinline__ void eks_bounds(const K* __restrict__ keys, const Geom& g, K L, K U,
                                            int gl, uint32_t gmask, uint64_t& rl, uint64_t& ru) {
@@ -75,34 +76,30 @@ __device__ __forceinline__ void eks_bounds(const K* __restrict__ keys, const Geo
   constexpr int P = (N + G - 1) / G;
   const uint64_t n = g.n;
   uint64_t s[2] = {0, 0}, cand[2] = {~0ull, ~0ull};
-  bool act[2] = {n > 0, n > 0};
   const K x[2] = {L, U};
   for (uint32_t lv = 0; lv < g.levels; ++lv) {
     K piv[2][P];
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
-      if (act[d]) {
+      if (s[d] < n) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           const int j = gl + p * G;
-          const uint64_t at = s[d] + j;
-          piv[d][p] = (j < N && at < n) ? __ldg(keys + at) : K(0);
+          piv[d][p] = j < N ? __ldg(keys + s[d] + j) : K(0);
         }
       }
     }
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
-      if (act[d]) {
+      if (s[d] < n) {
         uint32_t c = 0;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           const int j = gl + p * G;
-          const bool ok = j < N && s[d] + j < n;
-          c += __popc(__ballot_sync(gmask, ok && before(piv[d][p], x[d], d == 1)) & gmask);
+          c += __popc(__ballot_sync(gmask, j < N && before(piv[d][p], x[d], d == 1)) & gmask);
         }
         if (c < (uint32_t)N && s[d] + c < n) cand[d] = s[d] + c;
         s[d] = s[d] * KF + (uint64_t)(c + 1) * N;
-        if (s[d] >= n) act[d] = false;
       }
     }
   }

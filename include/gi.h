@@ -206,6 +206,35 @@ int gi_coalescing_probe(const uint32_t* buf, uint64_t entries, uint32_t threads,
                         uint32_t group, uint32_t steps, uint64_t seed, uint64_t* sink,
                         void* stream);
 
+/*
+ * gi_range_lookup_noalloc -- gi_range_lookup for callers that must not allocate.
+ * The paper has no counterpart: this entry point exists for users whose device
+ * memory is owned by someone else (a query engine or framework that hands the
+ * whole GPU to its own pool allocator) or who cannot afford an allocation call
+ * in the middle of a query (cudaMalloc/cudaFree can block or synchronise the
+ * device).  It computes exactly what gi_range_lookup computes, but its scratch
+ * (the lower rank of every range and the scan's block sums) lives in one
+ * fixed-size array inside the library, so it calls no allocator at all.
+ *   m            at most GI_NOALLOC_MAX_RANGES ranges; more returns GI_ERR_INVALID.
+ *   lo, hi, out_offsets, out_rowids
+ *                as in gi_range_lookup, but all must be DEVICE memory (staging
+ *                host memory would need an allocation): host pointers return
+ *                GI_ERR_INVALID.  out_rowids may be NULL (offsets only).
+ * The array is a static device variable of GI_NOALLOC_SCRATCH_BYTES bytes that
+ * every GPU which loads this library holds until the process exits.  The first
+ * call on a device looks up the array's device address on that device (a
+ * cudaGetSymbolAddress call, made with the index's device current); make that
+ * first call before any stream capture.  Every call on a device shares the one
+ * array and leaves its contents behind (nothing in it needs to start zeroed):
+ * calls whose GPU work overlaps -- on different streams, or from different
+ * threads -- race on it and must be serialised by the caller.  Asynchronous on
+ * the index's stream, like gi_range_lookup with device pointers.
+ */
+#define GI_NOALLOC_MAX_RANGES (1u << 20)
+#define GI_NOALLOC_SCRATCH_BYTES ((8u << 20) + 8192u)
+int gi_range_lookup_noalloc(const gi_index* index, const void* lo, const void* hi, uint64_t m,
+                            uint64_t* out_offsets, uint32_t* out_rowids);
+
 /* Number of kernels this library has launched in the process so far. */
 uint64_t gi_launch_count(void);
 

@@ -27,12 +27,14 @@ __all__ = [
     "gi_build", "gi_point_lookup", "gi_range_lookup", "gi_destroy", "gi_set_stream", "gi_sync",
     "gi_last_error", "gi_footprint_bytes", "gi_get_info", "gi_copy_layout", "gi_set_option", "gi_get_option",
     "gi_probe_random_sectors", "gi_coalescing_probe", "gi_launch_count",
+    "gi_range_lookup_noalloc", "GI_NOALLOC_MAX_RANGES",
 ]
 
 GI_SORTED, GI_EYTZINGER, GI_EYTZINGER_KARY = 0, 1, 2
 GI_KEY_U32, GI_KEY_U64 = 0x000, 0x100
 GI_OK, GI_ERR_INVALID, GI_ERR_NOMEM, GI_ERR_CUDA, GI_ERR_TIMEOUT = 0, 1, 2, 3, 4
 GI_MISS = 0xFFFFFFFF
+GI_NOALLOC_MAX_RANGES = 1 << 20
 (GI_OPT_GROUP, GI_OPT_PER_THREAD, GI_OPT_SMEM_LEVELS, GI_OPT_BLOCK, GI_OPT_BLOCKS_PER_SM,
  GI_OPT_PREFETCH, GI_OPT_EARLY_EXIT) = range(1, 8)
 
@@ -83,6 +85,7 @@ def load(build_if_missing: bool = False):
         "gi_probe_random_sectors": (I, [P, U64, U32, U64, U64, P, P]),
         "gi_coalescing_probe": (I, [P, U64, U32, U32, U32, U64, P, P]),
         "gi_launch_count": (U64, []),
+        "gi_range_lookup_noalloc": (I, [P, P, P, U64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -182,6 +185,16 @@ def gi_range_lookup(index: Index, lo, hi, out_offsets, out_rowids=None) -> None:
         raise ValueError("lo/hi lengths differ or out_offsets is shorter than m+1")
     _check(load().gi_range_lookup(index.handle, _ptr(lo), _ptr(hi), m, _ptr(out_offsets),
                                   _ptr(out_rowids)))
+
+
+def gi_range_lookup_noalloc(index: Index, lo, hi, out_offsets, out_rowids=None) -> None:
+    """gi_range_lookup without any allocation: device buffers only, at most
+    GI_NOALLOC_MAX_RANGES ranges, scratch in a fixed array inside the library."""
+    m = _len(lo)
+    if _len(hi) != m or _len(out_offsets) < m + 1:
+        raise ValueError("lo/hi lengths differ or out_offsets is shorter than m+1")
+    _check(load().gi_range_lookup_noalloc(index.handle, _ptr(lo), _ptr(hi), m, _ptr(out_offsets),
+                                          _ptr(out_rowids)))
 
 
 def gi_destroy(index: Index) -> None:

@@ -755,3 +755,64 @@ int gi_coalescing_probe(const uint32_t* buf, uint64_t entries, uint32_t threads,
 }
 
 }  // extern "C"
+
+// ================================================================= allocation-free range lookups
+// For callers that cannot allocate device memory (see gi_range_lookup_noalloc in
+// gi.h).  The scratch of the range lookup lives in this file-scope device array;
+// host code only ever passes the device address looked up below, never the
+// array's name (which in host code is a host-side stand-in, not device memory).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GI_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on `dev` (which must be current); looked
+// up once per device.
+int noalloc_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(GI_ERR_INVALID, "gi_range_lookup_noalloc: device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorUnknown,
+                                                 "gi_range_lookup_noalloc: scratch address");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return GI_OK;
+}
+}  // namespace
+
+extern "C" int gi_range_lookup_noalloc(const gi_index* idx, const void* lo, const void* hi,
+                                       uint64_t m, uint64_t* out_offsets, uint32_t* out_rowids) {
+  t_err.clear();
+  if (!idx) return fail(GI_ERR_INVALID, "gi_range_lookup_noalloc: NULL index");
+  if (!out_offsets) return fail(GI_ERR_INVALID, "gi_range_lookup_noalloc: NULL out_offsets");
+  if (m > GI_NOALLOC_MAX_RANGES)
+    return fail(GI_ERR_INVALID, "gi_range_lookup_noalloc: %llu ranges exceed the maximum of %u",
+                (unsigned long long)m, (unsigned)GI_NOALLOC_MAX_RANGES);
+  if (m > 0 && (!lo || !hi)) return fail(GI_ERR_INVALID, "gi_range_lookup_noalloc: NULL bounds");
+  if (gi::range_scratch_bytes(m) > GI_NOALLOC_SCRATCH_BYTES)
+    return fail(GI_ERR_INVALID, "gi_range_lookup_noalloc: scratch too small for %llu ranges",
+                (unsigned long long)m);
+  DeviceScope ds(idx->device);
+  if ((m && (pointer_kind(lo) != kDevice || pointer_kind(hi) != kDevice)) ||
+      pointer_kind(out_offsets) != kDevice || (out_rowids && pointer_kind(out_rowids) != kDevice))
+    return fail(GI_ERR_INVALID, "gi_range_lookup_noalloc: every buffer must be device memory");
+  void* scratch = nullptr;
+  int rc = noalloc_scratch(idx->device, &scratch);
+  if (rc != GI_OK) return rc;
+  const gi::LookupCfg c = resolve_cfg(idx);
+  // counts_ready = false: another call may have overwritten the shared scratch
+  cudaError_t e = idx->key_bytes == 4
+      ? gi::range_lookup_u32(idx->keys, idx->rows, idx->geom, c, lo, hi, m, out_offsets,
+                             out_rowids, scratch, false, idx->stream)
+      : gi::range_lookup_u64(idx->keys, idx->rows, idx->geom, c, lo, hi, m, out_offsets,
+                             out_rowids, scratch, false, idx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gi_range_lookup_noalloc");
+  return GI_OK;
+}
+

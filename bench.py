@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="timed steps only (for profiler launch lists)")
     return ap.parse_args()
 
 
@@ -238,7 +239,7 @@ def run_ours(a):
 
     # parity spot check of the timed configuration (results are integers: exact)
     res = {}
-    if rank == 0:
+    if rank == 0 and not a.no_extras:
         res = extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, layout,
                      total_rows)
     if world > 1:

@@ -173,7 +173,12 @@ int gi_copy_layout(const gi_index* index, void* keys_out, uint32_t* rowids_out);
  *                       of that many blocks per SM with a static schedule.
  *   GI_OPT_PREFETCH     EYTZINGER prefetch distance in levels: 0, 2, 3, 4.
  *   GI_OPT_EARLY_EXIT   stop a point lookup at an equal pivot: 0 or 1 (only honoured
- *                       when the keys are unique).
+ *                       when the keys are unique, by the kernel for k values that
+ *                       are not compiled in; the others resolve equality at the end).
+ *   GI_OPT_HOT_LEVELS   EYTZINGER_KARY: top levels read with an L2 evict-last hint;
+ *                       deeper levels, rowIDs, probes and results use evict-first
+ *                       (0 = every level streamed).  Default: the levels whose keys
+ *                       fit in two thirds of L2.
  */
 #define GI_OPT_GROUP         1
 #define GI_OPT_PER_THREAD    2
@@ -182,6 +187,7 @@ int gi_copy_layout(const gi_index* index, void* keys_out, uint32_t* rowids_out);
 #define GI_OPT_BLOCKS_PER_SM 5
 #define GI_OPT_PREFETCH      6
 #define GI_OPT_EARLY_EXIT    7
+#define GI_OPT_HOT_LEVELS    8
 int gi_set_option(gi_index* index, int option, int64_t value);
 int gi_get_option(const gi_index* index, int option, int64_t* value);
 

@@ -35,7 +35,7 @@ struct gi_index {
   uint32_t* rows = nullptr;
   uint32_t* dflags = nullptr;  // device status word
   gi::Geom geom{};
-  int64_t opt[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  int64_t opt[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
   // range-lookup scratch and the state of the two-call protocol
   void* rscratch = nullptr;
   size_t rscratch_bytes = 0;
@@ -109,7 +109,26 @@ size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t key_alloc_bytes(uint64_t n, int key_bytes) { return round256((n + 1 + 64) * key_bytes + 64); }
 size_t row_alloc_bytes(uint64_t n) { return round256((n + 64) * 4); }
 
-cudaError_t dalloc(void** p, size_t bytes, cudaStream_t s) { return cudaMallocAsync(p, bytes, s); }
+// Device memory comes from the device's stream-ordered pool.  The pool's release
+// threshold is raised once per device to 8 GiB (a setting of this process only):
+// the sort buffers a build frees are reused by the next build instead of being
+// unmapped and mapped again at every synchronisation, while freed memory beyond
+// 8 GiB still goes back to the driver.
+cudaError_t dalloc(void** p, size_t bytes, cudaStream_t s) {
+  static std::once_flag once[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+    std::call_once(once[dev], [dev] {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = 8ull << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+      cudaGetLastError();
+    });
+  }
+  return cudaMallocAsync(p, bytes, s);
+}
 void dfree(void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
@@ -148,6 +167,15 @@ gi::LookupCfg resolve_cfg(const gi_index* idx) {
   const int ee = o[GI_OPT_EARLY_EXIT] >= 0 ? (int)o[GI_OPT_EARLY_EXIT] : 1;
   c.early_exit = (ee && idx->unique) ? 1 : 0;
   if (c.layout == GI_SORTED) c.per_thread = 1;
+  if (o[GI_OPT_HOT_LEVELS] >= 0) {
+    c.hot_levels = (int)o[GI_OPT_HOT_LEVELS];
+  } else {
+    // keep the top levels that fit in about two thirds of L2 (the rest of L2
+    // absorbs the streamed probes, results and deep-level lines)
+    int dev = idx->device, l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    c.hot_levels = gi::levels_within(idx->geom, idx->key_bytes, (uint64_t)l2 * 2 / 3);
+  }
   return c;
 }
 
@@ -269,6 +297,21 @@ int eks_default_group(uint32_t k, int key_bytes) {
   for (int g = 32; g >= 1; g >>= 1)
     if (eks_group_supported(k, key_bytes, g)) return g;
   return 1;  // generic kernel
+}
+
+int levels_within(const Geom& g, int key_bytes, uint64_t budget) {
+  if (g.n == 0 || g.k < 2) return 0;
+  uint64_t cum = 0, width = g.k - 1;
+  int l = 0;
+  while (l < (int)g.levels) {
+    const uint64_t keys = l + 1 < (int)g.levels ? width : g.b;
+    cum += keys * key_bytes;
+    if (cum > budget) break;
+    ++l;
+    if (width > (~0ull) / g.k) break;
+    width *= g.k;
+  }
+  return l;
 }
 
 uint64_t smem_slots_for_levels(int layout, const Geom& g, int levels, int key_bytes) {
@@ -667,7 +710,7 @@ int gi_copy_layout(const gi_index* cidx, void* keys_out, uint32_t* rowids_out) {
 int gi_set_option(gi_index* idx, int option, int64_t v) {
   t_err.clear();
   if (!idx) return fail(GI_ERR_INVALID, "gi_set_option: NULL index");
-  if (option < 1 || option > 7) return fail(GI_ERR_INVALID, "gi_set_option: unknown option %d", option);
+  if (option < 1 || option > 8) return fail(GI_ERR_INVALID, "gi_set_option: unknown option %d", option);
   if (v == -1) {
     idx->opt[option] = -1;
     return GI_OK;
@@ -703,6 +746,9 @@ int gi_set_option(gi_index* idx, int option, int64_t v) {
     case GI_OPT_EARLY_EXIT:
       if (v != 0 && v != 1) return fail(GI_ERR_INVALID, "gi_set_option: early exit must be 0 or 1");
       break;
+    case GI_OPT_HOT_LEVELS:
+      if (v < 0 || v > 64) return fail(GI_ERR_INVALID, "gi_set_option: hot levels out of range");
+      break;
   }
   idx->opt[option] = v;
   return GI_OK;
@@ -711,7 +757,7 @@ int gi_set_option(gi_index* idx, int option, int64_t v) {
 int gi_get_option(const gi_index* idx, int option, int64_t* v) {
   t_err.clear();
   if (!idx || !v) return fail(GI_ERR_INVALID, "gi_get_option: NULL argument");
-  if (option < 1 || option > 7) return fail(GI_ERR_INVALID, "gi_get_option: unknown option %d", option);
+  if (option < 1 || option > 8) return fail(GI_ERR_INVALID, "gi_get_option: unknown option %d", option);
   const gi::LookupCfg c = resolve_cfg(idx);
   switch (option) {
     case GI_OPT_GROUP: *v = c.group; break;
@@ -721,6 +767,7 @@ int gi_get_option(const gi_index* idx, int option, int64_t* v) {
     case GI_OPT_BLOCKS_PER_SM: *v = c.blocks_per_sm; break;
     case GI_OPT_PREFETCH: *v = c.prefetch; break;
     case GI_OPT_EARLY_EXIT: *v = c.early_exit; break;
+    case GI_OPT_HOT_LEVELS: *v = c.hot_levels; break;
   }
   return GI_OK;
 }

@@ -149,7 +149,10 @@ struct LookupCfg {
   int blocks_per_sm;  // 0: one thread (group) per work item
   int prefetch;       // EBS prefetch distance
   int early_exit;     // stop on an equal pivot (unique keys only)
+  int hot_levels;     // k-ary: top levels kept in L2 (evict_last); the rest streamed
 };
+// top levels whose keys fit in `budget` bytes
+int levels_within(const Geom& g, int key_bytes, uint64_t budget);
 cudaError_t point_lookup_u32(const void* keys, const uint32_t* rows, const Geom& g,
                              const LookupCfg& c, const void* q, uint64_t m, uint32_t* out,
                              uint32_t* dflags, cudaStream_t s);

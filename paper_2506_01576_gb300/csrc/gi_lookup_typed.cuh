@@ -38,7 +38,9 @@ cudaError_t range_lookup_typed(const K* keys, const uint32_t* rows, const Geom& 
       bool done = false;
 #define GI_RC(KF)                                                                            \
   if (!done && g.k == KF) {                                                                  \
-    constexpr int GG = (KF - 1 <= 1) ? 1 : (KF - 1 <= 2) ? 2 : (KF - 1 <= 4) ? 4             \
+    /* one thread per range when a node is one vector of <= 64 bytes, else one key/lane */   \
+    constexpr bool SINGLE = pt::EksShape<K, KF, 1>::VEC && (KF - 1) * sizeof(K) <= 64;       \
+    constexpr int GG = SINGLE ? 1 : (KF - 1 <= 2) ? 2 : (KF - 1 <= 4) ? 4                    \
                      : (KF - 1 <= 8) ? 8 : (KF - 1 <= 16) ? 16 : 32;                         \
     k_range_count<K, 2, KF, GG><<<grid_for(m * GG), block, 0, s>>>(keys, g, lo, hi, m,       \
                                                                    offsets, lo_rank);        \

@@ -213,6 +213,95 @@ __device__ __forceinline__ void vec_load(const K* p, K* v) {
   }
 }
 
+// ---- L2 eviction-priority hints (createpolicy + ld/st ...L2::cache_hint)
+__device__ __forceinline__ uint64_t l2_policy(bool keep) {
+  uint64_t pol;
+  if (keep)
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  else
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+template <class K>
+__device__ __forceinline__ K ld_hint(const K* p, uint64_t pol) {
+  if constexpr (sizeof(K) == 8) {
+    unsigned long long v;
+    asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+    return (K)v;
+  } else {
+    uint32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return (K)v;
+  }
+}
+
+// a streamed (read-once) value: skip L1, evict first from L2
+template <class K>
+__device__ __forceinline__ K ld_stream(const K* p, uint64_t pol) {
+  if constexpr (sizeof(K) == 8) {
+    unsigned long long v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;"
+                 : "=l"(v) : "l"(p), "l"(pol));
+    return (K)v;
+  } else {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;"
+                 : "=r"(v) : "l"(p), "l"(pol));
+    return (K)v;
+  }
+}
+
+__device__ __forceinline__ void st_stream(uint32_t* p, uint32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+
+// P contiguous keys with the widest vector loads, under an L2 policy
+template <class K, int P>
+__device__ __forceinline__ void vec_load_hint(const K* p, K* v, uint64_t pol) {
+  constexpr int BYTES = P * (int)sizeof(K);
+  if constexpr (BYTES == 8) {
+    if constexpr (sizeof(K) == 8) {
+      v[0] = ld_hint<K>(p, pol);
+    } else {
+      uint32_t a, b;
+      asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+                   : "=r"(a), "=r"(b) : "l"(p), "l"(pol));
+      v[0] = a; v[1] = b;
+    }
+  } else if constexpr (BYTES == 16) {
+    if constexpr (sizeof(K) == 8) {
+      unsigned long long a, b;
+      asm volatile("ld.global.nc.L2::cache_hint.v2.u64 {%0,%1}, [%2], %3;"
+                   : "=l"(a), "=l"(b) : "l"(p), "l"(pol));
+      v[0] = a; v[1] = b;
+    } else {
+      uint32_t a, b, c, d;
+      asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                   : "=r"(a), "=r"(b), "=r"(c), "=r"(d) : "l"(p), "l"(pol));
+      v[0] = a; v[1] = b; v[2] = c; v[3] = d;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < BYTES / 32; ++i) {
+      if constexpr (sizeof(K) == 8) {
+        unsigned long long a, b, c, d;
+        asm volatile("ld.global.nc.L2::cache_hint.v4.u64 {%0,%1,%2,%3}, [%4], %5;"
+                     : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p + 4 * i), "l"(pol));
+        v[4 * i] = a; v[4 * i + 1] = b; v[4 * i + 2] = c; v[4 * i + 3] = d;
+      } else {
+        uint32_t a[8];
+        asm volatile("ld.global.nc.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+                     : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]),
+                       "=r"(a[6]), "=r"(a[7])
+                     : "l"(p + 8 * i), "l"(pol));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[8 * i + j] = a[j];
+      }
+    }
+  }
+}
+
 template <class K, int KF, int G>
 struct EksShape {
   static constexpr int N = KF - 1;           // pivots per node
@@ -237,7 +326,7 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
                                                    uint32_t levels, const K* __restrict__ q,
                                                    uint64_t m, uint32_t* __restrict__ out,
                                                    uint32_t smem_levels, uint32_t smem_slots,
-                                                   uint32_t* flags) {
+                                                   uint32_t hot_levels, uint32_t* flags) {
   using S = EksShape<K, KF, G>;
   constexpr int N = S::N, P = S::P;
   constexpr IDX kNoCand = ~IDX(0);
@@ -254,6 +343,9 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
   const uint64_t groups = ((uint64_t)gridDim.x * blockDim.x) / G;
   const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const IDX lane_off = S::VEC ? (IDX)(gl * P) : (IDX)gl;
+  // Top `hot_levels` levels are kept in L2 (evict_last); deeper levels, rowIDs,
+  // probes and results are touched once per lookup and evicted first.
+  const uint64_t pol_keep = l2_policy(true), pol_stream = l2_policy(false);
 
   for (uint64_t first = gid; first < m; first += groups * R) {
     K x[R];
@@ -261,13 +353,14 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint64_t i = first + r * groups;
-      x[r] = i < m ? q[i] : K(0);
+      x[r] = i < m ? ld_stream<K>(q + i, pol_stream) : K(0);
       s[r] = i < m ? IDX(0) : n;  // s >= n: nothing (more) to do
       cand[r] = kNoCand;
     }
     for (uint32_t lv = 0; lv < levels; ++lv) {
       K piv[R][P];
       const bool from_smem = lv < smem_levels;
+      const uint64_t pol = lv < hot_levels ? pol_keep : pol_stream;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (s[r] < n) {
@@ -295,12 +388,12 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
               }
             }
           } else if constexpr (S::VEC) {
-            vec_load<K, P>(keys + at, piv[r]);
+            vec_load_hint<K, P>(keys + at, piv[r], pol);
           } else {
 #pragma unroll
             for (int p = 0; p < P; ++p) {
               const int j = gl + p * G;
-              piv[r][p] = j < N ? ldg(keys + at + p * G) : K(0);
+              piv[r][p] = j < N ? ld_hint<K>(keys + at + p * G, pol) : K(0);
             }
           }
         }
@@ -327,8 +420,9 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
       const uint64_t i = first + r * groups;
       if (i < m && gl == r % G) {
         uint32_t res = GI_MISS;
-        if (cand[r] != kNoCand && ldg(keys + cand[r]) == x[r]) res = ldg(rows + cand[r]);
-        out[i] = res;
+        if (cand[r] != kNoCand && ld_hint<K>(keys + cand[r], pol_stream) == x[r])
+          res = ld_hint<uint32_t>(rows + cand[r], pol_stream);
+        st_stream(out + i, res, pol_stream);
       }
     }
   }

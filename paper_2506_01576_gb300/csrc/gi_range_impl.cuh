@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include "gi_internal.cuh"
+#include "gi_point_impl.cuh"
 
 namespace gi {
 namespace rg {
@@ -107,6 +108,37 @@ __device__ __forceinline__ void eks_bounds(const K* __restrict__ keys, const Geo
   ru = cand[1] != ~0ull ? slot_to_rank<KF>(cand[1], g) : n;
 }
 
+// k-ary, one thread per range when a node is one vector of at most 64 bytes:
+// both descents interleaved, whole nodes loaded with vector loads, no ballots.
+template <class K, int KF>
+__device__ __forceinline__ void eks_bounds_single(const K* __restrict__ keys, const Geom& g, K L,
+                                                  K U, uint64_t& rl, uint64_t& ru) {
+  constexpr int N = KF - 1;
+  const uint64_t n = g.n;
+  uint64_t s0 = 0, s1 = 0, c0 = ~0ull, c1 = ~0ull;
+  for (uint32_t lv = 0; lv < g.levels; ++lv) {
+    K a[N], b[N];
+    if (s0 < n) pt::vec_load<K, N>(keys + s0, a);
+    if (s1 < n) pt::vec_load<K, N>(keys + s1, b);
+    if (s0 < n) {
+      uint32_t c = 0;
+#pragma unroll
+      for (int p = 0; p < N; ++p) c += a[p] < L ? 1u : 0u;
+      if (c < (uint32_t)N && s0 + c < n) c0 = s0 + c;
+      s0 = s0 * KF + (uint64_t)(c + 1) * N;
+    }
+    if (s1 < n) {
+      uint32_t c = 0;
+#pragma unroll
+      for (int p = 0; p < N; ++p) c += b[p] <= U ? 1u : 0u;
+      if (c < (uint32_t)N && s1 + c < n) c1 = s1 + c;
+      s1 = s1 * KF + (uint64_t)(c + 1) * N;
+    }
+  }
+  rl = c0 != ~0ull ? slot_to_rank<KF>(c0, g) : n;
+  ru = c1 != ~0ull ? slot_to_rank<KF>(c1, g) : n;
+}
+
 // Any k at run time, one thread.
 template <class K>
 __device__ __forceinline__ uint64_t eks_bound_generic(const K* __restrict__ keys, const Geom& g,
@@ -148,6 +180,8 @@ __global__ void __launch_bounds__(256) k_range_count(const K* __restrict__ keys,
         ru = sorted_bound(keys, g.n, U, true);
       } else if constexpr (LAYOUT == 1) {
         ebs_bounds(keys, g, L, U, rl, ru);
+      } else if constexpr (KF > 0 && G == 1) {
+        eks_bounds_single<K, KF>(keys, g, L, U, rl, ru);
       } else if constexpr (KF > 0) {
         eks_bounds<K, KF, G>(keys, g, L, U, gl, gmask, rl, ru);
       } else {

@@ -154,30 +154,29 @@ __global__ void __launch_bounds__(256) k_scan_hist(const unsigned long long* __r
 
 // ---------------------------------------------------------------- one onesweep pass
 template <class K>
-__global__ void __launch_bounds__(kSortThreads) k_sort_pass(
+__global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
     const K* __restrict__ src_k, const uint32_t* __restrict__ src_v, K* __restrict__ dst_k,
     uint32_t* __restrict__ dst_v, uint64_t n, uint32_t shift,
     const unsigned long long* __restrict__ digit_off, uint64_t* __restrict__ status,
     uint32_t* __restrict__ tile_counter, uint32_t epoch, uint32_t* __restrict__ flags) {
   constexpr int ITEMS = SortTile<K>::kItems;
   constexpr int TILE = kSortThreads * ITEMS;
-  struct WarpHist {
+  // keys and rowIDs have their own exchange arrays, so one final loop writes both;
+  // the per-warp digit counters share space with the rowIDs (dead by then)
+  union HistOrVals {
     uint32_t h[kSortWarps][kRadix];
-  };
-  union Exchange {
-    WarpHist wh;
-    K keys[TILE];
     uint32_t vals[TILE];
   };
-  __shared__ Exchange ex;
-  __shared__ uint32_t s_start[kRadix];          // tile-local start of each digit's run
+  __shared__ K s_keys[TILE];
+  __shared__ HistOrVals hv;
+  __shared__ uint32_t s_start[kRadix];            // tile-local start of each digit's run
   __shared__ unsigned long long s_gbase[kRadix];  // global position of local position 0 per digit
   __shared__ uint32_t s_warp_tot[kSortWarps];
   __shared__ uint32_t s_tile;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
-  for (int i = lane; i < kRadix; i += 32) ex.wh.h[warp][i] = 0;
+  for (int i = lane; i < kRadix; i += 32) hv.h[warp][i] = 0;
   __syncthreads();
   const uint64_t tile = s_tile;
   const uint64_t tile_base = tile * TILE;
@@ -186,20 +185,18 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
   // Warp-striped ownership: item i of lane l in warp w is tile element
   // w*32*ITEMS + i*32 + l, so tile order is (warp, item, lane).
   K key[ITEMS];
-  uint32_t dig[ITEMS];
   uint32_t rnk[ITEMS];
   const uint64_t wbase = tile_base + (uint64_t)warp * 32 * ITEMS + lane;
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint64_t idx = wbase + (uint64_t)i * 32;
     key[i] = idx < n ? src_k[idx] : ~K(0);  // padding sorts last (digit 255, after real keys)
-    dig[i] = (uint32_t)(key[i] >> shift) & 0xFF;
   }
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
-    const uint32_t d = dig[i];
-    uint32_t peers = 0xffffffffu;
+    const uint32_t d = (uint32_t)(key[i] >> shift) & 0xFF;
+    uint32_t peers = 0xffffffffu;  // lanes holding the same digit, from one ballot per bit
 #pragma unroll
     for (int b = 0; b < kRadixBits; ++b) {
       const uint32_t bit = (d >> b) & 1u;
@@ -208,9 +205,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     }
     const uint32_t before = __popc(peers & lt_mask);
     const uint32_t leader = 31 - __clz(peers);
-    const uint32_t base = ex.wh.h[warp][d];
+    const uint32_t base = hv.h[warp][d];
     __syncwarp();
-    if (lane == leader) ex.wh.h[warp][d] = base + __popc(peers);
+    if (lane == leader) hv.h[warp][d] = base + __popc(peers);
     __syncwarp();
     rnk[i] = base + before;
   }
@@ -221,8 +218,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
   uint32_t cnt = 0;
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) {
-    const uint32_t c = ex.wh.h[w][d];
-    ex.wh.h[w][d] = cnt;
+    const uint32_t c = hv.h[w][d];
+    hv.h[w][d] = cnt;
     cnt += c;
   }
   const uint32_t cnt_valid = (d == kRadix - 1) ? cnt - (TILE - valid) : cnt;
@@ -270,35 +267,35 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
   s_gbase[d] = digit_off[d] + excl - start;
   __syncthreads();
 
-  uint32_t pos[ITEMS];
+  // Local sorted position of every key: its digit's run start + earlier warps'
+  // count of that digit + its rank within its warp.
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) pos[i] = s_start[dig[i]] + ex.wh.h[warp][dig[i]] + rnk[i];
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) ex.keys[pos[i]] = key[i];
-  __syncthreads();
-
-  // Consecutive threads take consecutive local positions: each digit run is
-  // written to consecutive global addresses.
-  uint64_t dst[ITEMS];
-#pragma unroll
-  for (int r = 0; r < ITEMS; ++r) {
-    const uint32_t j = tid + r * kSortThreads;
-    const K kk = ex.keys[j];
-    dst[r] = s_gbase[(uint32_t)(kk >> shift) & 0xFF] + j;
-    if (j < valid && dst[r] < n) dst_k[dst[r]] = kk;  // the bound only guards a failed wait
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t dd = (uint32_t)(key[i] >> shift) & 0xFF;
+    rnk[i] += s_start[dd] + hv.h[warp][dd];
+    s_keys[rnk[i]] = key[i];
   }
-  __syncthreads();
+  __syncthreads();  // the digit counters are dead: their space takes the rowIDs
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint64_t idx = wbase + (uint64_t)i * 32;
-    ex.vals[pos[i]] = idx < n ? src_v[idx] : 0u;
+    hv.vals[rnk[i]] = idx < n ? src_v[idx] : 0u;
   }
   __syncthreads();
+
+  // Consecutive threads take consecutive local positions: each digit run goes
+  // to consecutive global addresses, keys and rowIDs alike.
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
     const uint32_t j = tid + r * kSortThreads;
-    if (j < valid && dst[r] < n) dst_v[dst[r]] = ex.vals[j];
+    if (j < valid) {
+      const K kk = s_keys[j];
+      const uint64_t dst = s_gbase[(uint32_t)(kk >> shift) & 0xFF] + j;
+      if (dst < n) {  // the bound only guards a failed wait
+        dst_k[dst] = kk;
+        dst_v[dst] = hv.vals[j];
+      }
+    }
   }
 }
 

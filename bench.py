@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--ranges-log", type=int, default=22)
     ap.add_argument("--range-rows", type=float, default=16.0)
     ap.add_argument("--k", type=int, default=5, help="EKS fan-out")
+    ap.add_argument("--layout", default="eks", choices=["eks", "ebs", "bs"],
+                    help="layout built and probed in the timed step")
     ap.add_argument("--group", type=int, default=-1)
     ap.add_argument("--per-thread", type=int, default=-1)
     ap.add_argument("--smem-levels", type=int, default=-1)
@@ -60,6 +62,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="timed steps only (for profiler launch lists)")
+    ap.add_argument("--probe-sweep", action="store_true",
+                    help="print random-access throughput over buffer sizes (L2 vs HBM) and exit")
     return ap.parse_args()
 
 
@@ -182,10 +186,11 @@ def run_ours(a):
     off = torch.empty(mr + 1, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream()
     gi.gi_set_stream(None, stream)
-    layout = gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64
+    layout = {"eks": gi.GI_EYTZINGER_KARY, "ebs": gi.GI_EYTZINGER, "bs": gi.GI_SORTED}[a.layout] | gi.GI_KEY_U64
 
     def configure(idx):
-        for opt, v in ((gi.GI_OPT_GROUP, a.group), (gi.GI_OPT_PER_THREAD, a.per_thread),
+        for opt, v in ((gi.GI_OPT_GROUP, a.group if a.layout == "eks" else -1),
+                       (gi.GI_OPT_PER_THREAD, a.per_thread),
                        (gi.GI_OPT_SMEM_LEVELS, a.smem_levels),
                        (gi.GI_OPT_BLOCKS_PER_SM, a.blocks_per_sm)):
             gi.gi_set_option(idx, opt, v)
@@ -251,11 +256,13 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "build 2^%d unique u64 keys (EKS k=%d) + 2^%d point probes (hit 0.5, "
+        "config": {"workload": "build 2^%d unique u64 keys (%s) + 2^%d point probes (hit 0.5, "
                                "uniform) + 2^%d ranges (%.0f expected rows) per step"
-                               % (a.n_log, a.k, a.m_log, a.ranges_log, a.range_rows),
+                               % (a.n_log, "EKS k=%d" % a.k if a.layout == "eks" else a.layout.upper(),
+                                  a.m_log, a.ranges_log, a.range_rows),
                    "n_keys": n, "point_probes": m, "ranges": mr, "range_rows_total": total_rows,
-                   "layout": "EKS", "k": a.k, "l2": "inputs larger than L2 (no flush)",
+                   "layout": a.layout.upper(), "k": a.k if a.layout == "eks" else None,
+                   "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "clocks": clk.summary(), "gpu_launches": int(launches),
     }
@@ -463,9 +470,37 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def probe_sweep():
+    """Random 32 B / 128 B loads over buffers from 8 MiB to 16 GiB (one line each)."""
+    import torch
+
+    import paper_2506_01576_gb300 as gi
+    gi.load()
+    dev = torch.device("cuda", 0)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    for mb in (8, 32, 64, 96, 112, 128, 160, 256, 1024, 16384):
+        buf = torch.ones(mb << 20, dtype=torch.uint8, device=dev)
+        for c in (32, 128):
+            loads = 1 << 27
+            for _ in range(2):
+                gi.gi_probe_random_sectors(buf, c, loads, 3, sink)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gi.gi_probe_random_sectors(buf, c, loads, 5, sink)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            print(json.dumps({"buffer_mib": mb, "chunk_bytes": c, "chunks_per_s": loads / ms * 1e3,
+                              "GBps": loads * c / ms / 1e6}), flush=True)
+        del buf
+
+
 if __name__ == "__main__":
     args = parse()
-    if args.impl == "reference":
+    if args.probe_sweep:
+        probe_sweep()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

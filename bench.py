@@ -161,6 +161,22 @@ def eks_bytes_per_lookup(n: int, k: int, key_bytes: int, hit_rate: float, l2_byt
     return nbytes, reqs
 
 
+def max_over_ranks(ms: float, device="cpu") -> float:
+    """The slowest rank's time: the whole job is done only when every replica is."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, steps: int, ms: float) -> float:
+    """Whole-job rate: units every rank processed over the slowest rank's time."""
+    return units_per_rank * world * steps / (ms / 1e3)
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(a):
     import torch
@@ -233,13 +249,9 @@ def run_ours(a):
     launches = gi.gi_launch_count() - l0
     if world > 1:
         dist.barrier()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(t0.elapsed_time(t1), dev if world > 1 and dist.get_backend() == "nccl" else "cpu")
     ms_step = ms / a.steps
-    value = m * world * a.steps / (ms / 1e3)
+    value = job_throughput(m, world, a.steps, ms)
     pt_ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev_pt]))
 
     # parity spot check of the timed configuration (results are integers: exact)
@@ -335,7 +347,7 @@ def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, 
     bpl, reqs = eks_bytes_per_lookup(n, a.k, 8, 0.5, l2)
     achieved = bpl * m / (pt_ms / 1e3) / 1e9
     res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                       "frac": achieved / hbm, "traffic": None,
+                       "frac": achieved / hbm, "traffic": recorded_traffic(a, m),
                        "peak_source": "measured" if peaks else "fallback",
                        "kernel": "k_eks_point", "algorithmic_bytes_per_lookup": bpl,
                        "random_requests_per_lookup": reqs, "l2_bytes": l2}
@@ -391,6 +403,30 @@ def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, 
     if not a.no_cpu:
         res["cpu_baseline"] = cpu_oracle_sample(keys, q, n, m, a)
     return res
+
+
+def recorded_traffic(a, m):
+    """DRAM bytes of one k_eks_point launch from the committed ncu summary, or None.
+
+    Valid only for the configuration it was captured on (2^26 u64 keys, k = 5,
+    2^27 probes, default knobs) and while the kernel source is unchanged.
+    """
+    import hashlib
+    if (a.layout, a.k, a.n_log, a.m_log, a.group, a.per_thread, a.smem_levels,
+            a.blocks_per_sm) != ("eks", 5, 26, 27, -1, -1, -1, -1):
+        return None
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "k_eks_point_u64_k5_2e26.md")).read()
+        rec = dict(l.split(": ", 1) for l in txt.splitlines()
+                   if l.startswith(("traffic_full_launch_bytes:", "kernel_source_sha256:")))
+        h = hashlib.sha256()
+        for f in ("gi_point_impl.cuh", "gi_eks_inst.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_2506_01576_gb300", "csrc", f), "rb").read())
+        if h.hexdigest() != rec["kernel_source_sha256"].strip():
+            return None
+        return int(rec["traffic_full_launch_bytes"])
+    except Exception:
+        return None
 
 
 def cpu_oracle_sample(keys, q, n, m, a, sort_sample=1 << 22, point_sample=1 << 21):

@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="timed steps only (for profiler launch lists)")
+    ap.add_argument("--workload", default="point", choices=["point", "batched"],
+                    help="point: the 2^26-key step (default); batched: 4096 indexes in one graph")
+    ap.add_argument("--batch-k", type=int, default=5)
+    ap.add_argument("--batch-indexes", type=int, default=4096)
     ap.add_argument("--probe-sweep", action="store_true",
                     help="print random-access throughput over buffer sizes (L2 vs HBM) and exit")
     return ap.parse_args()
@@ -532,9 +536,109 @@ def probe_sweep():
         del buf
 
 
+def run_batched(a):
+    """4096 independent indexes (2^8..2^20 u64 keys, log-uniform) with 2^10..2^18
+    probes each at hit rate 0.75: build + lookup of all of them as one CUDA graph
+    (gi_batch_*), against one gi_build + gi_point_lookup per index."""
+    import torch
+
+    import paper_2506_01576_gb300 as gi
+    gi.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(2024)
+    B = a.batch_indexes
+    sizes = np.exp2(rng.uniform(8, 20, size=B)).astype(np.int64)
+    nq = np.exp2(rng.uniform(10, 18, size=B)).astype(np.int64)
+    off = np.zeros(B + 1, dtype=np.uint64)
+    np.cumsum(sizes.astype(np.uint64), out=off[1:])
+    keys = np.concatenate([W.unique_keys(int(n), 64, W.seed_for(3, 20, i)) for i, n in enumerate(sizes)])
+    qs = []
+    for i, n in enumerate(sizes):
+        k0 = int(off[i])
+        qs.append(W.point_probes(keys[k0:k0 + int(n)], int(nq[i]), 0.75, 64, W.seed_for(3, 20, i), 17 + i))
+    q = np.concatenate(qs)
+    qoff = np.zeros(B + 1, dtype=np.uint64)
+    np.cumsum(nq.astype(np.uint64), out=qoff[1:])
+    m = int(qoff[-1])
+    kd = torch.from_numpy(keys.view(np.int64)).to(dev)
+    rd = torch.arange(len(keys), dtype=torch.int32, device=dev)
+    qd = torch.from_numpy(q.view(np.int64)).to(dev)
+    qod = torch.from_numpy(qoff.view(np.int64)).to(dev)
+    out = torch.empty(m, dtype=torch.int32, device=dev)
+    layout = gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64
+    batch = gi.gi_batch_create(off, layout, a.batch_k)
+    s = torch.cuda.Stream()
+    gi.gi_batch_set_stream(batch, s)
+    with torch.cuda.stream(s):
+        gi.gi_batch_build(batch, kd, rd)
+        gi.gi_batch_point_lookup(batch, qd, qod, out)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    c0 = gi.gi_launch_count()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        gi.gi_batch_build(batch, kd, rd)
+        gi.gi_batch_point_lookup(batch, qd, qod, out)
+    kernels_per_replay = gi.gi_launch_count() - c0  # kernel nodes captured in the graph
+
+    def ev(fn, reps):
+        with torch.cuda.stream(s):  # replays and launches both go to stream s
+            for _ in range(a.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                fn()
+            e1.record(s)
+            e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    with ClockSampler(0) as clk:
+        graph_ms = ev(lambda: g.replay(), a.steps)
+        launches = kernels_per_replay * a.steps
+    gi.gi_batch_sync(batch)
+    got = out.cpu().numpy().view(np.uint32)
+    lookup_ms = ev(lambda: gi.gi_batch_point_lookup(batch, qd, qod, out), a.steps)
+    build_ms = ev(lambda: gi.gi_batch_build(batch, kd, rd), max(2, a.steps // 2))
+    # one index at a time through the single-index API
+    gi.gi_set_stream(None, s)
+    out2 = torch.empty(m, dtype=torch.int32, device=dev)
+
+    def per_index():
+        for i in range(B):
+            k0, k1 = int(off[i]), int(off[i + 1])
+            q0, q1 = int(qoff[i]), int(qoff[i + 1])
+            idx = gi.gi_build(kd[k0:k1], rd[k0:k1], layout, a.batch_k)
+            gi.gi_point_lookup(idx, qd[q0:q1], out2[q0:q1])
+            gi.gi_destroy(idx)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    per_index()
+    torch.cuda.synchronize()
+    per_ms = (time.perf_counter() - t0) * 1e3
+    same = bool(np.array_equal(got, out2.cpu().numpy().view(np.uint32)))
+    gi.gi_set_stream(None, None)
+    print(json.dumps({
+        "metric": "batched lookups/s (%d indexes, 2^8..2^20 u64 keys, 2^10..2^18 probes each, hit 0.75)" % B,
+        "value": m / (graph_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": graph_ms, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "batched build + lookup, one CUDA graph", "indexes": B,
+                   "keys_total": int(off[-1]), "probes_total": m, "k": a.batch_k},
+        "graph_step_ms": graph_ms, "build_ms": build_ms, "lookup_ms": lookup_ms,
+        "lookup_only_per_s": m / (lookup_ms / 1e3),
+        "per_index_launches_ms": per_ms, "speedup_vs_per_index": per_ms / graph_ms,
+        "per_index_results_identical": same, "gpu_launches": int(launches),
+        "clocks": clk.summary()}), flush=True)
+    gi.gi_batch_destroy(batch)
+
+
 if __name__ == "__main__":
     args = parse()
-    if args.probe_sweep:
+    if args.workload == "batched":
+        run_batched(args)
+    elif args.probe_sweep:
         probe_sweep()
     elif args.impl == "reference":
         run_reference(args)

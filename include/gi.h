@@ -213,6 +213,50 @@ int gi_coalescing_probe(const uint32_t* buf, uint64_t entries, uint32_t threads,
                         void* stream);
 
 /*
+ * Batched form: B independent indexes of uneven size, built and probed together.
+ * The paper evaluates one index at a time; this form serves many small indexes
+ * (e.g. one per partition of a join) with one launch per phase instead of one per
+ * index.  Index b holds pairs key_offsets[b] .. key_offsets[b+1]-1 of the
+ * concatenated key/rowID arrays.  Layouts: GI_EYTZINGER_KARY with k in
+ * {3, 5, 9, 17}, or GI_SORTED; either key width.
+ *
+ * gi_batch_create -- sizes and allocates all device memory of the batch from the
+ *   HOST array key_offsets[B+1] (key_offsets[0] = 0, non-decreasing, each index
+ *   below 2^31 keys) and uploads the tile tables.  Synchronous.
+ * gi_batch_build -- segmented radix sort of all pairs (no pair leaves its index)
+ *   and the per-index closed-form permutation (Sections 4, 6.1).  keys/rowids:
+ *   DEVICE memory.  Asynchronous on the batch's stream, no allocation and no host
+ *   synchronisation, so it can be captured in a CUDA graph.  Errors found on the
+ *   device (reserved rowID, a bounded wait that gave up) come back from gi_batch_sync.
+ * gi_batch_point_lookup -- one persistent launch over (index, chunk of probes).
+ *   queries: DEVICE, m probes; index b's probes are
+ *   queries[query_offsets[b] .. query_offsets[b+1]); query_offsets: DEVICE array of
+ *   B+1 uint64 with query_offsets[B] = m; out_rowids: DEVICE, m uint32 (rowID or
+ *   GI_MISS).  Each CTA pins the top levels of the index it serves in shared memory
+ *   (a bulk asynchronous copy; whole small indexes), up to a per-CTA budget.
+ *   Asynchronous, no allocation, capturable.
+ * gi_batch_copy_index -- copy index b's arrays in layout order (device or host).
+ * gi_batch_set_option -- GI_BATCH_OPT_CHUNK (probes per work item, default 1024),
+ *   GI_BATCH_OPT_BLOCKS_PER_SM (default 4), GI_BATCH_OPT_SMEM_BUDGET (bytes of
+ *   pinned levels per CTA, 0..40960, default 16384).
+ */
+typedef struct gi_batch gi_batch;
+#define GI_BATCH_OPT_CHUNK         1
+#define GI_BATCH_OPT_BLOCKS_PER_SM 2
+#define GI_BATCH_OPT_SMEM_BUDGET   3
+int gi_batch_create(const uint64_t* key_offsets, uint32_t B, int layout, uint32_t k,
+                    gi_batch** out);
+int gi_batch_set_stream(gi_batch* batch, void* stream);
+int gi_batch_build(gi_batch* batch, const void* keys, const uint32_t* rowids);
+int gi_batch_point_lookup(gi_batch* batch, const void* queries, const uint64_t* query_offsets,
+                          uint64_t m, uint32_t* out_rowids);
+int gi_batch_sync(gi_batch* batch);
+int gi_batch_copy_index(const gi_batch* batch, uint32_t i, void* keys_out, uint32_t* rowids_out);
+int gi_batch_set_option(gi_batch* batch, int option, int64_t value);
+uint64_t gi_batch_footprint_bytes(const gi_batch* batch);
+void gi_batch_destroy(gi_batch* batch);
+
+/*
  * gi_range_lookup_noalloc -- gi_range_lookup for callers that must not allocate.
  * The paper has no counterpart: this entry point exists for users whose device
  * memory is owned by someone else (a query engine or framework that hands the

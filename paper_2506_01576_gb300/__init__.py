@@ -28,6 +28,9 @@ __all__ = [
     "gi_last_error", "gi_footprint_bytes", "gi_get_info", "gi_copy_layout", "gi_set_option", "gi_get_option",
     "gi_probe_random_sectors", "gi_coalescing_probe", "gi_launch_count",
     "gi_range_lookup_noalloc", "GI_NOALLOC_MAX_RANGES",
+    "Batch", "gi_batch_create", "gi_batch_set_stream", "gi_batch_build", "gi_batch_point_lookup",
+    "gi_batch_sync", "gi_batch_copy_index", "gi_batch_set_option", "gi_batch_footprint_bytes",
+    "gi_batch_destroy", "GI_BATCH_OPT_CHUNK", "GI_BATCH_OPT_BLOCKS_PER_SM", "GI_BATCH_OPT_SMEM_BUDGET",
 ]
 
 GI_SORTED, GI_EYTZINGER, GI_EYTZINGER_KARY = 0, 1, 2
@@ -35,6 +38,7 @@ GI_KEY_U32, GI_KEY_U64 = 0x000, 0x100
 GI_OK, GI_ERR_INVALID, GI_ERR_NOMEM, GI_ERR_CUDA, GI_ERR_TIMEOUT = 0, 1, 2, 3, 4
 GI_MISS = 0xFFFFFFFF
 GI_NOALLOC_MAX_RANGES = 1 << 20
+GI_BATCH_OPT_CHUNK, GI_BATCH_OPT_BLOCKS_PER_SM, GI_BATCH_OPT_SMEM_BUDGET = 1, 2, 3
 (GI_OPT_GROUP, GI_OPT_PER_THREAD, GI_OPT_SMEM_LEVELS, GI_OPT_BLOCK, GI_OPT_BLOCKS_PER_SM,
  GI_OPT_PREFETCH, GI_OPT_EARLY_EXIT, GI_OPT_HOT_LEVELS) = range(1, 9)
 
@@ -86,6 +90,15 @@ def load(build_if_missing: bool = False):
         "gi_coalescing_probe": (I, [P, U64, U32, U32, U32, U64, P, P]),
         "gi_launch_count": (U64, []),
         "gi_range_lookup_noalloc": (I, [P, P, P, U64, P, P]),
+        "gi_batch_create": (I, [P, ctypes.c_uint32, I, U32, ctypes.POINTER(P)]),
+        "gi_batch_set_stream": (I, [P, P]),
+        "gi_batch_build": (I, [P, P, P]),
+        "gi_batch_point_lookup": (I, [P, P, P, U64, P]),
+        "gi_batch_sync": (I, [P]),
+        "gi_batch_copy_index": (I, [P, U32, P, P]),
+        "gi_batch_set_option": (I, [P, I, I64]),
+        "gi_batch_footprint_bytes": (U64, [P]),
+        "gi_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -195,6 +208,73 @@ def gi_range_lookup_noalloc(index: Index, lo, hi, out_offsets, out_rowids=None) 
         raise ValueError("lo/hi lengths differ or out_offsets is shorter than m+1")
     _check(load().gi_range_lookup_noalloc(index.handle, _ptr(lo), _ptr(hi), m, _ptr(out_offsets),
                                           _ptr(out_rowids)))
+
+
+class Batch:
+    """Handle of a batch of indexes (owns the C gi_batch*)."""
+
+    def __init__(self, handle: int, B: int):
+        self._h = handle
+        self.B = B
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise GIError(GI_ERR_INVALID, "batch was destroyed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().gi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gi_batch_create(key_offsets, layout: int, k: int = 0) -> Batch:
+    """key_offsets: host uint64 array of B+1 offsets into the concatenated pairs."""
+    import numpy as np
+    ko = np.ascontiguousarray(key_offsets, dtype=np.uint64)
+    out = ctypes.c_void_p()
+    _check(load().gi_batch_create(_ptr(ko), len(ko) - 1, layout, k, ctypes.byref(out)))
+    return Batch(out.value, len(ko) - 1)
+
+
+def gi_batch_set_stream(batch: Batch, stream) -> None:
+    _check(load().gi_batch_set_stream(batch.handle, _stream_handle(stream)))
+
+
+def gi_batch_build(batch: Batch, keys, rowids) -> None:
+    _check(load().gi_batch_build(batch.handle, _ptr(keys), _ptr(rowids)))
+
+
+def gi_batch_point_lookup(batch: Batch, queries, query_offsets, out_rowids) -> None:
+    _check(load().gi_batch_point_lookup(batch.handle, _ptr(queries), _ptr(query_offsets),
+                                        _len(queries), _ptr(out_rowids)))
+
+
+def gi_batch_sync(batch: Batch) -> None:
+    _check(load().gi_batch_sync(batch.handle))
+
+
+def gi_batch_copy_index(batch: Batch, i: int, keys_out=None, rowids_out=None) -> None:
+    _check(load().gi_batch_copy_index(batch.handle, i, _ptr(keys_out), _ptr(rowids_out)))
+
+
+def gi_batch_set_option(batch: Batch, option: int, value: int) -> None:
+    _check(load().gi_batch_set_option(batch.handle, option, value))
+
+
+def gi_batch_footprint_bytes(batch: Batch) -> int:
+    return int(load().gi_batch_footprint_bytes(batch.handle))
+
+
+def gi_batch_destroy(batch: Batch) -> None:
+    batch.close()
 
 
 def gi_destroy(index: Index) -> None:

@@ -230,6 +230,8 @@ namespace gi {
 
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+void set_last_error(const char* msg) { t_err = msg; }
+
 int sm_count() {
   static int cached[64];
   static std::once_flag once[64];

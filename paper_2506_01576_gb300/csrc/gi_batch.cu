@@ -1,0 +1,534 @@
+// Batched form: thousands of independent indexes of uneven size, built and
+// probed together.
+//
+// gi_batch_create sizes and allocates everything once from the host-side key
+// offsets (tile tables, sort buffers, the padded index arrays, per-index
+// descriptors), so gi_batch_build and gi_batch_point_lookup launch kernels only:
+// no allocation, no host synchronisation.  The sequence can be captured in a
+// CUDA graph and replayed.
+//
+//   build : one segmented radix sort over the concatenated pairs (gi_sort.cu:
+//           each tile stays inside its index; look-back stops at the index's
+//           first tile), then the per-index closed-form permutation into a padded
+//           per-index region (max-key padding after every index, 256-byte
+//           aligned starts).
+//   lookup: one persistent launch over (index, chunk of probes) work items.  A
+//           CTA takes a work item, copies the top levels of that index that fit
+//           in its shared-memory budget with one bulk asynchronous copy
+//           (mbarrier, bounded wait), then every thread runs the k-ary descent
+//           for its probes, reading pinned levels from shared memory and the
+//           rest from global memory.  The pinned depth is chosen per index by
+//           its size (small indexes are pinned whole).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "gi_internal.cuh"
+#include "gi_point_impl.cuh"
+
+namespace gi {
+
+struct BatchDesc {
+  uint64_t base;         // slot 0 of the index in the padded arrays
+  uint64_t n;            // keys
+  uint32_t levels;       // tree levels (k-ary) / 0 for sorted
+  uint32_t smem_levels;  // top levels pinned in shared memory for this index
+  uint32_t smem_slots;   // slots copied to shared memory (0: none)
+  uint32_t pad;
+};
+
+namespace bt {
+
+// Work item w -> index b: the last b with chunk_start[b] <= w.
+__device__ __forceinline__ uint32_t find_index(const uint64_t* cs, uint32_t B, uint64_t w) {
+  uint32_t lo = 0, hi = B;  // cs[lo] <= w < cs[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (cs[mid] <= w) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// chunk_start[b] = sum over c < b of ceil(probes of c / CH); one CTA, any B
+__global__ void __launch_bounds__(1024) k_chunk_starts(const uint64_t* __restrict__ qoff, uint32_t B,
+                                                       uint32_t CH, uint64_t* __restrict__ cs) {
+  __shared__ uint64_t s_warp[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t carry = 0;
+  for (uint64_t base = 0; base < B; base += blockDim.x) {
+    const uint64_t b = base + threadIdx.x;
+    const uint64_t v = b < B ? (qoff[b + 1] - qoff[b] + CH - 1) / CH : 0;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    uint64_t pre = 0, tot = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      if (i < w) pre += s_warp[i];
+      tot += s_warp[i];
+    }
+    if (b < B) cs[b] = carry + pre + x - v;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cs[B] = carry;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (uint32_t spin = 0; spin < kSpinLimit && !done; ++spin) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+template <class K, int KF>
+__device__ __forceinline__ uint32_t eks_one(const K* __restrict__ keys, const uint32_t* __restrict__ rows,
+                                            const BatchDesc& d, const K* sm, K x) {
+  constexpr int N = KF - 1;
+  uint64_t s = 0, cand = ~0ull;
+  const K* base = keys + d.base;
+  for (uint32_t lv = 0; lv < d.levels; ++lv) {
+    if (s >= d.n) break;
+    K piv[N];
+    if (lv < d.smem_levels) {
+#pragma unroll
+      for (int p = 0; p < N; ++p) piv[p] = sm[s + p];
+    } else if constexpr (pt::EksShape<K, KF, 1>::VEC) {
+      pt::vec_load<K, N>(base + s, piv);
+    } else {
+#pragma unroll
+      for (int p = 0; p < N; ++p) piv[p] = __ldg(base + s + p);
+    }
+    uint32_t c = 0;
+#pragma unroll
+    for (int p = 0; p < N; ++p) c += piv[p] < x ? 1u : 0u;
+    if (c < (uint32_t)N && s + c < d.n) cand = s + c;
+    s = s * KF + (uint64_t)(c + 1) * N;
+  }
+  if (cand != ~0ull && __ldg(base + cand) == x) return __ldg(rows + d.base + cand);
+  return GI_MISS;
+}
+
+template <class K>
+__device__ __forceinline__ uint32_t bs_one(const K* __restrict__ keys, const uint32_t* __restrict__ rows,
+                                           const BatchDesc& d, K x) {
+  const K* base = keys + d.base;
+  uint64_t lo = 0, len = d.n;
+  while (len > 0) {
+    const uint64_t half = len >> 1;
+    if (base[lo + half] < x) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  return (lo < d.n && base[lo] == x) ? rows[d.base + lo] : GI_MISS;
+}
+
+// KF == 0: sorted layout (binary search per index, no pinning)
+template <class K, int KF>
+__global__ void __launch_bounds__(256) k_batch_point(const K* __restrict__ keys,
+                                                     const uint32_t* __restrict__ rows,
+                                                     const BatchDesc* __restrict__ desc,
+                                                     const uint64_t* __restrict__ qoff,
+                                                     const uint64_t* __restrict__ cs, uint32_t B,
+                                                     const K* __restrict__ q,
+                                                     uint32_t* __restrict__ out, uint32_t CH,
+                                                     uint32_t* __restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t s_b;
+  const K* sm = (const K*)smem_raw;
+  const uint32_t bar = pt::smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  bool in_flight = false, ok = true;
+  const uint64_t total = cs[B];
+  for (uint64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    if (threadIdx.x == 0) s_b = find_index(cs, B, w);
+    __syncthreads();
+    const uint32_t b = s_b;
+    const BatchDesc d = desc[b];
+    const uint64_t q0 = qoff[b] + (w - cs[b]) * CH;
+    const uint64_t q1 = min(q0 + CH, qoff[b + 1]);
+    bool staged = true;
+    if (KF > 0 && d.smem_slots) {
+      const uint32_t bytes = (uint32_t)(((uint64_t)d.smem_slots * sizeof(K) + 15) & ~15ull);
+      if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+                "r"(pt::smem_u32(smem_raw)),
+            "l"(keys + d.base), "r"(bytes), "r"(bar)
+            : "memory");
+      }
+      const bool landed = mbar_wait(bar, phase & 1);
+      phase ^= 1;
+      // every thread takes the same decision (a partial timeout must not split the CTA)
+      staged = !__syncthreads_or(!landed);
+      if (!staged) {
+        in_flight = !landed;
+        ok = false;
+        if (threadIdx.x == 0) atomicOr(flags, kFlagTimeout);
+      }
+    }
+    if (staged) {
+      for (uint64_t i = q0 + threadIdx.x; i < q1; i += blockDim.x) {
+        const K x = q[i];
+        if constexpr (KF > 0)
+          out[i] = eks_one<K, KF>(keys, rows, d, sm, x);
+        else
+          out[i] = bs_one<K>(keys, rows, d, x);
+      }
+    }
+    __syncthreads();  // the staging buffer is reused by the next work item
+    if (!ok) break;
+  }
+  if (in_flight) mbar_wait(bar, phase & 1);  // a copy still in flight: let it land (bounded)
+}
+
+}  // namespace bt
+}  // namespace gi
+
+// ---------------------------------------------------------------- host side
+struct gi_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  uint32_t B = 0;
+  int layout = GI_EYTZINGER_KARY;
+  uint32_t k = 0;
+  int key_bytes = 8;
+  uint64_t n = 0;
+  std::vector<uint64_t> key_off;  // host copy, B+1
+  std::vector<gi::BatchDesc> desc_host;
+  uint64_t* d_seg_start = nullptr;
+  uint64_t* d_seg_base = nullptr;
+  gi::BatchDesc* d_desc = nullptr;
+  gi::BatchTile* d_tiles = nullptr;
+  uint64_t ntiles = 0;
+  gi::BatchTile* d_chunks = nullptr;
+  uint64_t nchunks = 0;
+  void* keys = nullptr;
+  uint32_t* rows = nullptr;
+  size_t keys_bytes = 0;
+  void* tmp_k[2] = {nullptr, nullptr};
+  uint32_t* tmp_v[2] = {nullptr, nullptr};
+  void* scratch = nullptr;
+  uint32_t* dflags = nullptr;
+  uint64_t* d_cs = nullptr;  // B+1 chunk starts of the last lookup
+  int result = -1;
+  uint32_t chunk = 1024;       // probes per work item
+  uint32_t smem_budget = 16384;  // bytes of pinned levels per CTA
+  int blocks_per_sm = 4;
+};
+
+namespace {
+int bfail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  gi::set_last_error(buf);
+  return code;
+}
+
+int bcuda(cudaError_t e, const char* what) {
+  cudaGetLastError();
+  return bfail(e == cudaErrorMemoryAllocation ? GI_ERR_NOMEM : GI_ERR_CUDA, "%s: %s", what,
+               cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool batch_kernel_k(uint32_t k) { return k == 3 || k == 5 || k == 9 || k == 17; }
+
+// per-index pinning: the top levels whose slots fit in the budget (whole index if small)
+void choose_pinning(gi::BatchDesc& d, uint32_t k, int key_bytes, uint32_t budget) {
+  d.smem_levels = 0;
+  d.smem_slots = 0;
+  if (d.n == 0 || k < 2) return;
+  uint64_t slots = 0, width = k - 1;
+  for (uint32_t l = 0; l < d.levels; ++l) {
+    const uint64_t next = slots + width;  // k^(l+1) - 1 slots: whole levels 0..l
+    const uint64_t need = std::min<uint64_t>(next, (d.n + k - 2) / (k - 1) * (k - 1));
+    if (need * key_bytes > budget) break;
+    slots = next;
+    d.smem_levels = l + 1;
+    d.smem_slots = (uint32_t)need;
+    if (need >= d.n) break;
+    width *= k;
+  }
+}
+
+void free_batch(gi_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  void* ptrs[] = {b->d_seg_start, b->d_seg_base, b->d_desc, b->d_tiles, b->d_chunks, b->keys,
+                  b->rows, b->tmp_k[0], b->tmp_k[1], b->tmp_v[0], b->tmp_v[1], b->scratch,
+                  b->dflags, b->d_cs};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  cudaGetLastError();
+  delete b;
+}
+}  // namespace
+
+extern "C" {
+
+int gi_batch_create(const uint64_t* key_offsets, uint32_t B, int layout, uint32_t k, gi_batch** out) {
+  gi::set_last_error("");
+  if (!out) return bfail(GI_ERR_INVALID, "gi_batch_create: out is NULL");
+  *out = nullptr;
+  if (!key_offsets || B == 0) return bfail(GI_ERR_INVALID, "gi_batch_create: need B >= 1 and key offsets");
+  const int lay = layout & 0xFF, kw = layout & ~0xFF;
+  if (kw != GI_KEY_U32 && kw != GI_KEY_U64) return bfail(GI_ERR_INVALID, "gi_batch_create: bad key width");
+  if (lay == GI_EYTZINGER_KARY) {
+    if (!batch_kernel_k(k)) return bfail(GI_ERR_INVALID, "gi_batch_create: k must be 3, 5, 9 or 17");
+  } else if (lay == GI_SORTED) {
+    k = 0;
+  } else {
+    return bfail(GI_ERR_INVALID, "gi_batch_create: layout must be GI_EYTZINGER_KARY or GI_SORTED");
+  }
+  if (key_offsets[0] != 0) return bfail(GI_ERR_INVALID, "gi_batch_create: key_offsets[0] must be 0");
+  for (uint32_t i = 0; i < B; ++i) {
+    if (key_offsets[i + 1] < key_offsets[i])
+      return bfail(GI_ERR_INVALID, "gi_batch_create: key offsets decrease at %u", i);
+    if (key_offsets[i + 1] - key_offsets[i] >= (1ull << 31))
+      return bfail(GI_ERR_INVALID, "gi_batch_create: index %u has 2^31 keys or more", i);
+  }
+  gi_batch* b = new gi_batch();
+  cudaGetDevice(&b->device);
+  b->B = B;
+  b->layout = lay;
+  b->k = k;
+  b->key_bytes = kw == GI_KEY_U64 ? 8 : 4;
+  b->key_off.assign(key_offsets, key_offsets + B + 1);
+  b->n = key_offsets[B];
+  const int kb = b->key_bytes;
+  // padded, 256-byte aligned region per index, >= 64 max-key slots after each
+  const uint64_t align_slots = 256 / kb;
+  std::vector<uint64_t> base(B);
+  uint64_t cur = 0;
+  b->desc_host.resize(B);
+  for (uint32_t i = 0; i < B; ++i) {
+    const uint64_t n = key_offsets[i + 1] - key_offsets[i];
+    base[i] = cur;
+    cur += (n + 64 + align_slots - 1) / align_slots * align_slots;
+    gi::BatchDesc& d = b->desc_host[i];
+    d = gi::BatchDesc{};
+    d.base = base[i];
+    d.n = n;
+    if (lay == GI_EYTZINGER_KARY) {
+      d.levels = gi::make_geom(n, k).levels;
+      choose_pinning(d, k, kb, b->smem_budget);
+    }
+  }
+  const uint64_t slots_total = cur + align_slots;
+  // tiles (radix) and chunks (histogram), host-built once
+  const uint32_t tile = gi::batch_sort_tile(kb);
+  std::vector<gi::BatchTile> tiles, chunks;
+  for (uint32_t i = 0; i < B; ++i) {
+    const uint64_t s0 = key_offsets[i], n = key_offsets[i + 1] - s0;
+    for (uint64_t t = 0, l = 0; t < n; t += tile, ++l)
+      tiles.push_back(gi::BatchTile{s0 + t, i, (uint32_t)std::min<uint64_t>(tile, n - t), (uint32_t)l, 0});
+    for (uint64_t t = 0, l = 0; t < n; t += gi::kBatchChunk, ++l)
+      chunks.push_back(gi::BatchTile{s0 + t, i, (uint32_t)std::min<uint64_t>(gi::kBatchChunk, n - t), (uint32_t)l, 0});
+  }
+  b->ntiles = tiles.size();
+  b->nchunks = chunks.size();
+  auto bail = [&](int rc) {
+    free_batch(b);
+    return rc;
+  };
+#define GI_B(call, what)                                      \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return bail(bcuda(e_, what));      \
+  } while (0)
+  b->keys_bytes = slots_total * kb;
+  GI_B(cudaMalloc(&b->keys, b->keys_bytes), "batch keys");
+  GI_B(cudaMalloc((void**)&b->rows, slots_total * 4), "batch rows");
+  for (int i = 0; i < 2; ++i) {
+    GI_B(cudaMalloc(&b->tmp_k[i], (b->n + 64) * kb), "batch sort buffer");
+    GI_B(cudaMalloc((void**)&b->tmp_v[i], (b->n + 64) * 4), "batch sort buffer");
+  }
+  GI_B(cudaMalloc(&b->scratch, gi::batch_sort_scratch_bytes(b->ntiles, B, kb)), "batch sort scratch");
+  GI_B(cudaMalloc((void**)&b->d_seg_start, (B + 1) * 8), "batch tables");
+  GI_B(cudaMalloc((void**)&b->d_seg_base, B * 8), "batch tables");
+  GI_B(cudaMalloc((void**)&b->d_desc, B * sizeof(gi::BatchDesc)), "batch tables");
+  GI_B(cudaMalloc((void**)&b->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(gi::BatchTile)), "batch tables");
+  GI_B(cudaMalloc((void**)&b->d_chunks, std::max<size_t>(1, chunks.size()) * sizeof(gi::BatchTile)), "batch tables");
+  GI_B(cudaMalloc((void**)&b->d_cs, (B + 1) * 8), "batch tables");
+  GI_B(cudaMalloc((void**)&b->dflags, 256), "batch status");
+  GI_B(cudaMemset(b->dflags, 0, 256), "batch status");
+  GI_B(cudaMemcpy(b->d_seg_start, key_offsets, (B + 1) * 8, cudaMemcpyHostToDevice), "batch tables");
+  GI_B(cudaMemcpy(b->d_seg_base, base.data(), B * 8, cudaMemcpyHostToDevice), "batch tables");
+  GI_B(cudaMemcpy(b->d_desc, b->desc_host.data(), B * sizeof(gi::BatchDesc), cudaMemcpyHostToDevice), "batch tables");
+  if (!tiles.empty())
+    GI_B(cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(gi::BatchTile), cudaMemcpyHostToDevice), "batch tables");
+  if (!chunks.empty())
+    GI_B(cudaMemcpy(b->d_chunks, chunks.data(), chunks.size() * sizeof(gi::BatchTile), cudaMemcpyHostToDevice), "batch tables");
+  // the shared-memory budget stays below 48 KB (option bound), so launches need no
+  // attribute change and can be captured in a graph
+#undef GI_B
+  *out = b;
+  return GI_OK;
+}
+
+int gi_batch_set_stream(gi_batch* b, void* stream) {
+  gi::set_last_error("");
+  if (!b) return bfail(GI_ERR_INVALID, "gi_batch_set_stream: NULL batch");
+  b->stream = (cudaStream_t)stream;
+  return GI_OK;
+}
+
+int gi_batch_build(gi_batch* b, const void* keys, const uint32_t* rowids) {
+  gi::set_last_error("");
+  if (!b) return bfail(GI_ERR_INVALID, "gi_batch_build: NULL batch");
+  if (b->n && (!is_device_ptr(keys) || !is_device_ptr(rowids)))
+    return bfail(GI_ERR_INVALID, "gi_batch_build: keys and rowids must be device memory");
+  cudaStream_t s = b->stream;
+  cudaError_t e = gi::batch_sort(keys, rowids, b->tmp_k, b->tmp_v, b->n, b->key_bytes, b->d_seg_start,
+                                 b->B, b->d_tiles, b->ntiles, b->d_chunks, b->nchunks, b->scratch,
+                                 b->dflags, s, &b->result);
+  if (e != cudaSuccess) return bcuda(e, "gi_batch_build: sort");
+  e = cudaMemsetAsync(b->keys, 0xFF, b->keys_bytes, s);  // max-key padding after every index
+  if (e != cudaSuccess) return bcuda(e, "gi_batch_build: padding");
+  if (b->result >= 0) {
+    e = gi::batch_gather(b->tmp_k[b->result], b->tmp_v[b->result], b->keys, b->rows, b->d_tiles,
+                         b->ntiles, b->d_seg_start, b->d_seg_base, b->k, b->key_bytes, b->dflags, s);
+    if (e != cudaSuccess) return bcuda(e, "gi_batch_build: permutation");
+  }
+  return GI_OK;
+}
+
+int gi_batch_point_lookup(gi_batch* b, const void* queries, const uint64_t* query_offsets, uint64_t m,
+                          uint32_t* out_rowids) {
+  gi::set_last_error("");
+  if (!b) return bfail(GI_ERR_INVALID, "gi_batch_point_lookup: NULL batch");
+  if (m == 0) return GI_OK;
+  if (!is_device_ptr(queries) || !is_device_ptr(query_offsets) || !is_device_ptr(out_rowids))
+    return bfail(GI_ERR_INVALID, "gi_batch_point_lookup: queries, offsets and output must be device memory");
+  cudaStream_t s = b->stream;
+  gi::bt::k_chunk_starts<<<1, 1024, 0, s>>>(query_offsets, b->B, b->chunk, b->d_cs);
+  const unsigned grid = (unsigned)(gi::sm_count() * b->blocks_per_sm);
+  const size_t smem = b->layout == GI_EYTZINGER_KARY ? b->smem_budget + 256 : 0;
+#define GI_BP(K, KF)                                                                           \
+  gi::bt::k_batch_point<K, KF><<<grid, 256, smem, s>>>((const K*)b->keys, b->rows, b->d_desc, \
+                                                       query_offsets, b->d_cs, b->B,         \
+                                                       (const K*)queries, out_rowids, b->chunk, \
+                                                       b->dflags)
+  if (b->key_bytes == 8) {
+    switch (b->k) {
+      case 0: GI_BP(uint64_t, 0); break;
+      case 3: GI_BP(uint64_t, 3); break;
+      case 5: GI_BP(uint64_t, 5); break;
+      case 9: GI_BP(uint64_t, 9); break;
+      default: GI_BP(uint64_t, 17); break;
+    }
+  } else {
+    switch (b->k) {
+      case 0: GI_BP(uint32_t, 0); break;
+      case 3: GI_BP(uint32_t, 3); break;
+      case 5: GI_BP(uint32_t, 5); break;
+      case 9: GI_BP(uint32_t, 9); break;
+      default: GI_BP(uint32_t, 17); break;
+    }
+  }
+#undef GI_BP
+  gi::count_launch(2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bcuda(e, "gi_batch_point_lookup");
+  return GI_OK;
+}
+
+int gi_batch_sync(gi_batch* b) {
+  gi::set_last_error("");
+  if (!b) return bfail(GI_ERR_INVALID, "gi_batch_sync: NULL batch");
+  uint32_t f = 0;
+  cudaError_t e = cudaMemcpyAsync(&f, b->dflags, 4, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "gi_batch_sync");
+  if (f & gi::kFlagTimeout) return bfail(GI_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  if (f & gi::kFlagReservedRowid) return bfail(GI_ERR_INVALID, "a rowID equals the reserved value GI_MISS");
+  return GI_OK;
+}
+
+int gi_batch_copy_index(const gi_batch* b, uint32_t i, void* keys_out, uint32_t* rowids_out) {
+  gi::set_last_error("");
+  if (!b || i >= b->B) return bfail(GI_ERR_INVALID, "gi_batch_copy_index: bad batch or index");
+  const gi::BatchDesc& d = b->desc_host[i];
+  cudaError_t e = cudaSuccess;
+  if (keys_out && d.n)
+    e = cudaMemcpyAsync(keys_out, (const char*)b->keys + d.base * b->key_bytes, d.n * b->key_bytes,
+                        cudaMemcpyDefault, b->stream);
+  if (e == cudaSuccess && rowids_out && d.n)
+    e = cudaMemcpyAsync(rowids_out, b->rows + d.base, d.n * 4, cudaMemcpyDefault, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "gi_batch_copy_index");
+  return GI_OK;
+}
+
+int gi_batch_set_option(gi_batch* b, int option, int64_t v) {
+  gi::set_last_error("");
+  if (!b) return bfail(GI_ERR_INVALID, "gi_batch_set_option: NULL batch");
+  switch (option) {
+    case GI_BATCH_OPT_CHUNK:
+      if (v < 32 || v > (1 << 20)) return bfail(GI_ERR_INVALID, "chunk must be in [32, 2^20]");
+      b->chunk = (uint32_t)v;
+      return GI_OK;
+    case GI_BATCH_OPT_BLOCKS_PER_SM:
+      if (v < 1 || v > 32) return bfail(GI_ERR_INVALID, "blocks per SM must be in [1, 32]");
+      b->blocks_per_sm = (int)v;
+      return GI_OK;
+    case GI_BATCH_OPT_SMEM_BUDGET: {
+      if (v < 0 || v > 40 * 1024) return bfail(GI_ERR_INVALID, "shared-memory budget must be in [0, 40 KiB]");
+      b->smem_budget = (uint32_t)v;
+      for (uint32_t i = 0; i < b->B; ++i) choose_pinning(b->desc_host[i], b->k, b->key_bytes, b->smem_budget);
+      cudaError_t e = cudaMemcpy(b->d_desc, b->desc_host.data(), b->B * sizeof(gi::BatchDesc),
+                                 cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return bcuda(e, "gi_batch_set_option");
+      return GI_OK;
+    }
+  }
+  return bfail(GI_ERR_INVALID, "gi_batch_set_option: unknown option %d", option);
+}
+
+uint64_t gi_batch_footprint_bytes(const gi_batch* b) {
+  return b ? b->n * (uint64_t)(b->key_bytes + 4) : 0;
+}
+
+void gi_batch_destroy(gi_batch* b) { free_batch(b); }
+
+}  // extern "C"

@@ -113,6 +113,7 @@ __host__ __device__ __forceinline__ uint64_t rank_to_slot(uint64_t r, const Geom
 
 // ---------------------------------------------------------------- launch bookkeeping
 void count_launch(uint64_t n = 1);
+void set_last_error(const char* msg);  // the thread's gi_last_error() text
 int sm_count();
 int device_max_smem_optin();
 
@@ -137,6 +138,30 @@ cudaError_t layout_gather(const void* sk, const uint32_t* sv, void* dk, uint32_t
                           cudaStream_t s);
 cudaError_t check_sorted_dups(const void* sk, uint64_t n, int key_bytes, uint32_t* dflags,
                               cudaStream_t s);
+
+// Batched build of many independent indexes (gi_sort.cu).  Inputs are the
+// concatenation of all indexes' pairs; seg_start[s] .. seg_start[s+1] is index s.
+struct BatchTile {
+  uint64_t start;   // first element (global position in the concatenated input)
+  uint32_t seg;     // index the tile belongs to
+  uint32_t count;   // elements in the tile
+  uint32_t local;   // tile number within its index
+  uint32_t pad;
+};
+constexpr uint32_t kBatchChunk = 65536;  // elements per histogram work item
+uint32_t batch_sort_tile(int key_bytes);  // elements per radix tile
+size_t batch_sort_scratch_bytes(uint64_t ntiles, uint32_t nseg, int key_bytes);
+// hist/offsets/status/counters live in `scratch` (batch_sort_scratch_bytes); no host sync
+cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], uint32_t* tmp_v[2],
+                       uint64_t n, int key_bytes, const uint64_t* seg_start, uint32_t nseg,
+                       const BatchTile* tiles, uint64_t ntiles, const BatchTile* chunks,
+                       uint64_t nchunks, void* scratch, uint32_t* dflags, cudaStream_t s,
+                       int* result_buf);
+// permute every index into k-ary order (k = 0: sorted) at out + seg_base[s]
+cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t* ov,
+                         const BatchTile* tiles, uint64_t ntiles, const uint64_t* seg_start,
+                         const uint64_t* seg_base, uint32_t k, int key_bytes, uint32_t* dflags,
+                         cudaStream_t s);
 
 // Point lookups (gi_point.cu).
 struct LookupCfg {

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "gi_internal.cuh"
 
 namespace gi {
@@ -337,6 +339,265 @@ inline int grid_for(uint64_t work, int block, int per_sm = 8) {
   return (int)(want < cap ? (want ? want : 1) : cap);
 }
 
+// ================================================================= batched form
+// Many independent indexes sorted at once.  Every tile belongs to one index; the
+// look-back stops at its index's first tile, and each index has its own digit
+// offsets, so keys never leave their index (a segmented LSD sort).
+
+template <class K>
+__global__ void __launch_bounds__(256) k_batch_histogram(const K* __restrict__ keys,
+                                                         const uint32_t* __restrict__ rows,
+                                                         const BatchTile* __restrict__ chunks,
+                                                         uint64_t nchunks,
+                                                         unsigned long long* __restrict__ hist,
+                                                         uint32_t* __restrict__ flags) {
+  constexpr int P = sizeof(K);
+  __shared__ uint32_t sh[P][kRadix];
+  bool bad = false;
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const BatchTile t = chunks[c];
+    for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < t.count; i += blockDim.x) {
+      const K key = keys[t.start + i];
+#pragma unroll
+      for (int p = 0; p < P; ++p) atomicAdd(&sh[p][(uint32_t)(key >> (8 * p)) & 0xFF], 1u);
+      bad |= rows[t.start + i] == GI_MISS;
+    }
+    __syncthreads();
+    unsigned long long* h = hist + (uint64_t)t.seg * P * kRadix;
+    for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) {
+      const uint32_t v = (&sh[0][0])[i];
+      if (v) atomicAdd(&h[i], (unsigned long long)v);
+    }
+    __syncthreads();
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagReservedRowid);
+}
+
+// one CTA per index: exclusive digit scans of every pass, offset by the index start
+__global__ void __launch_bounds__(256) k_batch_scan_hist(const unsigned long long* __restrict__ hist,
+                                                         unsigned long long* __restrict__ offs,
+                                                         const uint64_t* __restrict__ seg_start,
+                                                         int passes) {
+  __shared__ unsigned long long warp_tot[8];
+  const int d = threadIdx.x, lane = d & 31, w = d >> 5;
+  const uint64_t seg = blockIdx.x;
+  for (int p = 0; p < passes; ++p) {
+    const uint64_t at = (seg * passes + p) * kRadix + d;
+    const unsigned long long c = hist[at];
+    unsigned long long x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    unsigned long long base = 0;
+    for (int i = 0; i < w; ++i) base += warp_tot[i];
+    offs[at] = seg_start[seg] + base + x - c;
+    __syncthreads();
+  }
+}
+
+template <class K>
+__global__ void __launch_bounds__(kSortThreads, 4) k_batch_sort_pass(
+    const K* __restrict__ src_k, const uint32_t* __restrict__ src_v, K* __restrict__ dst_k,
+    uint32_t* __restrict__ dst_v, uint64_t n, uint32_t shift, const BatchTile* __restrict__ tiles,
+    const unsigned long long* __restrict__ offs, int pass, int passes,
+    uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter, uint32_t epoch,
+    uint32_t* __restrict__ flags) {
+  constexpr int ITEMS = SortTile<K>::kItems;
+  constexpr int TILE = kSortThreads * ITEMS;
+  union HistOrVals {
+    uint32_t h[kSortWarps][kRadix];
+    uint32_t vals[TILE];
+  };
+  __shared__ K s_keys[TILE];
+  __shared__ HistOrVals hv;
+  __shared__ uint32_t s_start[kRadix];
+  __shared__ unsigned long long s_gbase[kRadix];
+  __shared__ uint32_t s_warp_tot[kSortWarps];
+  __shared__ uint32_t s_tile;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+  for (int i = lane; i < kRadix; i += 32) hv.h[warp][i] = 0;
+  __syncthreads();
+  const uint64_t tile = s_tile;
+  const BatchTile desc = tiles[tile];
+  const uint64_t tile_base = desc.start;
+  const uint32_t valid = desc.count;
+  const unsigned long long* digit_off = offs + ((uint64_t)desc.seg * passes + pass) * kRadix;
+
+  K key[ITEMS];
+  uint32_t rnk[ITEMS];
+  const uint32_t wofs = (uint32_t)warp * 32 * ITEMS + lane;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t e = wofs + i * 32;
+    key[i] = e < valid ? src_k[tile_base + e] : ~K(0);
+  }
+  const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t d = (uint32_t)(key[i] >> shift) & 0xFF;
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      const uint32_t bit = (d >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bal : ~bal;
+    }
+    const uint32_t before = __popc(peers & lt_mask);
+    const uint32_t leader = 31 - __clz(peers);
+    const uint32_t base = hv.h[warp][d];
+    __syncwarp();
+    if (lane == leader) hv.h[warp][d] = base + __popc(peers);
+    __syncwarp();
+    rnk[i] = base + before;
+  }
+  __syncthreads();
+
+  const uint32_t d = tid;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) {
+    const uint32_t c = hv.h[w][d];
+    hv.h[w][d] = cnt;
+    cnt += c;
+  }
+  const uint32_t cnt_valid = (d == kRadix - 1) ? cnt - (TILE - valid) : cnt;
+  uint64_t* my_status = status + tile * kRadix + d;
+  const uint64_t ep = (uint64_t)epoch << 40;
+  const bool first = desc.local == 0;
+  st_volatile_u64(my_status, (first ? kStatInclusive : kStatAggregate) | ep | cnt_valid);
+
+  uint32_t x = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp_tot[warp] = x;
+  __syncthreads();
+  uint32_t wpre = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) wpre += (w < warp) ? s_warp_tot[w] : 0u;
+  const uint32_t start = wpre + x - cnt;
+  s_start[d] = start;
+
+  // look-back over the earlier tiles of the same index only
+  uint64_t excl = 0;
+  if (!first) {
+    const int64_t stop = (int64_t)tile - desc.local;
+    int64_t j = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    while (j >= stop) {
+      const uint64_t s = ld_volatile_u64(status + (uint64_t)j * kRadix + d);
+      const bool ready = ((s >> 40) & 0x3FFFFF) == epoch && (s >> 62) != 0;
+      if (ready) {
+        excl += s & kValueMask;
+        if ((s >> 62) == 2) break;
+        --j;
+      } else {
+        if (++spins > kSpinLimit) {
+          atomicOr(flags, kFlagTimeout);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    st_volatile_u64(my_status, kStatInclusive | ep | (excl + cnt_valid));
+  }
+  s_gbase[d] = digit_off[d] + excl - start;
+  __syncthreads();
+
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t dd = (uint32_t)(key[i] >> shift) & 0xFF;
+    rnk[i] += s_start[dd] + hv.h[warp][dd];
+    s_keys[rnk[i]] = key[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t e = wofs + i * 32;
+    hv.vals[rnk[i]] = e < valid ? src_v[tile_base + e] : 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    const uint32_t j = tid + r * kSortThreads;
+    if (j < valid) {
+      const K kk = s_keys[j];
+      const uint64_t dst = s_gbase[(uint32_t)(kk >> shift) & 0xFF] + j;
+      if (dst < n) {
+        dst_k[dst] = kk;
+        dst_v[dst] = hv.vals[j];
+      }
+    }
+  }
+}
+
+// Geometry of index s computed on the device (the host version is make_geom).
+__device__ __forceinline__ Geom device_geom(uint64_t n, uint32_t k) {
+  Geom g;
+  g.n = n;
+  g.k = k;
+  g.log2k = ((k & (k - 1)) == 0) ? (31 - __clz(k)) : 0;
+  g.m = 0;
+  g.top = 0;
+  g.b = n;
+  g.levels = n ? 1 : 0;
+  if (n) {
+    uint64_t p = 1;
+    uint32_t m = 0;
+    while (p <= n / k) {
+      p *= k;
+      ++m;
+    }
+    g.m = m;
+    g.top = p - 1;
+    g.b = n - g.top;
+    g.levels = m + 1;
+  }
+  return g;
+}
+
+// slot t of index s <- sorted position slot_to_rank(t); k = 0: the sorted order itself
+template <class K, int KF>
+__global__ void __launch_bounds__(256) k_batch_gather(const K* __restrict__ sk,
+                                                      const uint32_t* __restrict__ sv,
+                                                      K* __restrict__ ok, uint32_t* __restrict__ ov,
+                                                      const BatchTile* __restrict__ tiles,
+                                                      uint64_t ntiles,
+                                                      const uint64_t* __restrict__ seg_start,
+                                                      const uint64_t* __restrict__ seg_base,
+                                                      uint32_t k, uint32_t* __restrict__ flags) {
+  bool dup = false;
+  for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const BatchTile t = tiles[ti];
+    const uint64_t s0 = seg_start[t.seg];
+    const uint64_t n = seg_start[t.seg + 1] - s0;
+    const uint64_t out0 = seg_base[t.seg];
+    // KF == 1 marks the sorted order; fan-outs below 2 never reach device_geom
+    const Geom g = device_geom(n, KF > 1 ? (uint32_t)KF : (k >= 2 ? k : 2u));
+    for (uint32_t i = threadIdx.x; i < t.count; i += blockDim.x) {
+      const uint64_t slot = t.start - s0 + i;
+      uint64_t r;
+      if constexpr (KF == 1) r = slot;
+      else r = slot_to_rank<KF>(slot, g);
+      const K key = sk[s0 + r];
+      ok[out0 + slot] = key;
+      ov[out0 + slot] = sv[s0 + r];
+      if (r > 0) dup |= sk[s0 + r - 1] == key;
+    }
+  }
+  if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagDuplicate);
+}
+
 }  // namespace
 
 size_t sort_scratch_bytes(uint64_t n, int key_bytes) {
@@ -430,6 +691,104 @@ cudaError_t check_sorted_dups(const void* sk, uint64_t n, int key_bytes, uint32_
   else
     k_sorted_dups<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)sk, n, dflags);
   count_launch();
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------- batched form, host side
+uint32_t batch_sort_tile(int key_bytes) {
+  return kSortThreads * (key_bytes == 4 ? SortTile<uint32_t>::kItems : SortTile<uint64_t>::kItems);
+}
+
+size_t batch_sort_scratch_bytes(uint64_t ntiles, uint32_t nseg, int key_bytes) {
+  const int passes = key_bytes;
+  return 2 * align256(sizeof(uint64_t) * (uint64_t)nseg * passes * kRadix) +
+         align256(sizeof(uint32_t) * passes) +
+         align256(sizeof(uint64_t) * kRadix * (ntiles + 1));
+}
+
+cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], uint32_t* tmp_v[2],
+                       uint64_t n, int key_bytes, const uint64_t* seg_start, uint32_t nseg,
+                       const BatchTile* tiles, uint64_t ntiles, const BatchTile* chunks,
+                       uint64_t nchunks, void* scratch, uint32_t* dflags, cudaStream_t s,
+                       int* result_buf) {
+  const int passes = key_bytes;
+  char* p = (char*)scratch;
+  unsigned long long* hist = (unsigned long long*)p;
+  p += align256(sizeof(uint64_t) * (uint64_t)nseg * passes * kRadix);
+  unsigned long long* offs = (unsigned long long*)p;
+  p += align256(sizeof(uint64_t) * (uint64_t)nseg * passes * kRadix);
+  uint32_t* counter = (uint32_t*)p;
+  p += align256(sizeof(uint32_t) * passes);
+  uint64_t* status = (uint64_t*)p;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, batch_sort_scratch_bytes(ntiles, nseg, key_bytes), s);
+  if (e != cudaSuccess) return e;
+  if (n == 0 || ntiles == 0) {
+    *result_buf = -1;
+    return cudaSuccess;
+  }
+  const int hgrid = (int)std::min<uint64_t>(nchunks, (uint64_t)sm_count() * 8);
+  if (key_bytes == 4)
+    k_batch_histogram<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)keys, vals, chunks, nchunks, hist, dflags);
+  else
+    k_batch_histogram<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)keys, vals, chunks, nchunks, hist, dflags);
+  k_batch_scan_hist<<<nseg, 256, 0, s>>>(hist, offs, seg_start, passes);
+  count_launch(2);
+  // every pass runs (no host round trip to skip trivial digits, so the whole
+  // build can be captured in a graph)
+  const void* ck = keys;
+  const uint32_t* cv = vals;
+  int cur = -1;
+  for (int ps = 0; ps < passes; ++ps) {
+    const int dst = cur == 0 ? 1 : 0;
+    if (key_bytes == 4)
+      k_batch_sort_pass<uint32_t><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
+          (const uint32_t*)ck, cv, (uint32_t*)tmp_k[dst], tmp_v[dst], n, 8u * ps, tiles, offs, ps,
+          passes, status, counter + ps, (uint32_t)ps + 1, dflags);
+    else
+      k_batch_sort_pass<uint64_t><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
+          (const uint64_t*)ck, cv, (uint64_t*)tmp_k[dst], tmp_v[dst], n, 8u * ps, tiles, offs, ps,
+          passes, status, counter + ps, (uint32_t)ps + 1, dflags);
+    count_launch();
+    ck = tmp_k[dst];
+    cv = tmp_v[dst];
+    cur = dst;
+  }
+  *result_buf = cur;
+  return cudaGetLastError();
+}
+
+template <class K>
+static void launch_batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t* ov,
+                                const BatchTile* tiles, uint64_t ntiles, const uint64_t* seg_start,
+                                const uint64_t* seg_base, uint32_t k, uint32_t* dflags,
+                                cudaStream_t s) {
+  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)sm_count() * 16);
+  const K* a = (const K*)sk;
+  K* b = (K*)ok;
+#define GI_BG(KF) k_batch_gather<K, KF><<<grid, 256, 0, s>>>(a, sv, b, ov, tiles, ntiles, seg_start, seg_base, k, dflags)
+  switch (k) {
+    case 0: GI_BG(1); break;  // sorted order: rank == slot
+    case 2: GI_BG(2); break;
+    case 3: GI_BG(3); break;
+    case 5: GI_BG(5); break;
+    case 9: GI_BG(9); break;
+    case 17: GI_BG(17); break;
+    default: GI_BG(0); break;
+  }
+#undef GI_BG
+  count_launch();
+}
+
+cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t* ov,
+                         const BatchTile* tiles, uint64_t ntiles, const uint64_t* seg_start,
+                         const uint64_t* seg_base, uint32_t k, int key_bytes, uint32_t* dflags,
+                         cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  if (key_bytes == 4)
+    launch_batch_gather<uint32_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s);
+  else
+    launch_batch_gather<uint64_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s);
   return cudaGetLastError();
 }
 

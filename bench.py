@@ -62,8 +62,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="timed steps only (for profiler launch lists)")
-    ap.add_argument("--workload", default="point", choices=["point", "batched"],
-                    help="point: the 2^26-key step (default); batched: 4096 indexes in one graph")
+    ap.add_argument("--workload", default="point", choices=["point", "batched", "ranges", "dups"],
+                    help="point: the 2^26-key step (default); batched: 4096 indexes in one graph; "
+                         "ranges: 2^24 ranges on 2^26 u32 keys; dups: replicated keys, point = range [x, x]")
     ap.add_argument("--batch-k", type=int, default=5)
     ap.add_argument("--batch-indexes", type=int, default=4096)
     ap.add_argument("--probe-sweep", action="store_true",
@@ -634,9 +635,99 @@ def run_batched(a):
     gi.gi_batch_destroy(batch)
 
 
+def _ev_ms(torch, fn, reps, warm=2):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_ranges(a):
+    """2^26 unique u32 keys, 2^24 inclusive ranges with 1, 16 and 256 expected rows,
+    CSR output, for the sorted, Eytzinger and k-ary (16, 17) layouts and both
+    range-fill strategies; one JSON line per case (count + scan + fill, one call)."""
+    import torch
+
+    import paper_2506_01576_gb300 as gi
+    gi.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n, m = 1 << 26, 1 << 24
+    seed = W.seed_for(2, 26)
+    keys = W.unique_keys(n, 32, seed)
+    kd = torch.from_numpy(keys.view(np.int32)).to(dev)
+    rd = torch.arange(n, dtype=torch.int32, device=dev)
+    for E in (1, 16, 256):
+        lo, hi, w = W.ranges_with_expected_rows(n, m, E, 32, seed + E)
+        lod, hid = torch.from_numpy(lo.view(np.int32)).to(dev), torch.from_numpy(hi.view(np.int32)).to(dev)
+        off = torch.empty(m + 1, dtype=torch.int64, device=dev)
+        for layout, k, fills in ((gi.GI_SORTED, 0, (0,)), (gi.GI_EYTZINGER, 2, (0, 1)),
+                                 (gi.GI_EYTZINGER_KARY, 16, (0, 1)), (gi.GI_EYTZINGER_KARY, 17, (0, 1))):
+            idx = gi.gi_build(kd, rd, layout | gi.GI_KEY_U32, k)
+            gi.gi_range_lookup(idx, lod, hid, off)
+            total = int(off[-1].item())
+            out = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+            for fill in fills:
+                gi.gi_set_option(idx, gi.GI_OPT_RANGE_FILL, fill)
+                # a single call with the output: count + scan + fill
+                ms = _ev_ms(torch, lambda: gi.gi_range_lookup(idx, lod, hid, off, out), a.steps)
+                cnt_ms = _ev_ms(torch, lambda: gi.gi_range_lookup(idx, lod, hid, off), a.steps)
+                print(json.dumps({"workload": "ranges", "E": E, "width": w,
+                                  "layout": {0: "sorted", 1: "EBS", 2: "EKS"}[layout], "k": k,
+                                  "fill": "level runs" if fill else "rank map", "ranges": m,
+                                  "rows": total, "ms": ms, "count_scan_ms": cnt_ms,
+                                  "ranges_per_s": m / ms * 1e3, "rows_per_s": total / ms * 1e3,
+                                  "ms_per_expected_hit_per_2e18_ranges": ms / E / 64}), flush=True)
+            del out
+            gi.gi_destroy(idx)
+
+
+def run_dups(a):
+    """Section 8.11 / Fig 25 shape: 2^26 u64 keys, each distinct key replicated r
+    times; 2^20 point queries as ranges [x, x] returning every occurrence."""
+    import torch
+
+    import paper_2506_01576_gb300 as gi
+    gi.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n, m = 1 << 26, 1 << 20
+    for r in (1, 4, 16, 64, 256, 1024):
+        keys = W.duplicate_keys(n // r, r, 64, 7)
+        kd = torch.from_numpy(keys.view(np.int64)).to(dev)
+        rd = torch.arange(len(keys), dtype=torch.int32, device=dev)
+        rng = np.random.default_rng(r)
+        q = keys[rng.integers(0, len(keys), size=m)]
+        qd = torch.from_numpy(q.view(np.int64)).to(dev)
+        off = torch.empty(m + 1, dtype=torch.int64, device=dev)
+        for layout, k in ((gi.GI_SORTED, 0), (gi.GI_EYTZINGER, 2), (gi.GI_EYTZINGER_KARY, 5),
+                          (gi.GI_EYTZINGER_KARY, 9)):
+            idx = gi.gi_build(kd, rd, layout | gi.GI_KEY_U64, k)
+            gi.gi_range_lookup(idx, qd, qd, off)
+            total = int(off[-1].item())
+            out = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+            ms = _ev_ms(torch, lambda: gi.gi_range_lookup(idx, qd, qd, off, out), a.steps)
+            print(json.dumps({"workload": "duplicates", "replicas": r, "layout": {0: "sorted", 1: "EBS", 2: "EKS"}[layout],
+                              "k": k, "queries": m, "rows": total, "ms": ms,
+                              "queries_per_s": m / ms * 1e3, "rows_per_s": total / ms * 1e3}), flush=True)
+            del out
+            gi.gi_destroy(idx)
+        del kd, rd
+
+
 if __name__ == "__main__":
     args = parse()
-    if args.workload == "batched":
+    if args.workload == "ranges":
+        run_ranges(args)
+    elif args.workload == "dups":
+        run_dups(args)
+    elif args.workload == "batched":
         run_batched(args)
     elif args.probe_sweep:
         probe_sweep()

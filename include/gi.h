@@ -179,6 +179,10 @@ int gi_copy_layout(const gi_index* index, void* keys_out, uint32_t* rowids_out);
  *                       deeper levels, rowIDs, probes and results use evict-first
  *                       (0 = every level streamed).  Default: the levels whose keys
  *                       fit in two thirds of L2.
+ *   GI_OPT_RANGE_FILL   Eytzinger layouts: 1 writes a range's rows level by level,
+ *                       one contiguous slot run per level, a warp taking runs of
+ *                       >= 32 slots (Sections 5, 5.1); 0 (default) maps every rank
+ *                       to its slot one at a time.  Same output either way.
  */
 #define GI_OPT_GROUP         1
 #define GI_OPT_PER_THREAD    2
@@ -188,6 +192,7 @@ int gi_copy_layout(const gi_index* index, void* keys_out, uint32_t* rowids_out);
 #define GI_OPT_PREFETCH      6
 #define GI_OPT_EARLY_EXIT    7
 #define GI_OPT_HOT_LEVELS    8
+#define GI_OPT_RANGE_FILL    9
 int gi_set_option(gi_index* index, int option, int64_t value);
 int gi_get_option(const gi_index* index, int option, int64_t* value);
 

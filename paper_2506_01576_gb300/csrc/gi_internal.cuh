@@ -175,6 +175,7 @@ struct LookupCfg {
   int prefetch;       // EBS prefetch distance
   int early_exit;     // stop on an equal pivot (unique keys only)
   int hot_levels;     // k-ary: top levels kept in L2 (evict_last); the rest streamed
+  int range_fill;     // 0: rows by rank -> slot; 1: rows by per-level runs
 };
 // top levels whose keys fit in `budget` bytes
 int levels_within(const Geom& g, int key_bytes, uint64_t budget);

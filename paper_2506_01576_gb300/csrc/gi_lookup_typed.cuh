@@ -38,8 +38,8 @@ cudaError_t range_lookup_typed(const K* keys, const uint32_t* rows, const Geom& 
       bool done = false;
 #define GI_RC(KF)                                                                            \
   if (!done && g.k == KF) {                                                                  \
-    /* one thread per range when a node is one vector of <= 64 bytes, else one key/lane */   \
-    constexpr bool SINGLE = pt::EksShape<K, KF, 1>::VEC && (KF - 1) * sizeof(K) <= 64;       \
+    /* one thread per range when a node is at most 64 bytes, else one key per lane */       \
+    constexpr bool SINGLE = (KF - 1) * sizeof(K) <= 64;                                      \
     constexpr int GG = SINGLE ? 1 : (KF - 1 <= 2) ? 2 : (KF - 1 <= 4) ? 4                    \
                      : (KF - 1 <= 8) ? 8 : (KF - 1 <= 16) ? 16 : 32;                         \
     k_range_count<K, 2, KF, GG><<<grid_for(m * GG), block, 0, s>>>(keys, g, lo, hi, m,       \
@@ -67,6 +67,13 @@ cudaError_t range_lookup_typed(const K* keys, const uint32_t* rows, const Geom& 
     const unsigned grid = (unsigned)(gr ? gr : 1);
     if (c.layout == GI_SORTED) {
       k_range_fill<0, 0><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows);
+    } else if (c.range_fill == 1) {  // level runs (Section 5)
+      switch (c.layout == GI_EYTZINGER ? 2u : g.k) {
+#define GI_RL(KF) case KF: k_range_fill_levels<KF><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows); break;
+        GI_RL(2) GI_RL(3) GI_RL(4) GI_RL(5) GI_RL(8) GI_RL(9) GI_RL(16) GI_RL(17) GI_RL(32) GI_RL(33)
+#undef GI_RL
+        default: k_range_fill_levels<0><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows); break;
+      }
     } else if (c.layout == GI_EYTZINGER) {
       k_range_fill<1, 2><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows);
     } else {

@@ -108,8 +108,9 @@ __device__ __forceinline__ void eks_bounds(const K* __restrict__ keys, const Geo
   ru = cand[1] != ~0ull ? slot_to_rank<KF>(cand[1], g) : n;
 }
 
-// k-ary, one thread per range when a node is one vector of at most 64 bytes:
-// both descents interleaved, whole nodes loaded with vector loads, no ballots.
+// k-ary, one thread per range when a node is at most 64 bytes: both descents
+// interleaved, whole nodes loaded (vector loads where the node is a power-of-two
+// vector), no ballots.
 template <class K, int KF>
 __device__ __forceinline__ void eks_bounds_single(const K* __restrict__ keys, const Geom& g, K L,
                                                   K U, uint64_t& rl, uint64_t& ru) {
@@ -118,8 +119,16 @@ __device__ __forceinline__ void eks_bounds_single(const K* __restrict__ keys, co
   uint64_t s0 = 0, s1 = 0, c0 = ~0ull, c1 = ~0ull;
   for (uint32_t lv = 0; lv < g.levels; ++lv) {
     K a[N], b[N];
-    if (s0 < n) pt::vec_load<K, N>(keys + s0, a);
-    if (s1 < n) pt::vec_load<K, N>(keys + s1, b);
+    if constexpr (pt::EksShape<K, KF, 1>::VEC) {
+      if (s0 < n) pt::vec_load<K, N>(keys + s0, a);
+      if (s1 < n) pt::vec_load<K, N>(keys + s1, b);
+    } else {  // nodes that are not a power-of-two vector: plain loads
+#pragma unroll
+      for (int p = 0; p < N; ++p) {
+        if (s0 < n) a[p] = __ldg(keys + s0 + p);
+        if (s1 < n) b[p] = __ldg(keys + s1 + p);
+      }
+    }
     if (s0 < n) {
       uint32_t c = 0;
 #pragma unroll
@@ -326,6 +335,77 @@ __global__ void __launch_bounds__(256) k_range_fill(const uint32_t* __restrict__
     }
     if (!big) {
       for (uint64_t j = 0; j < cnt; ++j) out[off + j] = row_at<LAYOUT, KF>(rows, r0 + j, g);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- fill by level runs
+// Ranks < r that the complete k-ary tree stores on level l.  The bottom level
+// holds the ranks r' with r' mod k != k-1 until its b keys are used up, so
+// nb(r) = min(b, r - floor(r/k)) of them lie below r.  The other Q = r - nb(r)
+// ranks are the upper levels' keys in order; in the perfect upper tree, the
+// (x)th of them (x = 1..) sits on level m-1-v, where v is the number of trailing
+// zeros of x in base k.  So level l holds floor(Q/k^j) - floor(Q/k^(j+1)) of
+// them, with j = m-1-l.
+template <int KF>
+__device__ __forceinline__ uint64_t level_rank_count(uint64_t r, uint32_t l, const Geom& g) {
+  const uint64_t k = KF ? (uint64_t)KF : (uint64_t)g.k;
+  uint64_t nb = r - r / k;
+  if (nb > g.b) nb = g.b;
+  if (l == g.m) return nb;
+  const uint64_t Q = r - nb;
+  const uint64_t kj = kpow<KF>(g.m - 1 - l, g);
+  return Q / kj - Q / (kj * k);
+}
+
+// The rows of a range, level by level (Section 5): on every level the keys of
+// [lo_rank, hi_rank) occupy one contiguous run of slots, whose ends follow from
+// level_rank_count, so no key is read.  Each row goes to its key-order position
+// offset + p'(slot) - lo_rank.  A lane handles its own range's short runs; runs
+// of 32 slots or more are taken by the whole warp with coalesced reads, one at a
+// time -- the single-thread / warp switch of Section 5.1, made per level.
+template <int KF>
+__global__ void __launch_bounds__(256) k_range_fill_levels(const uint32_t* __restrict__ rows, Geom g,
+                                                           const uint64_t* __restrict__ offsets,
+                                                           const uint64_t* __restrict__ lo_rank,
+                                                           uint64_t m, uint32_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < m; w += warps) {
+    const uint64_t i = w * 32 + lane;
+    uint64_t off = 0, cnt = 0, r0 = 0;
+    if (i < m) {
+      off = offsets[i];
+      cnt = offsets[i + 1] - off;
+      r0 = lo_rank[i];
+    }
+    const uint64_t r1 = r0 + cnt;
+    for (uint32_t l = 0; l < g.levels; ++l) {
+      uint64_t a = 0, len = 0;
+      if (cnt) {
+        a = level_rank_count<KF>(r0, l, g);
+        len = level_rank_count<KF>(r1, l, g) - a;
+      }
+      const uint64_t start = (l == g.m ? g.top : kpow<KF>(l, g) - 1) + a;
+      const bool big = len >= 32;
+      if (!big) {
+        for (uint64_t j = 0; j < len; ++j) {
+          const uint64_t s = start + j;
+          out[off + slot_to_rank<KF>(s, g) - r0] = __ldg(rows + s);
+        }
+      }
+      uint32_t bm = __ballot_sync(0xffffffffu, big);
+      while (bm) {
+        const int b = __ffs(bm) - 1;
+        bm &= bm - 1;
+        const uint64_t bs = __shfl_sync(0xffffffffu, start, b);
+        const uint64_t bl = __shfl_sync(0xffffffffu, len, b);
+        const uint64_t bo = __shfl_sync(0xffffffffu, off - r0, b);
+        for (uint64_t j = lane; j < bl; j += 32) {
+          const uint64_t s = bs + j;
+          out[bo + slot_to_rank<KF>(s, g)] = __ldg(rows + s);
+        }
+      }
     }
   }
 }

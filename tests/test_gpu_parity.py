@@ -254,3 +254,47 @@ def test_probes_roofline_kernels_run():
     torch.cuda.synchronize()
     with pytest.raises(gi.GIError):
         gi.gi_probe_random_sectors(buf, 48, 10, 1, sink)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+@pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER, 2), (gi.GI_EYTZINGER_KARY, 5),
+                                      (gi.GI_EYTZINGER_KARY, 16), (gi.GI_EYTZINGER_KARY, 33),
+                                      (gi.GI_EYTZINGER_KARY, 6)])
+def test_range_fill_by_level_runs_equals_by_rank(dtype, layout, k):
+    # Section 5 level-by-level fill (warp switch at 32 slots per level, Section 5.1)
+    # and the per-rank map write the same CSR; widths from a few rows to thousands
+    bits = 8 * np.dtype(dtype).itemsize
+    n = 200003
+    keys = W.unique_keys(n, bits, 41)
+    rows = np.random.default_rng(1).permutation(n).astype(np.uint32)
+    sk, sr = oracle.sort_pairs(keys, rows)
+    idx = build(keys, rows, layout, k)
+    for E in (1, 5, 40, 300, 3000):
+        lo, hi, _ = W.ranges_with_expected_rows(n, 4000, E, bits, E)
+        woff, wrr = oracle.range_lookup(sk, sr, lo, hi)
+        for fill in (0, 1):
+            gi.gi_set_option(idx, gi.GI_OPT_RANGE_FILL, fill)
+            off, rr = ranges(idx, lo, hi)
+            assert np.array_equal(off, woff) and np.array_equal(rr, wrr), (E, fill)
+    gi.gi_destroy(idx)
+
+
+@pytest.mark.parametrize("replicas", [1, 4, 64, 1024])
+def test_duplicate_keys_all_occurrences_by_point_range(replicas):
+    # Section 8.11 / Fig 25: with duplicates a point query returns every occurrence,
+    # i.e. the range [x, x]; occurrences come in input order
+    n_distinct = max(1, 100000 // replicas)
+    keys = W.duplicate_keys(n_distinct, replicas, 64, 5)
+    rows = np.arange(len(keys), dtype=np.uint32)
+    sk, sr = oracle.sort_pairs(keys, rows)
+    probes = np.concatenate([np.unique(keys)[:3000], W.unique_keys(500, 64, 999)]).astype(np.uint64)
+    woff, wrr = oracle.range_lookup(sk, sr, probes, probes)
+    for layout, k in ((gi.GI_SORTED, 0), (gi.GI_EYTZINGER, 2), (gi.GI_EYTZINGER_KARY, 9)):
+        idx = build(keys, rows, layout, k)
+        off, rr = ranges(idx, probes, probes)
+        assert np.array_equal(off, woff) and np.array_equal(rr, wrr), (layout, k)
+        # the point lookup returns the first occurrence (input order)
+        first = point(idx, probes)
+        want_first = np.where(np.diff(woff) > 0, wrr[np.minimum(woff[:-1], len(wrr) - 1).astype(np.int64)], gi.GI_MISS)
+        assert np.array_equal(first, want_first.astype(np.uint32))
+        gi.gi_destroy(idx)

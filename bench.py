@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="timed steps only (for profiler launch lists)")
-    ap.add_argument("--workload", default="point", choices=["point", "batched", "ranges", "dups"],
+    ap.add_argument("--workload", default="point", choices=["point", "batched", "ranges", "dups", "skew"],
                     help="point: the 2^26-key step (default); batched: 4096 indexes in one graph; "
                          "ranges: 2^24 ranges on 2^26 u32 keys; dups: replicated keys, point = range [x, x]")
     ap.add_argument("--batch-k", type=int, default=5)
@@ -721,9 +721,55 @@ def run_dups(a):
         del kd, rd
 
 
+def run_skew(a):
+    """Sections 8.9-8.10 shapes on 2^26 u64 keys: 2^25 probes at hit rate 0.5 with
+    hits uniform, Zipf(s) for s up to 2.0, or the uniform probes pre-sorted; BS, EBS,
+    EKS single (k = 5) and EKS group (k = 9, 8 lanes), each with and without local
+    lookup reordering.  One JSON line per case."""
+    import torch
+
+    import paper_2506_01576_gb300 as gi
+    gi.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n, m = 1 << 26, 1 << 25
+    seed = W.seed_for(1, 26)
+    keys = W.unique_keys(n, 64, seed)
+    kd = torch.from_numpy(keys.view(np.int64)).to(dev)
+    rd = torch.arange(n, dtype=torch.int32, device=dev)
+    out = torch.empty(m, dtype=torch.int32, device=dev)
+    configs = [("BS", gi.GI_SORTED, 0, {}), ("EBS", gi.GI_EYTZINGER, 2, {gi.GI_OPT_PER_THREAD: 4}),
+               ("EKS single k=5", gi.GI_EYTZINGER_KARY, 5, {gi.GI_OPT_GROUP: 1}),
+               ("EKS group k=9", gi.GI_EYTZINGER_KARY, 9, {gi.GI_OPT_GROUP: 8})]
+    built = {}
+    for name, layout, k, opts in configs:
+        built[name] = gi.gi_build(kd, rd, layout | gi.GI_KEY_U64, k)
+        for o, v in opts.items():
+            gi.gi_set_option(built[name], o, v)
+    dists = [("uniform", 0.0)] + [("zipf", s) for s in (0.5, 0.99, 1.25, 1.5, 2.0)] + [("sorted", 0.0)]
+    for dname, zs in dists:
+        q = W.point_probes(keys, m, 0.5, 64, seed, seed + 5, dist="zipf" if dname == "zipf" else "uniform",
+                           zipf_s=zs if zs else 0.99)
+        if dname == "sorted":
+            q = np.sort(q)
+        qd = torch.from_numpy(q.view(np.int64)).to(dev)
+        for name, layout, k, opts in configs:
+            idx = built[name]
+            for ro in (0, 1):
+                gi.gi_set_option(idx, gi.GI_OPT_REORDER, ro)
+                ms = _ev_ms(torch, lambda: gi.gi_point_lookup(idx, qd, out), a.steps)
+                print(json.dumps({"workload": "skew", "probes": dname, "zipf_s": zs, "index": name,
+                                  "reorder": ro, "ms": ms, "lookups_per_s": m / ms * 1e3}), flush=True)
+        del qd
+    for v in built.values():
+        gi.gi_destroy(v)
+
+
 if __name__ == "__main__":
     args = parse()
-    if args.workload == "ranges":
+    if args.workload == "skew":
+        run_skew(args)
+    elif args.workload == "ranges":
         run_ranges(args)
     elif args.workload == "dups":
         run_dups(args)

@@ -183,6 +183,10 @@ int gi_copy_layout(const gi_index* index, void* keys_out, uint32_t* rowids_out);
  *                       one contiguous slot run per level, a warp taking runs of
  *                       >= 32 slots (Sections 5, 5.1); 0 (default) maps every rank
  *                       to its slot one at a time.  Same output either way.
+ *   GI_OPT_REORDER      point lookups: 1 sorts each CTA's tile of 2048 probes in
+ *                       shared memory before the descent and restores probe order
+ *                       before the store (local lookup reordering, Section 7.4);
+ *                       sorted, Eytzinger and k in {3, 5, 9, 17}.  Default 0.
  */
 #define GI_OPT_GROUP         1
 #define GI_OPT_PER_THREAD    2
@@ -193,6 +197,7 @@ int gi_copy_layout(const gi_index* index, void* keys_out, uint32_t* rowids_out);
 #define GI_OPT_EARLY_EXIT    7
 #define GI_OPT_HOT_LEVELS    8
 #define GI_OPT_RANGE_FILL    9
+#define GI_OPT_REORDER       10
 int gi_set_option(gi_index* index, int option, int64_t value);
 int gi_get_option(const gi_index* index, int option, int64_t* value);
 

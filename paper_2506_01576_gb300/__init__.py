@@ -22,7 +22,7 @@ __all__ = [
     "GI_SORTED", "GI_EYTZINGER", "GI_EYTZINGER_KARY", "GI_KEY_U32", "GI_KEY_U64", "GI_MISS",
     "GI_OK", "GI_ERR_INVALID", "GI_ERR_NOMEM", "GI_ERR_CUDA", "GI_ERR_TIMEOUT",
     "GI_OPT_GROUP", "GI_OPT_PER_THREAD", "GI_OPT_SMEM_LEVELS", "GI_OPT_BLOCK",
-    "GI_OPT_BLOCKS_PER_SM", "GI_OPT_PREFETCH", "GI_OPT_EARLY_EXIT", "GI_OPT_HOT_LEVELS", "GI_OPT_RANGE_FILL",
+    "GI_OPT_BLOCKS_PER_SM", "GI_OPT_PREFETCH", "GI_OPT_EARLY_EXIT", "GI_OPT_HOT_LEVELS", "GI_OPT_RANGE_FILL", "GI_OPT_REORDER",
     "GIError", "Index", "gi_info", "lib_path", "load",
     "gi_build", "gi_point_lookup", "gi_range_lookup", "gi_destroy", "gi_set_stream", "gi_sync",
     "gi_last_error", "gi_footprint_bytes", "gi_get_info", "gi_copy_layout", "gi_set_option", "gi_get_option",
@@ -40,7 +40,7 @@ GI_MISS = 0xFFFFFFFF
 GI_NOALLOC_MAX_RANGES = 1 << 20
 GI_BATCH_OPT_CHUNK, GI_BATCH_OPT_BLOCKS_PER_SM, GI_BATCH_OPT_SMEM_BUDGET = 1, 2, 3
 (GI_OPT_GROUP, GI_OPT_PER_THREAD, GI_OPT_SMEM_LEVELS, GI_OPT_BLOCK, GI_OPT_BLOCKS_PER_SM,
- GI_OPT_PREFETCH, GI_OPT_EARLY_EXIT, GI_OPT_HOT_LEVELS, GI_OPT_RANGE_FILL) = range(1, 10)
+ GI_OPT_PREFETCH, GI_OPT_EARLY_EXIT, GI_OPT_HOT_LEVELS, GI_OPT_RANGE_FILL, GI_OPT_REORDER) = range(1, 11)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(_HERE, "libgi.so")

@@ -35,7 +35,7 @@ struct gi_index {
   uint32_t* rows = nullptr;
   uint32_t* dflags = nullptr;  // device status word
   gi::Geom geom{};
-  int64_t opt[10] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+  int64_t opt[11] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
   // range-lookup scratch and the state of the two-call protocol
   void* rscratch = nullptr;
   size_t rscratch_bytes = 0;
@@ -169,6 +169,7 @@ gi::LookupCfg resolve_cfg(const gi_index* idx) {
   if (c.layout == GI_SORTED) c.per_thread = 1;
   // the per-rank map measured faster except for 256-row ranges on 17-ary trees
   c.range_fill = o[GI_OPT_RANGE_FILL] >= 0 ? (int)o[GI_OPT_RANGE_FILL] : 0;
+  c.reorder = o[GI_OPT_REORDER] >= 0 ? (int)o[GI_OPT_REORDER] : 0;
   if (o[GI_OPT_HOT_LEVELS] >= 0) {
     c.hot_levels = (int)o[GI_OPT_HOT_LEVELS];
   } else {
@@ -714,7 +715,7 @@ int gi_copy_layout(const gi_index* cidx, void* keys_out, uint32_t* rowids_out) {
 int gi_set_option(gi_index* idx, int option, int64_t v) {
   t_err.clear();
   if (!idx) return fail(GI_ERR_INVALID, "gi_set_option: NULL index");
-  if (option < 1 || option > 9) return fail(GI_ERR_INVALID, "gi_set_option: unknown option %d", option);
+  if (option < 1 || option > 10) return fail(GI_ERR_INVALID, "gi_set_option: unknown option %d", option);
   if (v == -1) {
     idx->opt[option] = -1;
     return GI_OK;
@@ -756,6 +757,9 @@ int gi_set_option(gi_index* idx, int option, int64_t v) {
     case GI_OPT_RANGE_FILL:
       if (v != 0 && v != 1) return fail(GI_ERR_INVALID, "gi_set_option: range fill must be 0 or 1");
       break;
+    case GI_OPT_REORDER:
+      if (v != 0 && v != 1) return fail(GI_ERR_INVALID, "gi_set_option: reorder must be 0 or 1");
+      break;
   }
   idx->opt[option] = v;
   return GI_OK;
@@ -764,7 +768,7 @@ int gi_set_option(gi_index* idx, int option, int64_t v) {
 int gi_get_option(const gi_index* idx, int option, int64_t* v) {
   t_err.clear();
   if (!idx || !v) return fail(GI_ERR_INVALID, "gi_get_option: NULL argument");
-  if (option < 1 || option > 9) return fail(GI_ERR_INVALID, "gi_get_option: unknown option %d", option);
+  if (option < 1 || option > 10) return fail(GI_ERR_INVALID, "gi_get_option: unknown option %d", option);
   const gi::LookupCfg c = resolve_cfg(idx);
   switch (option) {
     case GI_OPT_GROUP: *v = c.group; break;
@@ -776,6 +780,7 @@ int gi_get_option(const gi_index* idx, int option, int64_t* v) {
     case GI_OPT_EARLY_EXIT: *v = c.early_exit; break;
     case GI_OPT_HOT_LEVELS: *v = c.hot_levels; break;
     case GI_OPT_RANGE_FILL: *v = c.range_fill; break;
+    case GI_OPT_REORDER: *v = c.reorder; break;
   }
   return GI_OK;
 }

@@ -176,6 +176,7 @@ struct LookupCfg {
   int early_exit;     // stop on an equal pivot (unique keys only)
   int hot_levels;     // k-ary: top levels kept in L2 (evict_last); the rest streamed
   int range_fill;     // 0: rows by rank -> slot; 1: rows by per-level runs
+  int reorder;        // point lookups: sort each CTA's probe tile first (Section 7.4)
 };
 // top levels whose keys fit in `budget` bytes
 int levels_within(const Geom& g, int key_bytes, uint64_t budget);

@@ -428,6 +428,115 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
   }
 }
 
+// ---------------------------------------------------------------- local lookup reordering
+// Section 7.4: a CTA takes a tile of probes, sorts them in shared memory (keys
+// with their positions, bitonic network), looks them up in sorted order --
+// neighbouring lanes then walk nearly the same path and share cache lines --
+// and puts each result back at its probe's position before one coalesced store.
+constexpr int kReorderItems = 8;
+constexpr int kReorderThreads = 256;
+constexpr int kReorderTile = kReorderItems * kReorderThreads;
+
+template <class K, int KIND, int KF>  // KIND 0: sorted (BS), 1: Eytzinger, 2: k-ary single
+__device__ __forceinline__ uint32_t lookup_one(const K* __restrict__ keys,
+                                               const uint32_t* __restrict__ rows, uint64_t n,
+                                               uint32_t levels, K x) {
+  if constexpr (KIND == 0) {
+    uint64_t lo = 0, len = n;
+    while (len > 0) {
+      const uint64_t half = len >> 1;
+      if (ldg(keys + lo + half) < x) {
+        lo += half + 1;
+        len -= half + 1;
+      } else {
+        len = half;
+      }
+    }
+    return (lo < n && ldg(keys + lo) == x) ? ldg(rows + lo) : GI_MISS;
+  } else if constexpr (KIND == 1) {
+    uint64_t s = 1;
+    bool eq = false;
+    for (uint32_t lv = 0; lv < levels; ++lv) {
+      if (s <= n) {
+        const K v = ldg(keys + s);
+        const bool right = v < x;
+        eq = right ? eq : (v == x);
+        s = 2 * s + (right ? 1 : 0);
+      }
+    }
+    const uint64_t lb = s >> __ffsll((long long)~s);
+    return (lb != 0 && eq) ? ldg(rows + (lb - 1)) : GI_MISS;
+  } else {
+    constexpr int N = KF - 1;
+    uint64_t s = 0, cand = kNone;
+    for (uint32_t lv = 0; lv < levels; ++lv) {
+      if (s >= n) break;
+      K piv[N];
+      if constexpr (EksShape<K, KF, 1>::VEC) {
+        vec_load<K, N>(keys + s, piv);
+      } else {
+#pragma unroll
+        for (int p = 0; p < N; ++p) piv[p] = ldg(keys + s + p);
+      }
+      uint32_t c = 0;
+#pragma unroll
+      for (int p = 0; p < N; ++p) c += piv[p] < x ? 1u : 0u;
+      if (c < (uint32_t)N && s + c < n) cand = s + c;
+      s = s * KF + (uint64_t)(c + 1) * N;
+    }
+    return (cand != kNone && ldg(keys + cand) == x) ? ldg(rows + cand) : GI_MISS;
+  }
+}
+
+template <class K, int KIND, int KF>
+__global__ void __launch_bounds__(kReorderThreads) k_point_reorder(const K* __restrict__ keys,
+                                                                  const uint32_t* __restrict__ rows,
+                                                                  uint64_t n, uint32_t levels,
+                                                                  const K* __restrict__ q, uint64_t m,
+                                                                  uint32_t* __restrict__ out) {
+  __shared__ K s_key[kReorderTile];
+  __shared__ uint32_t s_pos[kReorderTile];
+  __shared__ uint32_t s_res[kReorderTile];
+  const int tid = threadIdx.x;
+  for (uint64_t base = (uint64_t)blockIdx.x * kReorderTile; base < m;
+       base += (uint64_t)gridDim.x * kReorderTile) {
+    const uint32_t cnt = (uint32_t)min((uint64_t)kReorderTile, m - base);
+    for (int i = tid; i < kReorderTile; i += kReorderThreads) {
+      s_key[i] = i < (int)cnt ? q[base + i] : ~K(0);  // padding sorts last
+      s_pos[i] = (uint32_t)i;
+    }
+    __syncthreads();
+    // bitonic sort of (key, position) pairs, ascending
+    for (int size = 2; size <= kReorderTile; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = tid; t < kReorderTile / 2; t += kReorderThreads) {
+          const int lo = 2 * t - (t & (stride - 1));
+          const int hi = lo + stride;
+          const bool up = (lo & size) == 0;
+          const K a = s_key[lo], b = s_key[hi];
+          if ((a > b) == up) {
+            s_key[lo] = b;
+            s_key[hi] = a;
+            const uint32_t pa = s_pos[lo];
+            s_pos[lo] = s_pos[hi];
+            s_pos[hi] = pa;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // neighbouring lanes take neighbouring sorted probes
+    for (int j = 0; j < kReorderItems; ++j) {
+      const int p = j * kReorderThreads + tid;
+      const uint32_t orig = s_pos[p];
+      if (orig < cnt) s_res[orig] = lookup_one<K, KIND, KF>(keys, rows, n, levels, s_key[p]);
+    }
+    __syncthreads();
+    for (int i = tid; i < (int)cnt; i += kReorderThreads) out[base + i] = s_res[i];
+    __syncthreads();
+  }
+}
+
 // Any k, one thread per lookup, pivots scanned in order.
 template <class K>
 __global__ void __launch_bounds__(512) k_eks_generic(const K* __restrict__ keys,

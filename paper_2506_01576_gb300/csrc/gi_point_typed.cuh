@@ -38,6 +38,30 @@ cudaError_t point_lookup_typed(const K* keys, const uint32_t* rows, const Geom& 
                                uint32_t* dflags, cudaStream_t s) {
   const int block = c.block;
   const int R = c.per_thread;
+  if (c.reorder) {  // local lookup reordering (Section 7.4)
+    uint64_t tiles = (m + kReorderTile - 1) / kReorderTile;
+    const uint64_t cap = (uint64_t)sm_count() * 8;
+    const unsigned grid = (unsigned)(tiles < cap ? (tiles ? tiles : 1) : cap);
+    const K* kb = keys;
+    bool done = true;
+    if (c.layout == GI_SORTED) {
+      k_point_reorder<K, 0, 2><<<grid, kReorderThreads, 0, s>>>(kb, rows, g.n, g.levels, q, m, out);
+    } else if (c.layout == GI_EYTZINGER) {
+      k_point_reorder<K, 1, 2><<<grid, kReorderThreads, 0, s>>>(kb, rows, g.n, g.levels, q, m, out);
+    } else {
+      switch (g.k) {
+        case 3: k_point_reorder<K, 2, 3><<<grid, kReorderThreads, 0, s>>>(kb, rows, g.n, g.levels, q, m, out); break;
+        case 5: k_point_reorder<K, 2, 5><<<grid, kReorderThreads, 0, s>>>(kb, rows, g.n, g.levels, q, m, out); break;
+        case 9: k_point_reorder<K, 2, 9><<<grid, kReorderThreads, 0, s>>>(kb, rows, g.n, g.levels, q, m, out); break;
+        case 17: k_point_reorder<K, 2, 17><<<grid, kReorderThreads, 0, s>>>(kb, rows, g.n, g.levels, q, m, out); break;
+        default: done = false; break;  // other fan-outs: the plain kernels below
+      }
+    }
+    if (done) {
+      count_launch();
+      return cudaGetLastError();
+    }
+  }
   if (c.layout == GI_SORTED) {
     const unsigned grid = grid_size(m, block, c.blocks_per_sm);
     k_bs_point<K><<<grid, block, 0, s>>>(keys, rows, g.n, q, m, out);

@@ -298,3 +298,24 @@ def test_duplicate_keys_all_occurrences_by_point_range(replicas):
         want_first = np.where(np.diff(woff) > 0, wrr[np.minimum(woff[:-1], len(wrr) - 1).astype(np.int64)], gi.GI_MISS)
         assert np.array_equal(first, want_first.astype(np.uint32))
         gi.gi_destroy(idx)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+@pytest.mark.parametrize("layout,k", [(gi.GI_SORTED, 0), (gi.GI_EYTZINGER, 2), (gi.GI_EYTZINGER_KARY, 3),
+                                      (gi.GI_EYTZINGER_KARY, 5), (gi.GI_EYTZINGER_KARY, 9),
+                                      (gi.GI_EYTZINGER_KARY, 17), (gi.GI_EYTZINGER_KARY, 4)])
+def test_local_lookup_reordering_changes_nothing(dtype, layout, k):
+    # Section 7.4: probes sorted per CTA tile, results restored to probe order;
+    # ragged last tile, duplicate keys, Zipf-skewed and pre-sorted probes
+    bits = 8 * np.dtype(dtype).itemsize
+    for n, dup in ((123457, False), (50000, True)):
+        keys = W.duplicate_keys(n // 5, 5, bits, 3) if dup else W.unique_keys(n, bits, 3)
+        rows = np.arange(len(keys), dtype=np.uint32)
+        sk, sr = oracle.sort_pairs(keys, rows)
+        idx = build(keys, rows, layout, k)
+        gi.gi_set_option(idx, gi.GI_OPT_REORDER, 1)
+        for q in (W.point_probes(np.unique(keys), 10007, 0.5, bits, 3, 4, dist="zipf", zipf_s=1.25),
+                  np.sort(W.point_probes(np.unique(keys), 20000, 0.5, bits, 3, 5)),
+                  np.array([0, np.iinfo(dtype).max], dtype=dtype)):
+            assert np.array_equal(point(idx, q.astype(dtype)), oracle.point_lookup(sk, sr, q.astype(dtype)))
+        gi.gi_destroy(idx)

@@ -62,6 +62,7 @@ typedef struct gi_index gi_index;
 #define GI_ERR_NOMEM   2 /* device or pinned allocation failed                          */
 #define GI_ERR_CUDA    3 /* a CUDA runtime call failed                                  */
 #define GI_ERR_TIMEOUT 4 /* a bounded device-side wait gave up; results are not valid  */
+#define GI_ERR_CAPACITY 5 /* a served range result is larger than the room given for it */
 
 #define GI_MISS 0xFFFFFFFFu
 
@@ -265,6 +266,53 @@ int gi_batch_copy_index(const gi_batch* batch, uint32_t i, void* keys_out, uint3
 int gi_batch_set_option(gi_batch* batch, int option, int64_t value);
 uint64_t gi_batch_footprint_bytes(const gi_batch* batch);
 void gi_batch_destroy(gi_batch* batch);
+
+/*
+ * Serving form: resident indexes answer a stream of requests with continuous
+ * batching.  The paper measures batches of lookups; this form serves requests
+ * that arrive at any time from many client threads.
+ *
+ * gi_server_create -- serve `count` built indexes (same key width, layout and k;
+ *   GI_SORTED or GI_EYTZINGER_KARY with k in {3, 5, 9, 17}).  `arena_bytes` of
+ *   device memory hold the admitted requests' inputs and results: a request is
+ *   admitted, first-in first-out, only when its bytes fit (admission by free
+ *   device memory).  Up to `max_inflight` batches run at once, each on its own
+ *   stream.  Starts one server thread.  The indexes must outlive the server.
+ * gi_server_submit -- queue a request (thread-safe, returns at once with a
+ *   ticket).  All buffers are HOST memory (pinned memory lets copies overlap):
+ *     GI_REQ_POINT: keys[m] probes -> out_rowids[m] (rowID or GI_MISS);
+ *     GI_REQ_RANGE: keys[m] lower and hi[m] upper bounds (inclusive) ->
+ *       out_offsets[m+1] and, when it fits, out_rowids[rows_capacity] in
+ *       ascending key order.
+ *   A request whose inputs and results exceed the whole arena is refused
+ *   (GI_ERR_NOMEM).  Requests that arrive while batches run join the next batch.
+ * gi_server_wait -- block until the ticket's request completes; returns its
+ *   status.  Ranges whose rows exceed rows_capacity return GI_ERR_CAPACITY with
+ *   out_offsets filled (out_offsets[m] is the row count).  Also reports the
+ *   submit and completion times (steady clock, ns) for latency figures.
+ * gi_server_stats -- batches launched, requests submitted, probes admitted.
+ * gi_server_destroy -- finish queued requests, stop the thread, free the server.
+ */
+typedef struct gi_server gi_server;
+#define GI_REQ_POINT 0
+#define GI_REQ_RANGE 1
+typedef struct gi_request {
+  uint32_t index;          /* which served index */
+  uint32_t kind;           /* GI_REQ_POINT or GI_REQ_RANGE */
+  uint64_t m;              /* probes or ranges, >= 1 */
+  const void* keys;        /* probes, or lower bounds */
+  const void* hi;          /* upper bounds (ranges) */
+  uint32_t* out_rowids;    /* point results, or range rows */
+  uint64_t* out_offsets;   /* range CSR offsets, m+1 */
+  uint64_t rows_capacity;  /* room in out_rowids for range rows */
+} gi_request;
+int gi_server_create(gi_index* const* indexes, uint32_t count, uint64_t arena_bytes,
+                     uint32_t max_inflight, gi_server** out);
+int gi_server_submit(gi_server* server, const gi_request* request, uint64_t* ticket);
+int gi_server_wait(gi_server* server, uint64_t ticket, int64_t* submit_ns, int64_t* done_ns);
+int gi_server_stats(const gi_server* server, uint64_t* batches, uint64_t* requests,
+                    uint64_t* probes);
+void gi_server_destroy(gi_server* server);
 
 /*
  * gi_range_lookup_noalloc -- gi_range_lookup for callers that must not allocate.

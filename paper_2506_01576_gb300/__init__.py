@@ -31,11 +31,14 @@ __all__ = [
     "Batch", "gi_batch_create", "gi_batch_set_stream", "gi_batch_build", "gi_batch_point_lookup",
     "gi_batch_sync", "gi_batch_copy_index", "gi_batch_set_option", "gi_batch_footprint_bytes",
     "gi_batch_destroy", "GI_BATCH_OPT_CHUNK", "GI_BATCH_OPT_BLOCKS_PER_SM", "GI_BATCH_OPT_SMEM_BUDGET",
+    "Server", "gi_request", "gi_server_create", "gi_server_submit", "gi_server_wait", "gi_server_stats",
+    "gi_server_destroy", "GI_REQ_POINT", "GI_REQ_RANGE", "GI_ERR_CAPACITY",
 ]
 
 GI_SORTED, GI_EYTZINGER, GI_EYTZINGER_KARY = 0, 1, 2
 GI_KEY_U32, GI_KEY_U64 = 0x000, 0x100
-GI_OK, GI_ERR_INVALID, GI_ERR_NOMEM, GI_ERR_CUDA, GI_ERR_TIMEOUT = 0, 1, 2, 3, 4
+GI_OK, GI_ERR_INVALID, GI_ERR_NOMEM, GI_ERR_CUDA, GI_ERR_TIMEOUT, GI_ERR_CAPACITY = 0, 1, 2, 3, 4, 5
+GI_REQ_POINT, GI_REQ_RANGE = 0, 1
 GI_MISS = 0xFFFFFFFF
 GI_NOALLOC_MAX_RANGES = 1 << 20
 GI_BATCH_OPT_CHUNK, GI_BATCH_OPT_BLOCKS_PER_SM, GI_BATCH_OPT_SMEM_BUDGET = 1, 2, 3
@@ -51,6 +54,12 @@ class GIError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__("gi error %d: %s" % (code, msg))
         self.code = code
+
+
+class gi_request(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_uint32), ("kind", ctypes.c_uint32), ("m", ctypes.c_uint64),
+                ("keys", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("out_rowids", ctypes.c_void_p),
+                ("out_offsets", ctypes.c_void_p), ("rows_capacity", ctypes.c_uint64)]
 
 
 class gi_info(ctypes.Structure):
@@ -99,6 +108,11 @@ def load(build_if_missing: bool = False):
         "gi_batch_set_option": (I, [P, I, I64]),
         "gi_batch_footprint_bytes": (U64, [P]),
         "gi_batch_destroy": (None, [P]),
+        "gi_server_create": (I, [ctypes.POINTER(P), U32, U64, U32, ctypes.POINTER(P)]),
+        "gi_server_submit": (I, [P, ctypes.POINTER(gi_request), ctypes.POINTER(U64)]),
+        "gi_server_wait": (I, [P, U64, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "gi_server_stats": (I, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64)]),
+        "gi_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -275,6 +289,67 @@ def gi_batch_footprint_bytes(batch: Batch) -> int:
 
 def gi_batch_destroy(batch: Batch) -> None:
     batch.close()
+
+
+class Server:
+    """Handle of a serving engine (owns the C gi_server*)."""
+
+    def __init__(self, handle: int, keep):
+        self._h = handle
+        self._keep = keep  # the served Index handles must outlive the server
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise GIError(GI_ERR_INVALID, "server was destroyed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().gi_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gi_server_create(indexes, arena_bytes: int, max_inflight: int = 3) -> Server:
+    arr = (ctypes.c_void_p * len(indexes))(*[ix.handle for ix in indexes])
+    out = ctypes.c_void_p()
+    _check(load().gi_server_create(arr, len(indexes), arena_bytes, max_inflight, ctypes.byref(out)))
+    return Server(out.value, list(indexes))
+
+
+def gi_server_submit(server: Server, index: int, kind: int, keys, out_rowids=None, hi=None,
+                     out_offsets=None, rows_capacity: int = 0) -> int:
+    """Queue a request on host buffers; returns its ticket."""
+    r = gi_request(index, kind, _len(keys), _ptr(keys), _ptr(hi), _ptr(out_rowids), _ptr(out_offsets),
+                   rows_capacity)
+    t = ctypes.c_uint64()
+    _check(load().gi_server_submit(server.handle, ctypes.byref(r), ctypes.byref(t)))
+    return int(t.value)
+
+
+def gi_server_wait(server: Server, ticket: int):
+    """Block until the request completes; returns (status, submit_ns, done_ns)."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    rc = load().gi_server_wait(server.handle, ticket, ctypes.byref(a), ctypes.byref(b))
+    if rc not in (GI_OK, GI_ERR_CAPACITY):
+        _check(rc)
+    return rc, int(a.value), int(b.value)
+
+
+def gi_server_stats(server: Server):
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().gi_server_stats(server.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return int(a.value), int(b.value), int(c.value)
+
+
+def gi_server_destroy(server: Server) -> None:
+    server.close()
 
 
 def gi_destroy(index: Index) -> None:

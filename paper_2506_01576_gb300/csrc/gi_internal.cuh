@@ -111,6 +111,31 @@ __host__ __device__ __forceinline__ uint64_t rank_to_slot(uint64_t r, const Geom
   return (kpow<KF>(l, g) - 1) + xd * km1 + (x - xd * k) - 1;
 }
 
+// Geometry computed on the device (the host version is make_geom); k >= 2.
+__device__ __forceinline__ Geom device_geom(uint64_t n, uint32_t k) {
+  Geom g;
+  g.n = n;
+  g.k = k;
+  g.log2k = ((k & (k - 1)) == 0) ? (31 - __clz(k)) : 0;
+  g.m = 0;
+  g.top = 0;
+  g.b = n;
+  g.levels = n ? 1 : 0;
+  if (n) {
+    uint64_t p = 1;
+    uint32_t m = 0;
+    while (p <= n / k) {
+      p *= k;
+      ++m;
+    }
+    g.m = m;
+    g.top = p - 1;
+    g.b = n - g.top;
+    g.levels = m + 1;
+  }
+  return g;
+}
+
 // ---------------------------------------------------------------- launch bookkeeping
 void count_launch(uint64_t n = 1);
 void set_last_error(const char* msg);  // the thread's gi_last_error() text

@@ -1,0 +1,781 @@
+// Serving form: a resident set of indexes answers a stream of point and range
+// requests with continuous batching.
+//
+// Client threads submit requests (host buffers) at any time.  One server thread
+// owns the device side:
+//   admission   requests are admitted first-in first-out while a fixed device
+//               arena has room for their inputs and results (the admission
+//               budget); a request that can never fit is rejected at once.
+//   batching    every admitted request, of any index and kind, joins the next
+//               batch; one batch is a handful of launches shared by all of its
+//               requests (lookups and range counts in one kernel, a per-request
+//               scan, a range fill), with the copies in and out on the batch's
+//               own stream.
+//   overlap     up to `max_inflight` batches are on the GPU at once, each on its
+//               own stream, so requests that arrive while others run are admitted
+//               into the next batch as soon as arena space frees up.
+//   ranges      take two passes: the count pass returns the offsets and the total;
+//               the fill is admitted once arena room for the rows is free.
+// Each request's submit and completion times are recorded for latency figures.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gi_internal.cuh"
+#include "gi_point_impl.cuh"
+
+namespace gi {
+namespace sv {
+
+struct ServeIndex {  // device descriptor of a resident index
+  const void* keys;
+  const uint32_t* rows;
+  uint64_t n;
+  uint32_t levels;
+  uint32_t pad;
+};
+
+enum : uint32_t { kItemPoint = 0, kItemCount = 1, kItemFill = 2 };
+
+struct ServeItem {  // one request's share of a batch (device copy of the table)
+  uint64_t in_off;     // arena byte offsets
+  uint64_t in2_off;
+  uint64_t out_off;    // point: results; count/fill: offsets (m+1)
+  uint64_t aux_off;    // count/fill: lower ranks; fill: rows at out2
+  uint64_t rows_off;   // fill: rows
+  uint64_t m;
+  uint64_t work_start;  // first work item of this request in the batch
+  uint32_t index;
+  uint32_t kind;
+};
+
+constexpr uint32_t kChunk = 1024;  // probes or ranges per work item
+
+__device__ __forceinline__ uint32_t find_item(const ServeItem* items, uint32_t count, uint64_t w) {
+  uint32_t lo = 0, hi = count;  // items[lo].work_start <= w < items[hi].work_start
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (items[mid].work_start <= w) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// lower-bound slot (or ~0) of x in a k-ary index, one thread
+template <class K, int KF>
+__device__ __forceinline__ uint64_t eks_bound(const K* __restrict__ keys, uint64_t n, uint32_t levels,
+                                              K x, bool upper) {
+  constexpr int N = KF - 1;
+  uint64_t s = 0, cand = ~0ull;
+  for (uint32_t lv = 0; lv < levels; ++lv) {
+    if (s >= n) break;
+    K piv[N];
+    if constexpr (pt::EksShape<K, KF, 1>::VEC) {
+      pt::vec_load<K, N>(keys + s, piv);
+    } else {
+#pragma unroll
+      for (int p = 0; p < N; ++p) piv[p] = __ldg(keys + s + p);
+    }
+    uint32_t c = 0;
+#pragma unroll
+    for (int p = 0; p < N; ++p) c += (upper ? piv[p] <= x : piv[p] < x) ? 1u : 0u;
+    if (c < (uint32_t)N && s + c < n) cand = s + c;
+    s = s * KF + (uint64_t)(c + 1) * N;
+  }
+  return cand;
+}
+
+template <class K>
+__device__ __forceinline__ uint64_t sorted_bound(const K* __restrict__ keys, uint64_t n, K x, bool upper) {
+  uint64_t lo = 0, len = n;
+  while (len > 0) {
+    const uint64_t half = len >> 1;
+    const K v = __ldg(keys + lo + half);
+    if (upper ? v <= x : v < x) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  return lo;
+}
+
+// KF == 0: sorted layout.  Point lookups and range counts of a whole batch.
+template <class K, int KF>
+__global__ void __launch_bounds__(256) k_serve_lookup(const ServeIndex* __restrict__ idx,
+                                                      const ServeItem* __restrict__ items,
+                                                      uint32_t nitems, uint64_t nwork,
+                                                      unsigned char* __restrict__ arena) {
+  __shared__ uint32_t s_item;
+  for (uint64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
+    if (threadIdx.x == 0) s_item = find_item(items, nitems, w);
+    __syncthreads();
+    const ServeItem it = items[s_item];
+    __syncthreads();
+    if (it.kind == kItemFill) continue;
+    const ServeIndex d = idx[it.index];
+    const K* keys = (const K*)d.keys;
+    const uint64_t i0 = (w - it.work_start) * kChunk;
+    const uint64_t i1 = min(i0 + kChunk, it.m);
+    const K* q = (const K*)(arena + it.in_off);
+    if (it.kind == kItemPoint) {
+      uint32_t* out = (uint32_t*)(arena + it.out_off);
+      for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const K x = q[i];
+        uint32_t res = GI_MISS;
+        if constexpr (KF > 0) {
+          const uint64_t c = eks_bound<K, KF>(keys, d.n, d.levels, x, false);
+          if (c != ~0ull && __ldg(keys + c) == x) res = __ldg(d.rows + c);
+        } else {
+          const uint64_t c = sorted_bound<K>(keys, d.n, x, false);
+          if (c < d.n && __ldg(keys + c) == x) res = __ldg(d.rows + c);
+        }
+        out[i] = res;
+      }
+    } else {  // range count: lower rank of L, upper rank of U
+      const K* hi = (const K*)(arena + it.in2_off);
+      uint64_t* cnt = (uint64_t*)(arena + it.out_off);
+      uint64_t* lo_rank = (uint64_t*)(arena + it.aux_off);
+      const Geom g = device_geom(d.n, KF > 1 ? (uint32_t)KF : 2u);
+      for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const K L = q[i], U = hi[i];
+        uint64_t rl = 0, ru = 0;
+        if (L <= U) {
+          if constexpr (KF > 0) {
+            const uint64_t a = eks_bound<K, KF>(keys, d.n, d.levels, L, false);
+            const uint64_t b = eks_bound<K, KF>(keys, d.n, d.levels, U, true);
+            rl = a != ~0ull ? slot_to_rank<KF>(a, g) : d.n;
+            ru = b != ~0ull ? slot_to_rank<KF>(b, g) : d.n;
+          } else {
+            rl = sorted_bound<K>(keys, d.n, L, false);
+            ru = sorted_bound<K>(keys, d.n, U, true);
+          }
+        }
+        cnt[i] = ru - rl;
+        lo_rank[i] = rl;
+      }
+    }
+  }
+}
+
+// exclusive scan of one count item's counts, in place, total at [m]; one CTA per item
+__global__ void __launch_bounds__(1024) k_serve_scan(const ServeItem* __restrict__ items,
+                                                     const uint32_t* __restrict__ count_items,
+                                                     unsigned char* __restrict__ arena) {
+  __shared__ uint64_t s_warp[32];
+  const ServeItem it = items[count_items[blockIdx.x]];
+  uint64_t* a = (uint64_t*)(arena + it.out_off);
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  uint64_t carry = 0;
+  for (uint64_t base = 0; base < it.m; base += blockDim.x) {
+    const uint64_t j = base + threadIdx.x;
+    const uint64_t v = j < it.m ? a[j] : 0;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wp] = x;
+    __syncthreads();
+    uint64_t pre = 0, tot = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      if (i < wp) pre += s_warp[i];
+      tot += s_warp[i];
+    }
+    if (j < it.m) a[j] = carry + pre + x - v;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a[it.m] = carry;
+}
+
+// range fill: rows of rank r come from slot(r); a warp per 32 ranges, ranges of
+// >= 32 rows done by the whole warp
+template <int KF>
+__global__ void __launch_bounds__(256) k_serve_fill(const ServeIndex* __restrict__ idx,
+                                                    const ServeItem* __restrict__ items,
+                                                    uint32_t nitems, uint64_t nwork,
+                                                    unsigned char* __restrict__ arena) {
+  __shared__ uint32_t s_item;
+  const int lane = threadIdx.x & 31;
+  for (uint64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
+    if (threadIdx.x == 0) s_item = find_item(items, nitems, w);
+    __syncthreads();
+    const ServeItem it = items[s_item];
+    __syncthreads();
+    if (it.kind != kItemFill) continue;
+    const ServeIndex d = idx[it.index];
+    const Geom g = device_geom(d.n, KF > 1 ? (uint32_t)KF : 2u);
+    const uint64_t* offs = (const uint64_t*)(arena + it.out_off);
+    const uint64_t* lo_rank = (const uint64_t*)(arena + it.aux_off);
+    uint32_t* out = (uint32_t*)(arena + it.rows_off);
+    const uint64_t i0 = (w - it.work_start) * kChunk;
+    const uint64_t i1 = min(i0 + kChunk, it.m);
+    for (uint64_t wb = i0 + (threadIdx.x >> 5) * 32; wb < i1; wb += (blockDim.x >> 5) * 32) {
+      const uint64_t i = wb + lane;
+      uint64_t off = 0, cnt = 0, r0 = 0;
+      if (i < i1) {
+        off = offs[i];
+        cnt = offs[i + 1] - off;
+        r0 = lo_rank[i];
+      }
+      auto slot = [&](uint64_t r) -> uint64_t {
+        if constexpr (KF > 0) return rank_to_slot<KF>(r, g);
+        else return r;
+      };
+      const bool big = cnt >= 32;
+      uint32_t bm = __ballot_sync(0xffffffffu, big);
+      while (bm) {
+        const int b = __ffs(bm) - 1;
+        bm &= bm - 1;
+        const uint64_t bo = __shfl_sync(0xffffffffu, off, b);
+        const uint64_t bc = __shfl_sync(0xffffffffu, cnt, b);
+        const uint64_t br = __shfl_sync(0xffffffffu, r0, b);
+        for (uint64_t j = lane; j < bc; j += 32) out[bo + j] = __ldg(d.rows + slot(br + j));
+      }
+      if (!big)
+        for (uint64_t j = 0; j < cnt; ++j) out[off + j] = __ldg(d.rows + slot(r0 + j));
+    }
+  }
+}
+
+}  // namespace sv
+}  // namespace gi
+
+// ================================================================= host side
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over the arena (byte offsets), 256-byte granules.
+class Arena {
+ public:
+  void init(uint64_t bytes) {
+    total_ = bytes;
+    free_.clear();
+    free_[0] = bytes;
+  }
+  bool alloc(uint64_t bytes, uint64_t* off) {
+    bytes = (bytes + 255) & ~255ull;
+    if (bytes == 0) bytes = 256;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const uint64_t rest = it->second - bytes, at = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[at] = rest;
+        used_ += bytes;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t bytes) {
+    bytes = (bytes + 255) & ~255ull;
+    if (bytes == 0) bytes = 256;
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  uint64_t total() const { return total_; }
+  uint64_t used() const { return used_; }
+
+ private:
+  uint64_t total_ = 0, used_ = 0;
+  std::map<uint64_t, uint64_t> free_;
+};
+
+struct Block {
+  uint64_t off = 0, bytes = 0;
+  bool live = false;
+};
+
+struct Req {
+  gi_request r;
+  uint64_t ticket = 0;
+  int phase = 0;  // 0 queued, 1 point/count in flight, 2 counted, 3 fill in flight, 4 done
+  int status = GI_OK;
+  Block in, in2, out, aux, rows;
+  uint64_t total = 0;
+  int64_t t_submit = 0, t_done = 0;
+};
+
+struct Batch {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  gi::sv::ServeItem* h_items = nullptr;  // pinned
+  gi::sv::ServeItem* d_items = nullptr;
+  uint32_t* h_count_items = nullptr;     // pinned
+  uint32_t* d_count_items = nullptr;
+  uint32_t capacity = 0;
+  std::vector<std::shared_ptr<Req>> reqs;
+  bool busy = false;
+};
+
+}  // namespace
+
+struct gi_server {
+  int device = 0;
+  int key_bytes = 8;
+  int layout = GI_EYTZINGER_KARY;
+  uint32_t k = 0;
+  uint32_t nidx = 0;
+  gi::sv::ServeIndex* d_idx = nullptr;
+  std::vector<gi::sv::ServeIndex> h_idx;
+  unsigned char* arena = nullptr;
+  Arena alloc;
+  uint64_t max_batch = 1ull << 22;
+  std::vector<Batch> batches;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_submit, cv_done;
+  std::deque<std::shared_ptr<Req>> incoming;
+  std::unordered_map<uint64_t, std::shared_ptr<Req>> by_ticket;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::atomic<uint64_t> n_batches{0}, n_requests{0}, n_probes{0};
+  int fatal = GI_OK;
+};
+
+namespace {
+
+int sfail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  gi::set_last_error(buf);
+  return code;
+}
+
+uint64_t in_bytes(const gi_request& r, int kb) { return r.m * kb; }
+
+void free_block(gi_server* s, Block& b) {
+  if (b.live) s->alloc.release(b.off, b.bytes);
+  b.live = false;
+}
+
+bool take_block(gi_server* s, Block& b, uint64_t bytes) {
+  if (!s->alloc.alloc(bytes, &b.off)) return false;
+  b.bytes = bytes;
+  b.live = true;
+  return true;
+}
+
+// reserve arena room for a request's next phase; false if it does not fit now
+bool admit(gi_server* s, Req& q) {
+  const int kb = s->key_bytes;
+  const uint64_t m = q.r.m;
+  if (q.phase == 0 && q.r.kind == GI_REQ_POINT) {
+    if (!take_block(s, q.in, m * kb)) return false;
+    if (!take_block(s, q.out, m * 4)) {
+      free_block(s, q.in);
+      return false;
+    }
+    return true;
+  }
+  if (q.phase == 0) {  // range count
+    if (!take_block(s, q.in, m * kb)) return false;
+    if (!take_block(s, q.in2, m * kb)) { free_block(s, q.in); return false; }
+    if (!take_block(s, q.out, (m + 1) * 8)) { free_block(s, q.in); free_block(s, q.in2); return false; }
+    if (!take_block(s, q.aux, m * 8)) {
+      free_block(s, q.in); free_block(s, q.in2); free_block(s, q.out);
+      return false;
+    }
+    return true;
+  }
+  // fill: rows of the counted ranges
+  return take_block(s, q.rows, std::max<uint64_t>(q.total, 1) * 4);
+}
+
+// bytes a request needs at its largest phase (for the can-never-fit check)
+uint64_t peak_bytes(const gi_request& r, int kb) {
+  auto g = [](uint64_t b) { return (std::max<uint64_t>(b, 1) + 255) & ~255ull; };
+  if (r.kind == GI_REQ_POINT) return g(r.m * kb) + g(r.m * 4);
+  return g(r.m * kb) * 2 + g((r.m + 1) * 8) + g(r.m * 8);
+}
+
+void launch_batch(gi_server* s, Batch& b) {
+  using namespace gi::sv;
+  const int kb = s->key_bytes;
+  cudaStream_t st = b.stream;
+  uint32_t n = 0, ncount = 0;
+  uint64_t work = 0, fill_work = 0;
+  // lookups and counts first, then fills (two work ranges in one table)
+  for (auto& q : b.reqs) {
+    if (q->phase == 3) continue;
+    ServeItem& it = b.h_items[n++];
+    it.index = q->r.index;
+    it.m = q->r.m;
+    it.in_off = q->in.off;
+    it.in2_off = q->in2.off;
+    it.out_off = q->out.off;
+    it.aux_off = q->aux.off;
+    it.rows_off = 0;
+    it.kind = q->r.kind == GI_REQ_POINT ? kItemPoint : kItemCount;
+    it.work_start = work;
+    work += (q->r.m + kChunk - 1) / kChunk;
+    if (it.kind == kItemCount) b.h_count_items[ncount++] = n - 1;
+    cudaMemcpyAsync(s->arena + q->in.off, q->r.keys, q->r.m * kb, cudaMemcpyHostToDevice, st);
+    if (it.kind == kItemCount)
+      cudaMemcpyAsync(s->arena + q->in2.off, q->r.hi, q->r.m * kb, cudaMemcpyHostToDevice, st);
+  }
+  const uint32_t nlook = n;
+  for (auto& q : b.reqs) {
+    if (q->phase != 3) continue;
+    ServeItem& it = b.h_items[n++];
+    it.index = q->r.index;
+    it.m = q->r.m;
+    it.out_off = q->out.off;
+    it.aux_off = q->aux.off;
+    it.rows_off = q->rows.off;
+    it.in_off = it.in2_off = 0;
+    it.kind = kItemFill;
+    it.work_start = fill_work;
+    fill_work += (q->r.m + kChunk - 1) / kChunk;
+  }
+  cudaMemcpyAsync(b.d_items, b.h_items, n * sizeof(ServeItem), cudaMemcpyHostToDevice, st);
+  if (ncount)
+    cudaMemcpyAsync(b.d_count_items, b.h_count_items, ncount * 4, cudaMemcpyHostToDevice, st);
+  const unsigned cap = (unsigned)(gi::sm_count() * 8);
+  auto grid = [&](uint64_t w) { return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(w, cap)); };
+#define GI_SV(K, KF)                                                                              \
+  do {                                                                                            \
+    if (nlook) {                                                                                  \
+      k_serve_lookup<K, KF><<<grid(work), 256, 0, st>>>(s->d_idx, b.d_items, nlook, work, s->arena); \
+      gi::count_launch();                                                                         \
+    }                                                                                             \
+    if (ncount) {                                                                                 \
+      k_serve_scan<<<ncount, 1024, 0, st>>>(b.d_items, b.d_count_items, s->arena);                \
+      gi::count_launch();                                                                         \
+    }                                                                                             \
+    if (n > nlook) {                                                                              \
+      k_serve_fill<KF><<<grid(fill_work), 256, 0, st>>>(s->d_idx, b.d_items + nlook, n - nlook,  \
+                                                        fill_work, s->arena);                     \
+      gi::count_launch();                                                                         \
+    }                                                                                             \
+  } while (0)
+  if (kb == 8) {
+    switch (s->k) {
+      case 0: GI_SV(uint64_t, 0); break;
+      case 3: GI_SV(uint64_t, 3); break;
+      case 5: GI_SV(uint64_t, 5); break;
+      case 9: GI_SV(uint64_t, 9); break;
+      default: GI_SV(uint64_t, 17); break;
+    }
+  } else {
+    switch (s->k) {
+      case 0: GI_SV(uint32_t, 0); break;
+      case 3: GI_SV(uint32_t, 3); break;
+      case 5: GI_SV(uint32_t, 5); break;
+      case 9: GI_SV(uint32_t, 9); break;
+      default: GI_SV(uint32_t, 17); break;
+    }
+  }
+#undef GI_SV
+  // results back to the callers' host buffers
+  for (auto& q : b.reqs) {
+    if (q->phase == 3) {
+      if (q->total)
+        cudaMemcpyAsync(q->r.out_rowids, s->arena + q->rows.off, q->total * 4, cudaMemcpyDeviceToHost, st);
+    } else if (q->r.kind == GI_REQ_POINT) {
+      cudaMemcpyAsync(q->r.out_rowids, s->arena + q->out.off, q->r.m * 4, cudaMemcpyDeviceToHost, st);
+    } else {
+      cudaMemcpyAsync(q->r.out_offsets, s->arena + q->out.off, (q->r.m + 1) * 8, cudaMemcpyDeviceToHost, st);
+    }
+  }
+  cudaEventRecord(b.done, st);
+  b.busy = true;
+  s->n_batches++;
+}
+
+// a finished batch: complete its requests or move counted ranges to the fill phase
+void retire_batch(gi_server* s, Batch& b, std::deque<std::shared_ptr<Req>>& fills) {
+  cudaError_t e = cudaEventQuery(b.done);
+  if (e == cudaErrorNotReady) return;
+  if (e != cudaSuccess) {
+    s->fatal = GI_ERR_CUDA;
+    cudaGetLastError();
+  }
+  const int64_t t = now_ns();
+  std::vector<std::shared_ptr<Req>> done;
+  for (auto& q : b.reqs) {
+    if (q->r.kind == GI_REQ_POINT) {
+      free_block(s, q->in);
+      free_block(s, q->out);
+      q->phase = 4;
+      done.push_back(q);
+    } else if (q->phase == 1) {  // counted
+      free_block(s, q->in);
+      free_block(s, q->in2);
+      q->total = q->r.out_offsets[q->r.m];
+      if (q->total > q->r.rows_capacity) {
+        q->status = GI_ERR_CAPACITY;
+        free_block(s, q->out);
+        free_block(s, q->aux);
+        q->phase = 4;
+        done.push_back(q);
+      } else {
+        q->phase = 2;
+        fills.push_back(q);
+      }
+    } else {  // filled
+      free_block(s, q->out);
+      free_block(s, q->aux);
+      free_block(s, q->rows);
+      q->phase = 4;
+      done.push_back(q);
+    }
+  }
+  if (s->fatal != GI_OK)
+    for (auto& q : b.reqs) q->status = s->fatal;
+  b.reqs.clear();
+  b.busy = false;
+  if (!done.empty()) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto& q : done) q->t_done = t;
+  }
+  s->cv_done.notify_all();
+}
+
+void server_loop(gi_server* s) {
+  cudaSetDevice(s->device);
+  std::deque<std::shared_ptr<Req>> queue, fills;
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      const bool idle = queue.empty() && fills.empty() &&
+                        std::none_of(s->batches.begin(), s->batches.end(), [](const Batch& b) { return b.busy; });
+      if (idle && s->incoming.empty() && !s->stop)
+        s->cv_submit.wait_for(lk, std::chrono::milliseconds(2));
+      if (s->stop && s->incoming.empty() && idle) return;
+      while (!s->incoming.empty()) {
+        queue.push_back(s->incoming.front());
+        s->incoming.pop_front();
+      }
+    }
+    for (auto& b : s->batches)
+      if (b.busy) retire_batch(s, b, fills);
+    // a free batch slot takes every request whose memory can be reserved now:
+    // counted ranges first (they hold memory already), then new requests in order
+    Batch* slot = nullptr;
+    for (auto& b : s->batches)
+      if (!b.busy) {
+        slot = &b;
+        break;
+      }
+    if (!slot) {
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      continue;
+    }
+    uint64_t probes = 0;
+    while (!fills.empty() && slot->reqs.size() < slot->capacity && probes < s->max_batch) {
+      auto& q = fills.front();
+      if (!admit(s, *q)) break;
+      q->phase = 3;
+      probes += q->r.m;
+      slot->reqs.push_back(q);
+      fills.pop_front();
+    }
+    while (!queue.empty() && slot->reqs.size() < slot->capacity && probes < s->max_batch) {
+      auto& q = queue.front();
+      if (!admit(s, *q)) break;  // first-in first-out: later requests wait too
+      q->phase = 1;
+      probes += q->r.m;
+      slot->reqs.push_back(q);
+      queue.pop_front();
+    }
+    if (!slot->reqs.empty()) {
+      s->n_probes += probes;
+      launch_batch(s, *slot);
+    } else {
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int gi_server_create(gi_index* const* indexes, uint32_t count, uint64_t arena_bytes,
+                     uint32_t max_inflight, gi_server** out) {
+  gi::set_last_error("");
+  if (!out) return sfail(GI_ERR_INVALID, "gi_server_create: out is NULL");
+  *out = nullptr;
+  if (!indexes || count == 0) return sfail(GI_ERR_INVALID, "gi_server_create: no indexes");
+  if (arena_bytes < (1u << 20)) return sfail(GI_ERR_INVALID, "gi_server_create: arena below 1 MiB");
+  if (max_inflight == 0 || max_inflight > 16) return sfail(GI_ERR_INVALID, "gi_server_create: 1..16 batches in flight");
+  gi_server* s = new gi_server();
+  cudaGetDevice(&s->device);
+  for (uint32_t i = 0; i < count; ++i) {
+    gi_info inf;
+    if (!indexes[i] || gi_get_info(indexes[i], &inf) != GI_OK) {
+      delete s;
+      return sfail(GI_ERR_INVALID, "gi_server_create: index %u is not valid", i);
+    }
+    const int lay = inf.layout;
+    const uint32_t k = lay == GI_SORTED ? 0 : inf.k;
+    if (i == 0) {
+      s->key_bytes = (int)inf.key_bytes;
+      s->layout = lay;
+      s->k = k;
+      if (!(lay == GI_SORTED || (lay == GI_EYTZINGER_KARY && (k == 3 || k == 5 || k == 9 || k == 17)))) {
+        delete s;
+        return sfail(GI_ERR_INVALID, "gi_server_create: indexes must be GI_SORTED or GI_EYTZINGER_KARY with k in {3,5,9,17}");
+      }
+    } else if ((int)inf.key_bytes != s->key_bytes || lay != s->layout || k != s->k) {
+      delete s;
+      return sfail(GI_ERR_INVALID, "gi_server_create: all indexes need the same key width, layout and k");
+    }
+    gi::sv::ServeIndex d{};
+    d.keys = inf.keys;
+    d.rows = inf.rowids;
+    d.n = inf.n;
+    d.levels = lay == GI_SORTED ? 0 : inf.levels;
+    s->h_idx.push_back(d);
+  }
+  s->nidx = count;
+  auto fail_cuda = [&](cudaError_t e, const char* what) {
+    cudaGetLastError();
+    for (auto& b : s->batches) {
+      if (b.stream) cudaStreamDestroy(b.stream);
+      if (b.done) cudaEventDestroy(b.done);
+      cudaFreeHost(b.h_items);
+      cudaFree(b.d_items);
+      cudaFreeHost(b.h_count_items);
+      cudaFree(b.d_count_items);
+    }
+    cudaFree(s->d_idx);
+    cudaFree(s->arena);
+    delete s;
+    return sfail(e == cudaErrorMemoryAllocation ? GI_ERR_NOMEM : GI_ERR_CUDA, "gi_server_create: %s: %s",
+                 what, cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&s->d_idx, count * sizeof(gi::sv::ServeIndex))) != cudaSuccess) return fail_cuda(e, "descriptors");
+  if ((e = cudaMemcpy(s->d_idx, s->h_idx.data(), count * sizeof(gi::sv::ServeIndex), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail_cuda(e, "descriptors");
+  if ((e = cudaMalloc((void**)&s->arena, arena_bytes)) != cudaSuccess) return fail_cuda(e, "arena");
+  s->alloc.init(arena_bytes);
+  s->batches.resize(max_inflight);
+  for (auto& b : s->batches) {
+    b.capacity = 4096;
+    if ((e = cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking)) != cudaSuccess) return fail_cuda(e, "stream");
+    if ((e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming)) != cudaSuccess) return fail_cuda(e, "event");
+    if ((e = cudaMallocHost((void**)&b.h_items, b.capacity * sizeof(gi::sv::ServeItem))) != cudaSuccess) return fail_cuda(e, "tables");
+    if ((e = cudaMalloc((void**)&b.d_items, b.capacity * sizeof(gi::sv::ServeItem))) != cudaSuccess) return fail_cuda(e, "tables");
+    if ((e = cudaMallocHost((void**)&b.h_count_items, b.capacity * 4)) != cudaSuccess) return fail_cuda(e, "tables");
+    if ((e = cudaMalloc((void**)&b.d_count_items, b.capacity * 4)) != cudaSuccess) return fail_cuda(e, "tables");
+  }
+  s->worker = std::thread(server_loop, s);
+  *out = s;
+  return GI_OK;
+}
+
+int gi_server_submit(gi_server* s, const gi_request* r, uint64_t* ticket) {
+  gi::set_last_error("");
+  if (!s || !r || !ticket) return sfail(GI_ERR_INVALID, "gi_server_submit: NULL argument");
+  if (r->index >= s->nidx) return sfail(GI_ERR_INVALID, "gi_server_submit: index %u out of range", r->index);
+  if (r->kind != GI_REQ_POINT && r->kind != GI_REQ_RANGE) return sfail(GI_ERR_INVALID, "gi_server_submit: bad kind");
+  if (r->m == 0) return sfail(GI_ERR_INVALID, "gi_server_submit: empty request");
+  if (!r->keys || (r->kind == GI_REQ_RANGE && (!r->hi || !r->out_offsets)) ||
+      (r->kind == GI_REQ_POINT && !r->out_rowids) ||
+      (r->kind == GI_REQ_RANGE && r->rows_capacity && !r->out_rowids))
+    return sfail(GI_ERR_INVALID, "gi_server_submit: missing buffer");
+  if (peak_bytes(*r, s->key_bytes) > s->alloc.total())
+    return sfail(GI_ERR_NOMEM, "gi_server_submit: the request needs more than the whole arena");
+  auto q = std::make_shared<Req>();
+  q->r = *r;
+  q->t_submit = now_ns();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    q->ticket = s->next_ticket++;
+    s->by_ticket[q->ticket] = q;
+    s->incoming.push_back(q);
+  }
+  s->n_requests++;
+  s->cv_submit.notify_one();
+  *ticket = q->ticket;
+  return GI_OK;
+}
+
+int gi_server_wait(gi_server* s, uint64_t ticket, int64_t* submit_ns, int64_t* done_ns) {
+  gi::set_last_error("");
+  if (!s) return sfail(GI_ERR_INVALID, "gi_server_wait: NULL server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->by_ticket.find(ticket);
+  if (it == s->by_ticket.end()) return sfail(GI_ERR_INVALID, "gi_server_wait: unknown ticket");
+  auto q = it->second;
+  s->cv_done.wait(lk, [&] { return q->t_done != 0; });
+  s->by_ticket.erase(it);
+  if (submit_ns) *submit_ns = q->t_submit;
+  if (done_ns) *done_ns = q->t_done;
+  if (q->status == GI_ERR_CAPACITY)
+    return sfail(GI_ERR_CAPACITY, "range result of %llu rows exceeds rows_capacity", (unsigned long long)q->total);
+  if (q->status != GI_OK) return sfail(q->status, "request failed on the device");
+  return GI_OK;
+}
+
+int gi_server_stats(const gi_server* s, uint64_t* batches, uint64_t* requests, uint64_t* probes) {
+  if (!s) return sfail(GI_ERR_INVALID, "gi_server_stats: NULL server");
+  if (batches) *batches = s->n_batches.load();
+  if (requests) *requests = s->n_requests.load();
+  if (probes) *probes = s->n_probes.load();
+  return GI_OK;
+}
+
+void gi_server_destroy(gi_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_submit.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (auto& b : s->batches) {
+    if (b.stream) cudaStreamSynchronize(b.stream);
+    if (b.stream) cudaStreamDestroy(b.stream);
+    if (b.done) cudaEventDestroy(b.done);
+    cudaFreeHost(b.h_items);
+    cudaFree(b.d_items);
+    cudaFreeHost(b.h_count_items);
+    cudaFree(b.d_count_items);
+  }
+  cudaFree(s->d_idx);
+  cudaFree(s->arena);
+  cudaGetLastError();
+  delete s;
+}
+
+}  // extern "C"

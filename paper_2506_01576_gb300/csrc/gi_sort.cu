@@ -541,31 +541,6 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_batch_sort_pass(
   }
 }
 
-// Geometry of index s computed on the device (the host version is make_geom).
-__device__ __forceinline__ Geom device_geom(uint64_t n, uint32_t k) {
-  Geom g;
-  g.n = n;
-  g.k = k;
-  g.log2k = ((k & (k - 1)) == 0) ? (31 - __clz(k)) : 0;
-  g.m = 0;
-  g.top = 0;
-  g.b = n;
-  g.levels = n ? 1 : 0;
-  if (n) {
-    uint64_t p = 1;
-    uint32_t m = 0;
-    while (p <= n / k) {
-      p *= k;
-      ++m;
-    }
-    g.m = m;
-    g.top = p - 1;
-    g.b = n - g.top;
-    g.levels = m + 1;
-  }
-  return g;
-}
-
 // slot t of index s <- sorted position slot_to_rank(t); k = 0: the sorted order itself
 template <class K, int KF>
 __global__ void __launch_bounds__(256) k_batch_gather(const K* __restrict__ sk,

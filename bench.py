@@ -62,10 +62,16 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="timed steps only (for profiler launch lists)")
-    ap.add_argument("--workload", default="point", choices=["point", "batched", "ranges", "dups", "skew"],
+    ap.add_argument("--workload", default="point",
+                    choices=["point", "batched", "ranges", "dups", "skew", "serve"],
                     help="point: the 2^26-key step (default); batched: 4096 indexes in one graph; "
                          "ranges: 2^24 ranges on 2^26 u32 keys; dups: replicated keys, point = range [x, x]")
     ap.add_argument("--batch-k", type=int, default=5)
+    ap.add_argument("--serve-indexes", type=int, default=64)
+    ap.add_argument("--serve-min-log", type=int, default=20)
+    ap.add_argument("--serve-max-log", type=int, default=27)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-rates", default="2000,8000,32000,64000")
     ap.add_argument("--batch-indexes", type=int, default=4096)
     ap.add_argument("--probe-sweep", action="store_true",
                     help="print random-access throughput over buffer sizes (L2 vs HBM) and exit")
@@ -765,9 +771,121 @@ def run_skew(a):
         gi.gi_destroy(v)
 
 
+def run_serving(a):
+    """Serving form: resident indexes (2^20..2^27 u64 keys, log-uniform sizes), Poisson
+    arrivals, requests of 1..2^16 probes (log-uniform), 80% point (hit rate 0.5), 20%
+    range (16 expected rows).  For each offered load: the continuous-batching server
+    (gi_server_*) and, as the baseline, one request at a time through gi_point_lookup /
+    gi_range_lookup (a FIFO queue alone).  Reports lookups/s and p50/p99 latency."""
+    import threading
+
+    import torch
+
+    import paper_2506_01576_gb300 as gi
+    gi.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(77)
+    NI = a.serve_indexes
+    sizes = np.exp2(rng.uniform(a.serve_min_log, a.serve_max_log, size=NI)).astype(np.int64)
+    idx, pool = [], []
+    layout = gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64
+    per_index_requests = max(8, 3000 // NI)
+    for i, n in enumerate(sizes):
+        keys = W.unique_keys(int(n), 64, W.seed_for(5, 27, i))
+        kd = torch.from_numpy(keys.view(np.int64)).to(dev)
+        rd = torch.arange(int(n), dtype=torch.int32, device=dev)
+        idx.append(gi.gi_build(kd, rd, layout, 5))
+        del kd, rd
+        for _ in range(per_index_requests):
+            m = int(np.exp2(rng.uniform(0, 16)))
+            pin = lambda x: torch.from_numpy(x.view(np.int64)).pin_memory()
+            if rng.random() < 0.8:
+                q = W.point_probes(keys, m, 0.5, 64, W.seed_for(5, 27, i), int(rng.integers(1 << 30)))
+                pool.append(("point", i, pin(q), torch.empty(m, dtype=torch.int32).pin_memory()))
+            else:
+                lo, hi, _ = W.ranges_with_expected_rows(int(n), m, 16, 64, int(rng.integers(1 << 30)))
+                cap = 64 * m + 256
+                pool.append(("range", i, pin(lo), pin(hi), torch.empty(m + 1, dtype=torch.int64).pin_memory(),
+                             torch.empty(cap, dtype=torch.int32).pin_memory(), cap))
+        del keys
+    torch.cuda.synchronize()
+    order = rng.permutation(len(pool))
+    mean_m = float(np.mean([p[2].numel() for p in pool]))
+
+    def schedule(rate):
+        t, out = 0.0, []
+        r2 = np.random.default_rng(int(rate))
+        while t < a.serve_seconds:
+            t += r2.exponential(1.0 / rate)
+            out.append((t, pool[order[len(out) % len(pool)]]))
+        return out
+
+    def summarize(mode, rate, lat, probes, wall):
+        lat = np.array(lat) / 1e6
+        print(json.dumps({"workload": "serve", "mode": mode, "offered_requests_per_s": rate,
+                          "offered_lookups_per_s": rate * mean_m, "requests": len(lat),
+                          "lookups_per_s": probes / wall, "p50_ms": float(np.percentile(lat, 50)),
+                          "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall,
+                          "indexes": NI, "keys_total": int(sizes.sum())}), flush=True)
+
+    rates = [float(x) for x in a.serve_rates.split(",")]
+    server = gi.gi_server_create(idx, 2 << 30, 3)
+    for rate in rates:
+        sched = schedule(rate)
+        tickets = [None] * len(sched)
+        t0 = time.perf_counter()
+
+        def producer():
+            for j, (t, req) in enumerate(sched):
+                d = t - (time.perf_counter() - t0)
+                if d > 0:
+                    time.sleep(d)
+                if req[0] == "point":
+                    tickets[j] = gi.gi_server_submit(server, req[1], gi.GI_REQ_POINT, req[2], out_rowids=req[3])
+                else:
+                    tickets[j] = gi.gi_server_submit(server, req[1], gi.GI_REQ_RANGE, req[2], out_rowids=req[5],
+                                                     hi=req[3], out_offsets=req[4], rows_capacity=req[6])
+
+        th = threading.Thread(target=producer)
+        th.start()
+        lat, probes = [], 0
+        for j in range(len(sched)):
+            while tickets[j] is None:
+                time.sleep(0.0001)
+            st, ts, td = gi.gi_server_wait(server, tickets[j])
+            lat.append(td - ts)
+            probes += sched[j][1][2].numel()
+        th.join()
+        summarize("server (continuous batching)", rate, lat, probes, time.perf_counter() - t0)
+    gi.gi_server_destroy(server)
+    # baseline: one request at a time, in arrival order, through the plain calls
+    for rate in rates:
+        sched = schedule(rate)
+        t0 = time.perf_counter()
+        lat, probes = [], 0
+        for t, req in sched:
+            now = time.perf_counter() - t0
+            if now > 4 * a.serve_seconds:  # saturated: the queue only grows
+                break
+            if t > now:
+                time.sleep(t - now)
+            if req[0] == "point":
+                gi.gi_point_lookup(idx[req[1]], req[2], req[3])
+            else:
+                gi.gi_range_lookup(idx[req[1]], req[2], req[3], req[4], req[5])
+            lat.append(((time.perf_counter() - t0) - t) * 1e9)
+            probes += req[2].numel()
+        summarize("one request at a time", rate, lat, probes, time.perf_counter() - t0)
+    for ix in idx:
+        gi.gi_destroy(ix)
+
+
 if __name__ == "__main__":
     args = parse()
-    if args.workload == "skew":
+    if args.workload == "serve":
+        run_serving(args)
+    elif args.workload == "skew":
         run_skew(args)
     elif args.workload == "ranges":
         run_ranges(args)

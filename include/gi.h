@@ -55,6 +55,12 @@ typedef struct gi_index gi_index;
 /* Key width, OR-ed into `layout`. */
 #define GI_KEY_U32 0x000
 #define GI_KEY_U64 0x100
+/* Build flag, OR-ed into `layout` of gi_build: sort with the plain 8-bit LSD radix
+ * passes only.  By default a large build first scatters by its top one or two
+ * non-trivial digits (stable) and then sorts every resulting bucket inside one
+ * CTA's shared memory, which takes fewer passes over global memory; it falls
+ * back to the LSD passes when a bucket is too large.  Same result either way. */
+#define GI_BUILD_LSD 0x10000
 
 /* Return codes. */
 #define GI_OK          0
@@ -75,7 +81,7 @@ typedef struct gi_index gi_index;
  *   k       fan-out for GI_EYTZINGER_KARY, 2 <= k <= 33 (nodes of k-1 keys); the
  *           paper prefers k-1 a power of two (Section 6.1).  Ignored otherwise.
  *   out     receives the new index.
- * The pairs are key-value radix sorted (stable) and, for the Eytzinger layouts,
+ * The pairs are key-value radix sorted (stable; see GI_BUILD_LSD) and, for the Eytzinger layouts,
  * moved into place by the closed-form permutation of Sections 4 and 6.1.  Runs on
  * the thread's default gi stream (gi_set_stream(NULL, s)); returns after the index
  * is complete.  The index stores exactly n keys and n rowIDs (plus the empty slot

@@ -173,11 +173,14 @@ gi::LookupCfg resolve_cfg(const gi_index* idx) {
   if (o[GI_OPT_HOT_LEVELS] >= 0) {
     c.hot_levels = (int)o[GI_OPT_HOT_LEVELS];
   } else {
-    // keep the top levels that fit in about two thirds of L2 (the rest of L2
-    // absorbs the streamed probes, results and deep-level lines)
+    // evict-last for the top levels that fit in a quarter of L2.  Measured at
+    // 2^26 u64 keys, k = 5: marking the levels within a quarter of L2 (0..8,
+    // 16 MB) is the best setting; marking those within two thirds (0..9, 78 MB)
+    // is 7% slower than no hints at all, as the evict-last lines then crowd out
+    // the lines of the level below that the lookups reuse.
     int dev = idx->device, l2 = 0;
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
-    c.hot_levels = gi::levels_within(idx->geom, idx->key_bytes, (uint64_t)l2 * 2 / 3);
+    c.hot_levels = gi::levels_within(idx->geom, idx->key_bytes, (uint64_t)l2 / 4);
   }
   return c;
 }
@@ -384,8 +387,10 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   if (!out) return fail(GI_ERR_INVALID, "gi_build: out is NULL");
   *out = nullptr;
   const int lay = layout & 0xFF;
-  const int kw = layout & ~0xFF;
+  const int kw = layout & 0xFF00;
+  const int flags = layout & ~0xFFFF;
   if (kw != GI_KEY_U32 && kw != GI_KEY_U64) return fail(GI_ERR_INVALID, "gi_build: bad key width bits 0x%x", kw);
+  if (flags & ~GI_BUILD_LSD) return fail(GI_ERR_INVALID, "gi_build: unknown build flags 0x%x", flags);
   if (lay != GI_SORTED && lay != GI_EYTZINGER && lay != GI_EYTZINGER_KARY)
     return fail(GI_ERR_INVALID, "gi_build: unknown layout %d", lay);
   if (lay == GI_EYTZINGER_KARY && (k < 2 || k > 33))
@@ -466,14 +471,33 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   const size_t sbytes = gi::sort_scratch_bytes(n, kb);
   GI_TRY2(dalloc(&scratch, sbytes, s), "sort scratch");
   uint32_t trivial = 0;
-  GI_TRY2(gi::sort_prepare(src_k, src_v, n, kb, scratch, idx->dflags, s, &trivial), "histogram");
+  std::vector<unsigned long long> hist(8 * 256);
+  GI_TRY2(gi::sort_prepare(src_k, src_v, n, kb, scratch, idx->dflags, s, &trivial, hist.data()),
+          "histogram");
   // Ping-pong between the two buffers; the first pass writes the buffer that does
   // not hold a staged copy of the input.
   const void* ck = src_k;
   const uint32_t* cv = src_v;
   int cur = -1;  // -1: the data is still the (caller's or staged) input
   int next_dst = staged ? 1 : 0;
-  for (int p = 0; p < kb; ++p) {
+  bool sorted_done = false;
+  if (!(flags & GI_BUILD_LSD)) {  // hybrid MSD + shared-memory bucket sort where it applies
+    int res = -1;
+    bool used = false;
+    const uint32_t nontrivial = ~trivial & ((1u << kb) - 1);
+    GI_TRY2(gi::hybrid_sort(ck, cv, bk, bv, next_dst, n, kb, nontrivial, hist.data(), scratch,
+                            idx->geom, lay == GI_SORTED, lay == GI_EYTZINGER ? 1u : 0u,
+                            idx->dflags, s, &res, &used),
+            "hybrid sort");
+    if (res >= 0) {
+      ck = bk[res];
+      cv = bv[res];
+      cur = res;
+      next_dst = 1 - res;
+      sorted_done = used;  // bk[res] holds the finished layout, duplicates flagged
+    }
+  }
+  for (int p = 0; p < kb && !sorted_done; ++p) {
     if (trivial & (1u << p)) continue;  // every key has the same digit here
     const int dst = next_dst;
     GI_TRY2(gi::sort_pass(ck, cv, bk[dst], bv[dst], n, kb, p, scratch, idx->dflags, s), "radix pass");
@@ -482,7 +506,10 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
     cur = dst;
     next_dst = 1 - dst;
   }
-  if (lay == GI_SORTED) {
+  if (sorted_done) {
+    idx->keys = bk[cur];
+    idx->rows = bv[cur];
+  } else if (lay == GI_SORTED) {
     if (cur < 0) {  // no pass ran (all keys equal): the input order is the sorted order
       cur = next_dst;
       GI_TRY2(cudaMemcpyAsync(bk[cur], ck, n * kb, cudaMemcpyDefault, s), "copy");

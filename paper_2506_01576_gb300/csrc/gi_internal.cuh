@@ -154,7 +154,8 @@ size_t sort_scratch_bytes(uint64_t n, int key_bytes);
 // Histogram all digits, check rowIDs; fills hist scan on device; host reads trivial mask.
 cudaError_t sort_prepare(const void* keys, const uint32_t* vals, uint64_t n, int key_bytes,
                          void* scratch, uint32_t* dflags, cudaStream_t s,
-                         uint32_t* host_trivial_mask /* pinned or pageable, sync inside */);
+                         uint32_t* host_trivial_mask /* pinned or pageable, sync inside */,
+                         unsigned long long* host_hist /* [key_bytes][256], may be NULL */);
 cudaError_t sort_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
                       uint64_t n, int key_bytes, int pass, void* scratch, uint32_t* dflags,
                       cudaStream_t s);
@@ -187,6 +188,28 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
                          const BatchTile* tiles, uint64_t ntiles, const uint64_t* seg_start,
                          const uint64_t* seg_base, uint32_t k, int key_bytes, uint32_t* dflags,
                          cudaStream_t s);
+
+// Hybrid sort: stable MSD scatter(s) on the top one or two non-trivial digits,
+// then every bucket sorted in shared memory and written straight into the final
+// layout (gi_local_sort.cu): slot = rank for the sorted layout, else the k-ary
+// (k = g.k; Eytzinger for k = 2, keys shifted by key_off) slot of the rank.
+// *used = true: bk[*result] / bv[*result] hold the finished layout and the
+// duplicate flag is set.  *used = false and *result = -1: not applicable,
+// nothing launched.  *used = false and *result >= 0: a bucket turned out too
+// large after the first MSD pass; bk[*result] holds the data after that stable
+// pass for a full LSD sort.
+cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], uint32_t* bv[2],
+                        int first_dst, uint64_t n, int key_bytes, uint32_t nontrivial,
+                        const unsigned long long* host_hist, void* scratch, const Geom& g,
+                        bool sorted_layout, uint32_t key_off, uint32_t* dflags, cudaStream_t s,
+                        int* result, bool* used);
+// Shared-memory sort of buckets of at most local_sort_capacity() pairs that
+// agree on every digit outside local_mask, written into the layout (see above).
+uint32_t local_sort_capacity();
+cudaError_t local_sort(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
+                       const BatchTile* segs, uint64_t nseg, uint64_t max_count,
+                       uint32_t local_mask, int key_bytes, const Geom& g, bool sorted_layout,
+                       uint32_t key_off, uint32_t* dflags, cudaStream_t s);
 
 // Point lookups (gi_point.cu).
 struct LookupCfg {

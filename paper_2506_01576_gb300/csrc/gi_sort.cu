@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "gi_internal.cuh"
 
@@ -202,8 +203,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
 #pragma unroll
     for (int b = 0; b < kRadixBits; ++b) {
       const uint32_t bit = (d >> b) & 1u;
-      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-      peers &= bit ? bal : ~bal;
+      peers &= ~(__ballot_sync(0xffffffffu, bit) ^ (0u - bit));  // lanes agreeing on bit b
     }
     const uint32_t before = __popc(peers & lt_mask);
     const uint32_t leader = 31 - __clz(peers);
@@ -447,8 +447,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_batch_sort_pass(
 #pragma unroll
     for (int b = 0; b < kRadixBits; ++b) {
       const uint32_t bit = (d >> b) & 1u;
-      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-      peers &= bit ? bal : ~bal;
+      peers &= ~(__ballot_sync(0xffffffffu, bit) ^ (0u - bit));
     }
     const uint32_t before = __popc(peers & lt_mask);
     const uint32_t leader = 31 - __clz(peers);
@@ -573,15 +572,43 @@ __global__ void __launch_bounds__(256) k_batch_gather(const K* __restrict__ sk,
   if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagDuplicate);
 }
 
+// ================================================================= hybrid MSD + bucket sort
+// After the stable MSD scatters on the top digits, every bucket is small enough
+// for one CTA, which sorts it in shared memory and writes it into the final
+// layout (gi_local_sort.cu).
+
+// one digit's histogram per segment (no atomics across segments' counters)
+template <class K>
+__global__ void __launch_bounds__(256) k_seg_hist1(const K* __restrict__ keys,
+                                                   const BatchTile* __restrict__ chunks,
+                                                   uint64_t nchunks, uint32_t shift,
+                                                   unsigned long long* __restrict__ hist) {
+  __shared__ uint32_t sh[kRadix];
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const BatchTile t = chunks[c];
+    sh[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < t.count; i += blockDim.x)
+      atomicAdd(&sh[(uint32_t)(keys[t.start + i] >> shift) & 0xFF], 1u);
+    __syncthreads();
+    const uint32_t v = sh[threadIdx.x];
+    if (v) atomicAdd(&hist[(uint64_t)t.seg * kRadix + threadIdx.x], (unsigned long long)v);
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 size_t sort_scratch_bytes(uint64_t n, int key_bytes) {
-  return header_bytes(key_bytes) + align256(sizeof(uint64_t) * kRadix * (tiles_for(n, key_bytes) + 1));
+  // status words for the most tiles any pass launches: a segmented pass over the
+  // 256 buckets of one digit cuts at most one extra (partial) tile per bucket
+  return header_bytes(key_bytes) +
+         align256(sizeof(uint64_t) * kRadix * (tiles_for(n, key_bytes) + kRadix + 1));
 }
 
 cudaError_t sort_prepare(const void* keys, const uint32_t* vals, uint64_t n, int key_bytes,
                          void* scratch, uint32_t* dflags, cudaStream_t s,
-                         uint32_t* host_trivial_mask) {
+                         uint32_t* host_trivial_mask, unsigned long long* host_hist) {
   ScratchView v = view(scratch, key_bytes);
   cudaError_t e = cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, key_bytes), s);
   if (e != cudaSuccess) return e;
@@ -595,6 +622,10 @@ cudaError_t sort_prepare(const void* keys, const uint32_t* vals, uint64_t n, int
   uint32_t triv[8] = {0};
   e = cudaMemcpyAsync(triv, v.trivial, sizeof(uint32_t) * key_bytes, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return e;
+  if (host_hist) {
+    e = cudaMemcpyAsync(host_hist, v.hist, sizeof(uint64_t) * key_bytes * kRadix, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+  }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
   uint32_t mask = 0;
@@ -764,6 +795,165 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
     launch_batch_gather<uint32_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s);
   else
     launch_batch_gather<uint64_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s);
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------- hybrid sort, host side
+cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], uint32_t* bv[2],
+                        int first_dst, uint64_t n, int key_bytes, uint32_t nontrivial,
+                        const unsigned long long* host_hist, void* scratch, const Geom& g,
+                        bool sorted_layout, uint32_t key_off, uint32_t* dflags, cudaStream_t s,
+                        int* result, bool* used) {
+  *used = false;
+  *result = -1;
+  // digits from the most significant down
+  int digits[8], nd = 0;
+  for (int p = key_bytes - 1; p >= 0; --p)
+    if (nontrivial & (1u << p)) digits[nd++] = p;
+  if (nd < 2 || n < (1ull << 20)) return cudaSuccess;
+  const uint64_t cap = local_sort_capacity();
+  const int d1 = digits[0];
+  const bool two = nd >= 3 && n / 256 > cap / 4;  // a second MSD digit keeps buckets small
+  const int d2 = two ? digits[1] : -1;
+  // level-1 buckets straight from the full histogram
+  std::vector<uint64_t> start1(kRadix + 1, 0);
+  uint64_t mx1 = 0;
+  for (int d = 0; d < kRadix; ++d) {
+    start1[d + 1] = start1[d] + host_hist[d1 * kRadix + d];
+    mx1 = std::max<uint64_t>(mx1, host_hist[d1 * kRadix + d]);
+  }
+  // the largest level-1 bucket decides: with one MSD digit it must fit a CTA;
+  // with two, the mean of its level-2 buckets must (else one of them cannot)
+  if (!two && mx1 > cap) return cudaSuccess;
+  if (two && mx1 / kRadix > cap) return cudaSuccess;
+  uint32_t local_mask = 0;
+  for (int i = two ? 2 : 1; i < nd; ++i) local_mask |= 1u << digits[i];
+
+  ScratchView v = view(scratch, key_bytes);
+  cudaError_t e;
+  // pass 1: a plain global pass on digit d1 (its offsets are in v.offs)
+  const int dst1 = first_dst;
+  if (key_bytes == 4)
+    k_sort_pass<uint32_t><<<(unsigned)tiles_for(n, 4), kSortThreads, 0, s>>>(
+        (const uint32_t*)src_k, src_v, (uint32_t*)bk[dst1], bv[dst1], n, 8u * d1,
+        v.offs + d1 * kRadix, v.status, v.counter + d1, 20u + d1, dflags);
+  else
+    k_sort_pass<uint64_t><<<(unsigned)tiles_for(n, 8), kSortThreads, 0, s>>>(
+        (const uint64_t*)src_k, src_v, (uint64_t*)bk[dst1], bv[dst1], n, 8u * d1,
+        v.offs + d1 * kRadix, v.status, v.counter + d1, 20u + d1, dflags);
+  count_launch();
+  int cur = dst1;
+  std::vector<BatchTile> segs;  // the buckets the shared-memory sort takes
+  if (two) {
+    // tables of the level-1 buckets for the segmented pass on d2 (host-built
+    // from the full histogram while pass 1 runs)
+    std::vector<BatchTile> tiles, chunks;
+    std::vector<uint64_t> seg_start;
+    const uint32_t tile = batch_sort_tile(key_bytes);
+    uint32_t nseg1 = 0;
+    for (int d = 0; d < kRadix; ++d) {
+      const uint64_t a = start1[d], c = start1[d + 1] - a;
+      if (!c) continue;
+      seg_start.push_back(a);
+      for (uint64_t t = 0, l = 0; t < c; t += tile, ++l)
+        tiles.push_back(BatchTile{a + t, nseg1, (uint32_t)std::min<uint64_t>(tile, c - t), (uint32_t)l, 0});
+      for (uint64_t t = 0; t < c; t += kBatchChunk)
+        chunks.push_back(BatchTile{a + t, nseg1, (uint32_t)std::min<uint64_t>(kBatchChunk, c - t), 0, 0});
+      ++nseg1;
+    }
+    seg_start.push_back(n);
+    const size_t tbytes = tiles.size() * sizeof(BatchTile), cbytes = chunks.size() * sizeof(BatchTile);
+    const size_t hbytes = (size_t)nseg1 * kRadix * 8;
+    char* blob = nullptr;
+    const size_t blob_bytes = 8 * 256 + tbytes + cbytes + 2 * hbytes + (nseg1 + 1) * 8 + 64;
+    e = cudaMallocAsync((void**)&blob, blob_bytes, s);
+    if (e != cudaSuccess) return e;
+    char* q = blob;
+    auto take = [&](size_t b) { char* r = q; q += (b + 255) & ~size_t(255); return r; };
+    BatchTile* d_tiles = (BatchTile*)take(tbytes);
+    BatchTile* d_chunks = (BatchTile*)take(cbytes);
+    unsigned long long* d_hist = (unsigned long long*)take(hbytes);
+    unsigned long long* d_offs = (unsigned long long*)take(hbytes);
+    uint64_t* d_seg_start = (uint64_t*)take((nseg1 + 1) * 8);
+    uint32_t* d_counter = (uint32_t*)take(64);
+    e = cudaMemcpyAsync(d_tiles, tiles.data(), tbytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_chunks, chunks.data(), cbytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_seg_start, seg_start.data(), (nseg1 + 1) * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_hist, 0, hbytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, 64, s);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(blob, s);
+      return e;
+    }
+    // per-bucket histogram of d2 and its scan into absolute offsets
+    const int hgrid = (int)std::min<uint64_t>(chunks.size(), (uint64_t)sm_count() * 8);
+    if (key_bytes == 4)
+      k_seg_hist1<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)bk[cur], d_chunks, chunks.size(), 8u * d2, d_hist);
+    else
+      k_seg_hist1<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)bk[cur], d_chunks, chunks.size(), 8u * d2, d_hist);
+    k_batch_scan_hist<<<nseg1, 256, 0, s>>>(d_hist, d_offs, d_seg_start, 1);
+    count_launch(2);
+    std::vector<unsigned long long> h2((size_t)nseg1 * kRadix);
+    e = cudaMemcpyAsync(h2.data(), d_hist, hbytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(blob, s);
+      return e;
+    }
+    uint64_t mx = 0;
+    for (auto c : h2) mx = std::max<uint64_t>(mx, c);
+    if (mx > cap) {  // a bucket too large for one CTA: the caller runs the full LSD sort
+      cudaFreeAsync(blob, s);
+      *result = cur;  // the data after the stable d1 pass
+      return cudaMemsetAsync(v.counter, 0, align256(sizeof(uint32_t) * key_bytes), s);
+    }
+    // pass 2: segmented on d2; tiles.size() <= tiles_for(n) + 256, which the
+    // status array is sized for
+    const int dst2 = 1 - cur;
+    if (key_bytes == 4)
+      k_batch_sort_pass<uint32_t><<<(unsigned)tiles.size(), kSortThreads, 0, s>>>(
+          (const uint32_t*)bk[cur], bv[cur], (uint32_t*)bk[dst2], bv[dst2], n, 8u * d2, d_tiles,
+          d_offs, 0, 1, v.status, d_counter, 40u, dflags);
+    else
+      k_batch_sort_pass<uint64_t><<<(unsigned)tiles.size(), kSortThreads, 0, s>>>(
+          (const uint64_t*)bk[cur], bv[cur], (uint64_t*)bk[dst2], bv[dst2], n, 8u * d2, d_tiles,
+          d_offs, 0, 1, v.status, d_counter, 40u, dflags);
+    count_launch();
+    cur = dst2;
+    cudaFreeAsync(blob, s);
+    // level-2 buckets, built while pass 2 runs
+    segs.reserve(h2.size());
+    for (uint32_t a = 0; a < nseg1; ++a) {
+      uint64_t at = seg_start[a];
+      for (int d = 0; d < kRadix; ++d) {
+        const uint64_t c = h2[(size_t)a * kRadix + d];
+        if (c) segs.push_back(BatchTile{at, 0, (uint32_t)c, 0, 0});
+        at += c;
+      }
+    }
+  } else {
+    for (int d = 0; d < kRadix; ++d) {
+      const uint64_t c = start1[d + 1] - start1[d];
+      if (c) segs.push_back(BatchTile{start1[d], 0, (uint32_t)c, 0, 0});
+    }
+  }
+  // every bucket sorted in shared memory and written into the final layout
+  uint64_t max_count = 1;
+  for (const BatchTile& t : segs) max_count = std::max<uint64_t>(max_count, t.count);
+  BatchTile* d_segs = nullptr;
+  e = cudaMallocAsync((void**)&d_segs, std::max<size_t>(1, segs.size()) * sizeof(BatchTile), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, s);
+  const int dst3 = 1 - cur;
+  if (e == cudaSuccess)
+    e = local_sort(bk[cur], bv[cur], bk[dst3], bv[dst3], d_segs, segs.size(), max_count, local_mask,
+                   key_bytes, g, sorted_layout, key_off, dflags, s);
+  cudaFreeAsync(d_segs, s);
+  if (e != cudaSuccess) return e;
+  *result = dst3;
+  *used = true;
   return cudaGetLastError();
 }
 

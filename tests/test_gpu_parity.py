@@ -319,3 +319,46 @@ def test_local_lookup_reordering_changes_nothing(dtype, layout, k):
                   np.array([0, np.iinfo(dtype).max], dtype=dtype)):
             assert np.array_equal(point(idx, q.astype(dtype)), oracle.point_lookup(sk, sr, q.astype(dtype)))
         gi.gi_destroy(idx)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+@pytest.mark.parametrize("dist", ["uniform", "narrow", "dups", "cluster", "skewed"])
+def test_hybrid_msd_build_equals_plain_lsd_build(dtype, dist):
+    # The default build scatters by the top digit(s) and sorts each bucket in shared
+    # memory; GI_BUILD_LSD forces the plain LSD passes.  Both must give the oracle's
+    # layout.  narrow: the top digits are trivial; dups: 16 copies of every key
+    # (stability); cluster: 20000 keys share their top 16 bits, so one level-2 bucket
+    # is too big for a CTA and the build falls back to LSD after the first scatter;
+    # skewed: 70% of the keys below 2^16, so the hybrid sort is not tried at all.
+    bits = 8 * np.dtype(dtype).itemsize
+    top = np.iinfo(dtype).max
+    n = (1 << 21) + 12345
+    rng = np.random.default_rng(17)
+    if dist == "uniform":
+        keys = W.unique_keys(n, bits, 8)
+    elif dist == "narrow":
+        keys = rng.integers(0, 1 << 24, size=n).astype(dtype)
+    elif dist == "dups":
+        keys = W.duplicate_keys(n // 16, 16, bits, 8)
+        n = len(keys)
+    elif dist == "cluster":
+        keys = rng.integers(0, top, size=n, dtype=dtype, endpoint=True)
+        hi = dtype(0xABCD) << dtype(bits - 16)
+        keys[:20000] = hi | rng.integers(0, 1 << (bits - 16), size=20000, dtype=np.uint64).astype(dtype)
+        rng.shuffle(keys)
+    else:
+        keys = np.where(rng.random(n) < 0.7, rng.integers(0, 1 << 16, size=n).astype(dtype),
+                        rng.integers(0, top, size=n, dtype=dtype, endpoint=True))
+    rows = rng.permutation(n).astype(np.uint32)
+    sk, sr = oracle.sort_pairs(keys, rows)
+    q = np.concatenate([keys[rng.integers(0, n, size=20000)],
+                        rng.integers(0, top, size=5000, dtype=dtype, endpoint=True)])
+    want = oracle.point_lookup(sk, sr, q)
+    for layout, k in ((gi.GI_SORTED, 0), (gi.GI_EYTZINGER_KARY, 5)):
+        ok, orr = _oracle_layout(keys, rows, layout, k)
+        for flag in (0, gi.GI_BUILD_LSD):
+            idx = build(keys, rows, layout | flag, k)
+            lk, lr = layout_arrays(idx, n, dtype)
+            assert np.array_equal(lk, ok) and np.array_equal(lr, orr), (layout, flag)
+            assert np.array_equal(point(idx, q), want), (layout, flag)
+            gi.gi_destroy(idx)

@@ -319,7 +319,7 @@ def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, 
     opts = {name: gi.gi_get_option(idx, o) for name, o in
             (("group", gi.GI_OPT_GROUP), ("per_thread", gi.GI_OPT_PER_THREAD),
              ("smem_levels", gi.GI_OPT_SMEM_LEVELS), ("block", gi.GI_OPT_BLOCK),
-             ("blocks_per_sm", gi.GI_OPT_BLOCKS_PER_SM))}
+             ("blocks_per_sm", gi.GI_OPT_BLOCKS_PER_SM), ("hot_levels", gi.GI_OPT_HOT_LEVELS))}
     gi.gi_point_lookup(idx, qd, out)
     torch.cuda.synchronize()
     got = out.cpu().numpy().view(np.uint32)
@@ -358,7 +358,7 @@ def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, 
     bpl, reqs = eks_bytes_per_lookup(n, a.k, 8, 0.5, l2)
     achieved = bpl * m / (pt_ms / 1e3) / 1e9
     res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                       "frac": achieved / hbm, "traffic": recorded_traffic(a, m),
+                       "frac": achieved / hbm, "traffic": recorded_traffic(a, m, opts["hot_levels"]),
                        "peak_source": "measured" if peaks else "fallback",
                        "kernel": "k_eks_point", "algorithmic_bytes_per_lookup": bpl,
                        "random_requests_per_lookup": reqs, "l2_bytes": l2}
@@ -416,11 +416,12 @@ def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, 
     return res
 
 
-def recorded_traffic(a, m):
+def recorded_traffic(a, m, hot_levels):
     """DRAM bytes of one k_eks_point launch from the committed ncu summary, or None.
 
     Valid only for the configuration it was captured on (2^26 u64 keys, k = 5,
-    2^27 probes, default knobs) and while the kernel source is unchanged.
+    2^27 probes, default knobs, the same number of evict-last levels) and while
+    the kernel source is unchanged.
     """
     import hashlib
     if (a.layout, a.k, a.n_log, a.m_log, a.group, a.per_thread, a.smem_levels,
@@ -429,11 +430,14 @@ def recorded_traffic(a, m):
     try:
         txt = open(os.path.join(ROOT, "profiles", "k_eks_point_u64_k5_2e26.md")).read()
         rec = dict(l.split(": ", 1) for l in txt.splitlines()
-                   if l.startswith(("traffic_full_launch_bytes:", "kernel_source_sha256:")))
+                   if l.startswith(("traffic_full_launch_bytes:", "kernel_source_sha256:",
+                                    "hot_levels:")))
         h = hashlib.sha256()
         for f in ("gi_point_impl.cuh", "gi_eks_inst.cuh"):
             h.update(open(os.path.join(ROOT, "paper_2506_01576_gb300", "csrc", f), "rb").read())
         if h.hexdigest() != rec["kernel_source_sha256"].strip():
+            return None
+        if int(rec["hot_levels"]) != int(hot_levels):
             return None
         return int(rec["traffic_full_launch_bytes"])
     except Exception:

@@ -354,6 +354,7 @@ def test_hybrid_msd_build_equals_plain_lsd_build(dtype, dist):
     q = np.concatenate([keys[rng.integers(0, n, size=20000)],
                         rng.integers(0, top, size=5000, dtype=dtype, endpoint=True)])
     want = oracle.point_lookup(sk, sr, q)
+    unique = bool(np.all(sk[1:] != sk[:-1]))
     for layout, k in ((gi.GI_SORTED, 0), (gi.GI_EYTZINGER_KARY, 5)):
         ok, orr = _oracle_layout(keys, rows, layout, k)
         for flag in (0, gi.GI_BUILD_LSD):
@@ -361,4 +362,33 @@ def test_hybrid_msd_build_equals_plain_lsd_build(dtype, dist):
             lk, lr = layout_arrays(idx, n, dtype)
             assert np.array_equal(lk, ok) and np.array_equal(lr, orr), (layout, flag)
             assert np.array_equal(point(idx, q), want), (layout, flag)
+            assert bool(gi.gi_get_info(idx).unique) == unique, (layout, flag)
             gi.gi_destroy(idx)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+@pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER, 0), (gi.GI_EYTZINGER_KARY, 3), (gi.GI_EYTZINGER_KARY, 9),
+                                      (gi.GI_EYTZINGER_KARY, 17), (gi.GI_EYTZINGER_KARY, 4),
+                                      (gi.GI_EYTZINGER_KARY, 33)])
+def test_hybrid_build_writes_every_layout(dtype, layout, k):
+    # the bucket sort writes each key straight to its slot in the layout (the
+    # 32-bit rank -> slot map, specialised for k = 2, 3, 5, 9, 17, generic otherwise);
+    # the extreme keys 0 and the maximum are in the input, n just above 2^20
+    bits = 8 * np.dtype(dtype).itemsize
+    top = np.iinfo(dtype).max
+    n = (1 << 20) + 3
+    keys = W.unique_keys(n, bits, 31)
+    keys[:2] = [0, top]
+    keys = np.unique(keys)
+    n = len(keys)
+    rng = np.random.default_rng(5)
+    keys = keys[rng.permutation(n)]
+    rows = rng.permutation(n).astype(np.uint32)
+    ok, orr = _oracle_layout(keys, rows, layout, k)
+    for flag in (0, gi.GI_BUILD_LSD):
+        idx = build(keys, rows, layout | flag, k)
+        lk, lr = layout_arrays(idx, n, dtype)
+        assert np.array_equal(lk, ok) and np.array_equal(lr, orr), flag
+        info = gi.gi_get_info(idx)
+        assert info.unique == 1
+        gi.gi_destroy(idx)

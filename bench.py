@@ -44,7 +44,7 @@ UNIT = "lookups/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-log", type=int, default=26)
@@ -86,50 +86,71 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs.
+
+    One nvidia-smi process in loop mode (every `interval_ms`) runs from start()
+    to stop(); samples are stamped on arrival, and summary() keeps those that
+    arrived between begin() and end() (the timed region).
+    """
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 50):
         self.gpu = gpu_index
-        self.samples = []
-        self._stop = threading.Event()
+        self.interval_ms = interval_ms
+        self.samples = []  # (arrival time, fields)
+        self.window = (0.0, float("inf"))
+        self._proc = None
         self._t = None
 
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                      "--format=csv,noheader,nounits"], capture_output=True,
-                                     text=True, timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+    def _read(self):
+        for line in self._proc.stdout:
+            line = line.strip()
+            if line:
+                self.samples.append((time.monotonic(), [x.strip() for x in line.split(",")]))
 
-    def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+    def start(self):
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self._proc = None
         return self
 
-    def __exit__(self, *a):
-        self._stop.set()
-        self._t.join(timeout=10)
+    def begin(self):
+        self.window = (time.monotonic(), float("inf"))
+
+    def end(self):
+        self.window = (self.window[0], time.monotonic())
+
+    def stop(self):
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+            self._t.join(timeout=5)
 
     def summary(self):
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        t0, t1 = self.window
+        inside = [f for t, f in self.samples if t0 <= t <= t1]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(s[0]) for s in inside if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in inside if s[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4)
+        reasons = sorted({names[i] for s in inside for i in range(4)
                           if len(s) > 3 + i and s[3 + i].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+                "samples": len(inside)}
 
 
 def kary_level_sizes(n: int, k: int):
@@ -244,19 +265,22 @@ def run_ours(a):
         gi.gi_range_lookup(idx, lod, hid, off, rout)  # single call: count + scan + fill
         gi.gi_destroy(idx)  # waits for the stream
 
+    clk = ClockSampler(local).start()  # the sampler's start-up overlaps the warm-up
     for _ in range(a.warmup):
         step(False)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     l0 = gi.gi_launch_count()
-    with ClockSampler(local) as clk:
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for _ in range(a.steps):
-            step(True)
-        t1.record(stream)
-        torch.cuda.synchronize()
+    clk.begin()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(a.steps):
+        step(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk.end()
+    clk.stop()
     launches = gi.gi_launch_count() - l0
     if world > 1:
         dist.barrier()
@@ -605,9 +629,15 @@ def run_batched(a):
             e1.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    with ClockSampler(0) as clk:
-        graph_ms = ev(lambda: g.replay(), a.steps)
-        launches = kernels_per_replay * a.steps
+    clk = ClockSampler(0).start()
+    for _ in range(3):  # warm replays while the sampler starts
+        g.replay()
+    torch.cuda.synchronize()
+    clk.begin()
+    graph_ms = ev(lambda: g.replay(), a.steps)
+    clk.end()
+    clk.stop()
+    launches = kernels_per_replay * a.steps
     gi.gi_batch_sync(batch)
     got = out.cpu().numpy().view(np.uint32)
     lookup_ms = ev(lambda: gi.gi_batch_point_lookup(batch, qd, qod, out), a.steps)

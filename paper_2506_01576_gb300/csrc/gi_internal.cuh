@@ -111,6 +111,45 @@ __host__ __device__ __forceinline__ uint64_t rank_to_slot(uint64_t r, const Geom
   return (kpow<KF>(l, g) - 1) + xd * km1 + (x - xd * k) - 1;
 }
 
+// The rank -> slot map of the k-ary layout (rank_to_slot) in 32-bit arithmetic,
+// valid because n < 2^32 (rowIDs are 32-bit), with the first slot of every level
+// (k^l - 1) from a table instead of a power loop.  A rank with remainder o < k-1
+// mod k is a bottom-level key while the bottom level lasts; every other rank is
+// an upper-level key of the perfect tree, whose level is m-1 minus the number of
+// factors k in its 1-based rank among the upper-level keys.
+struct SlotMap {
+  uint32_t top, b, m, k;
+  uint32_t first[32];  // first slot of level l, l <= m
+};
+
+template <int KF>
+__host__ __device__ __forceinline__ uint32_t slot_of_rank(uint32_t r, const SlotMap& sm) {
+  const uint32_t k = KF ? (uint32_t)KF : sm.k, km1 = k - 1;
+  const uint32_t c = r / k, o = r - c * k;
+  const uint32_t below = c * km1 + o;  // bottom-level keys of smaller rank, if unbounded
+  if (o < km1 && below < sm.b) return sm.top + below;
+  uint32_t x = r - (below < sm.b ? below : sm.b) + 1;
+  uint32_t l = sm.m - 1;
+  while (x % k == 0) {
+    x /= k;
+    --l;
+  }
+  const uint32_t xd = x / k;
+  return sm.first[l] + xd * km1 + (x - xd * k) - 1;
+}
+
+// Host: the 32-bit map of a geometry with n < 2^32.
+inline SlotMap make_slot_map(const Geom& g) {
+  SlotMap sm{};
+  sm.top = (uint32_t)g.top;
+  sm.b = (uint32_t)g.b;
+  sm.m = g.m;
+  sm.k = g.k;
+  uint64_t p = 1;
+  for (uint32_t l = 0; l < 32 && l <= g.m; ++l, p *= g.k) sm.first[l] = (uint32_t)(p - 1);
+  return sm;
+}
+
 // Geometry computed on the device (the host version is make_geom); k >= 2.
 __device__ __forceinline__ Geom device_geom(uint64_t n, uint32_t k) {
   Geom g;

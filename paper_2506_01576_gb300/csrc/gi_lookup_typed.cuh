@@ -65,8 +65,17 @@ cudaError_t range_lookup_typed(const K* keys, const uint32_t* rows, const Geom& 
     uint64_t gr = (m + block - 1) / block;  // one lane per range
     if (gr > 0x7fffffffull) gr = 0x7fffffffull;
     const unsigned grid = (unsigned)(gr ? gr : 1);
+    const SlotMap sm = make_slot_map(g);
+    const bool narrow = g.n < (1ull << 32);  // 32-bit rank -> slot map
+#define GI_F(L, KF)                                                                              \
+  do {                                                                                           \
+    if (narrow)                                                                                  \
+      k_range_fill<L, KF, uint32_t><<<grid, block, 0, s>>>(rows, g, sm, offsets, lo_rank, m, out_rows); \
+    else                                                                                         \
+      k_range_fill<L, KF, uint64_t><<<grid, block, 0, s>>>(rows, g, sm, offsets, lo_rank, m, out_rows); \
+  } while (0)
     if (c.layout == GI_SORTED) {
-      k_range_fill<0, 0><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows);
+      k_range_fill<0, 0, uint64_t><<<grid, block, 0, s>>>(rows, g, sm, offsets, lo_rank, m, out_rows);
     } else if (c.range_fill == 1) {  // level runs (Section 5)
       switch (c.layout == GI_EYTZINGER ? 2u : g.k) {
 #define GI_RL(KF) case KF: k_range_fill_levels<KF><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows); break;
@@ -75,15 +84,16 @@ cudaError_t range_lookup_typed(const K* keys, const uint32_t* rows, const Geom& 
         default: k_range_fill_levels<0><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows); break;
       }
     } else if (c.layout == GI_EYTZINGER) {
-      k_range_fill<1, 2><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows);
+      GI_F(1, 2);
     } else {
       switch (g.k) {
-#define GI_RF(KF) case KF: k_range_fill<2, KF><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows); break;
+#define GI_RF(KF) case KF: GI_F(2, KF); break;
         GI_RF(3) GI_RF(4) GI_RF(5) GI_RF(8) GI_RF(9) GI_RF(16) GI_RF(17) GI_RF(32) GI_RF(33)
 #undef GI_RF
-        default: k_range_fill<2, 0><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows); break;
+        default: GI_F(2, 0); break;
       }
     }
+#undef GI_F
     count_launch();
   }
   return cudaGetLastError();

@@ -293,22 +293,26 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint64_t* __r
 }
 
 // ---------------------------------------------------------------- fill
-template <int LAYOUT, int KF>
-__device__ __forceinline__ uint64_t slot_of(uint64_t r, const Geom& g) {
+// rank -> slot: 32-bit map with a level table when n < 2^32 (IDX = uint32_t), the
+// 64-bit closed form otherwise
+template <int LAYOUT, int KF, class IDX>
+__device__ __forceinline__ uint64_t slot_of(uint64_t r, const Geom& g, const SlotMap& sm) {
   if constexpr (LAYOUT == 0) return r;
+  else if constexpr (sizeof(IDX) == 4) return slot_of_rank<LAYOUT == 1 ? 2 : KF>((uint32_t)r, sm);
   else if constexpr (LAYOUT == 1) return rank_to_slot<2>(r, g);
   else return rank_to_slot<KF>(r, g);
 }
 
-template <int LAYOUT, int KF>
+template <int LAYOUT, int KF, class IDX>
 __device__ __forceinline__ uint32_t row_at(const uint32_t* __restrict__ rows, uint64_t r,
-                                           const Geom& g) {
-  const uint64_t s = slot_of<LAYOUT, KF>(r, g);
+                                           const Geom& g, const SlotMap& sm) {
+  const uint64_t s = slot_of<LAYOUT, KF, IDX>(r, g, sm);
   return s < g.n ? __ldg(rows + s) : GI_MISS;  // ranks are < n; the bound is a guard
 }
 
-template <int LAYOUT, int KF>
+template <int LAYOUT, int KF, class IDX>
 __global__ void __launch_bounds__(256) k_range_fill(const uint32_t* __restrict__ rows, Geom g,
+                                                    SlotMap sm,
                                                     const uint64_t* __restrict__ offsets,
                                                     const uint64_t* __restrict__ lo_rank,
                                                     uint64_t m, uint32_t* __restrict__ out) {
@@ -331,10 +335,10 @@ __global__ void __launch_bounds__(256) k_range_fill(const uint32_t* __restrict__
       const uint64_t bo = __shfl_sync(0xffffffffu, off, b);
       const uint64_t bc = __shfl_sync(0xffffffffu, cnt, b);
       const uint64_t br = __shfl_sync(0xffffffffu, r0, b);
-      for (uint64_t j = lane; j < bc; j += 32) out[bo + j] = row_at<LAYOUT, KF>(rows, br + j, g);
+      for (uint64_t j = lane; j < bc; j += 32) out[bo + j] = row_at<LAYOUT, KF, IDX>(rows, br + j, g, sm);
     }
     if (!big) {
-      for (uint64_t j = 0; j < cnt; ++j) out[off + j] = row_at<LAYOUT, KF>(rows, r0 + j, g);
+      for (uint64_t j = 0; j < cnt; ++j) out[off + j] = row_at<LAYOUT, KF, IDX>(rows, r0 + j, g, sm);
     }
   }
 }

@@ -811,7 +811,8 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
   int digits[8], nd = 0;
   for (int p = key_bytes - 1; p >= 0; --p)
     if (nontrivial & (1u << p)) digits[nd++] = p;
-  if (nd < 2 || n < (1ull << 20)) return cudaSuccess;
+  // the bucket sort's slot map is 32-bit: larger indexes take the LSD sort
+  if (nd < 2 || n < (1ull << 20) || n >= (1ull << 32)) return cudaSuccess;
   const uint64_t cap = local_sort_capacity();
   const int d1 = digits[0];
   const bool two = nd >= 3 && n / 256 > cap / 4;  // a second MSD digit keeps buckets small

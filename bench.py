@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="timed steps only (for profiler launch lists)")
     ap.add_argument("--workload", default="point",
-                    choices=["point", "batched", "ranges", "dups", "skew", "serve"],
+                    choices=["point", "batched", "ranges", "dups", "skew", "serve", "sizes"],
                     help="point: the 2^26-key step (default); batched: 4096 indexes in one graph; "
                          "ranges: 2^24 ranges on 2^26 u32 keys; dups: replicated keys, point = range [x, x]")
     ap.add_argument("--batch-k", type=int, default=5)
@@ -728,6 +728,47 @@ def run_ranges(a):
             gi.gi_destroy(idx)
 
 
+def run_sizes(a):
+    """Point lookups and builds over the index size: n = 2^10 .. 2^28 unique u64 keys,
+    2^27 probes (hit rate 0.5, uniform) per size, textbook BS, EBS and EKS with
+    k = 4, 5, 8, 9, 16, 17; build time of the k = 5 layout (hybrid sort and plain
+    LSD) and of the sorted layout.  One JSON line per size."""
+    import torch
+
+    import paper_2506_01576_gb300 as gi
+    gi.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    m = 1 << a.m_log
+    out = torch.empty(m, dtype=torch.int32, device=dev)
+    lo_log, hi_log = 10, 28
+    for nl in range(lo_log, hi_log + 1):
+        n = 1 << nl
+        seed = W.seed_for(5, nl)
+        keys = W.unique_keys(n, 64, seed)
+        q = W.point_probes(keys, m, 0.5, 64, seed, seed + 1)
+        kd = torch.from_numpy(keys.view(np.int64)).to(dev)
+        rd = torch.arange(n, dtype=torch.int32, device=dev)
+        qd = torch.from_numpy(q.view(np.int64)).to(dev)
+        U = gi.GI_KEY_U64
+        line = {"workload": "sizes", "n_log": nl, "probes": m, "lookups_per_s": {}, "build_ms": {}}
+        for name, lay, k in (("BS", gi.GI_SORTED, 0), ("EBS", gi.GI_EYTZINGER, 0),
+                             ("EKS4", gi.GI_EYTZINGER_KARY, 4), ("EKS5", gi.GI_EYTZINGER_KARY, 5),
+                             ("EKS8", gi.GI_EYTZINGER_KARY, 8), ("EKS9", gi.GI_EYTZINGER_KARY, 9),
+                             ("EKS16", gi.GI_EYTZINGER_KARY, 16), ("EKS17", gi.GI_EYTZINGER_KARY, 17)):
+            idx = gi.gi_build(kd, rd, lay | U, k)
+            ms = _ev_ms(torch, lambda: gi.gi_point_lookup(idx, qd, out), a.steps)
+            line["lookups_per_s"][name] = m / ms * 1e3
+            gi.gi_destroy(idx)
+        for name, lay, k in (("EKS5", gi.GI_EYTZINGER_KARY, 5),
+                             ("EKS5_lsd", gi.GI_EYTZINGER_KARY | gi.GI_BUILD_LSD, 5),
+                             ("sorted", gi.GI_SORTED, 0)):
+            line["build_ms"][name] = _ev_ms(
+                torch, lambda: gi.gi_destroy(gi.gi_build(kd, rd, lay | U, k)), max(3, a.steps // 3))
+        print(json.dumps(line), flush=True)
+        del kd, rd, qd
+
+
 def run_dups(a):
     """Section 8.11 / Fig 25 shape: 2^26 u64 keys, each distinct key replicated r
     times; 2^20 point queries as ranges [x, x] returning every occurrence."""
@@ -927,6 +968,8 @@ if __name__ == "__main__":
         run_dups(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "sizes":
+        run_sizes(args)
     elif args.probe_sweep:
         probe_sweep()
     elif args.impl == "reference":

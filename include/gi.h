@@ -55,12 +55,21 @@ typedef struct gi_index gi_index;
 /* Key width, OR-ed into `layout`. */
 #define GI_KEY_U32 0x000
 #define GI_KEY_U64 0x100
-/* Build flag, OR-ed into `layout` of gi_build: sort with the plain 8-bit LSD radix
- * passes only.  By default a large build first scatters by its top one or two
- * non-trivial digits (stable) and then sorts every resulting bucket inside one
- * CTA's shared memory, which takes fewer passes over global memory; it falls
- * back to the LSD passes when a bucket is too large.  Same result either way. */
+/* Build flags, OR-ed into `layout` of gi_build (at most one).  Both give the same
+ * index; they choose how the pairs are sorted.
+ *   default          u64 keys with at least five non-trivial digits (bytes that
+ *                    differ between keys) and 2^24 <= n < 2^32 take the hybrid
+ *                    sort: stable scatters on the top two non-trivial digits, then
+ *                    every resulting bucket sorted in one CTA's shared memory and
+ *                    written straight into the layout.  Smaller or narrower inputs,
+ *                    and inputs whose buckets come out larger than 4096 pairs,
+ *                    take the plain LSD sort.
+ *   GI_BUILD_LSD     always the plain 8-bit LSD radix passes (then the permutation).
+ *   GI_BUILD_HYBRID  the hybrid sort whenever it can run (at least two non-trivial
+ *                    digits, n < 2^32, buckets of at most 4096 pairs), whatever n
+ *                    and the key width; else the LSD sort. */
 #define GI_BUILD_LSD 0x10000
+#define GI_BUILD_HYBRID 0x20000
 
 /* Return codes. */
 #define GI_OK          0

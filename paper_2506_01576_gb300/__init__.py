@@ -20,7 +20,7 @@ import os
 
 __all__ = [
     "GI_SORTED", "GI_EYTZINGER", "GI_EYTZINGER_KARY", "GI_KEY_U32", "GI_KEY_U64", "GI_MISS",
-    "GI_BUILD_LSD",
+    "GI_BUILD_LSD", "GI_BUILD_HYBRID",
     "GI_OK", "GI_ERR_INVALID", "GI_ERR_NOMEM", "GI_ERR_CUDA", "GI_ERR_TIMEOUT",
     "GI_OPT_GROUP", "GI_OPT_PER_THREAD", "GI_OPT_SMEM_LEVELS", "GI_OPT_BLOCK",
     "GI_OPT_BLOCKS_PER_SM", "GI_OPT_PREFETCH", "GI_OPT_EARLY_EXIT", "GI_OPT_HOT_LEVELS", "GI_OPT_RANGE_FILL", "GI_OPT_REORDER",
@@ -39,6 +39,7 @@ __all__ = [
 GI_SORTED, GI_EYTZINGER, GI_EYTZINGER_KARY = 0, 1, 2
 GI_KEY_U32, GI_KEY_U64 = 0x000, 0x100
 GI_BUILD_LSD = 0x10000
+GI_BUILD_HYBRID = 0x20000
 GI_OK, GI_ERR_INVALID, GI_ERR_NOMEM, GI_ERR_CUDA, GI_ERR_TIMEOUT, GI_ERR_CAPACITY = 0, 1, 2, 3, 4, 5
 GI_REQ_POINT, GI_REQ_RANGE = 0, 1
 GI_MISS = 0xFFFFFFFF

@@ -390,7 +390,10 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   const int kw = layout & 0xFF00;
   const int flags = layout & ~0xFFFF;
   if (kw != GI_KEY_U32 && kw != GI_KEY_U64) return fail(GI_ERR_INVALID, "gi_build: bad key width bits 0x%x", kw);
-  if (flags & ~GI_BUILD_LSD) return fail(GI_ERR_INVALID, "gi_build: unknown build flags 0x%x", flags);
+  if (flags & ~(GI_BUILD_LSD | GI_BUILD_HYBRID))
+    return fail(GI_ERR_INVALID, "gi_build: unknown build flags 0x%x", flags);
+  if ((flags & GI_BUILD_LSD) && (flags & GI_BUILD_HYBRID))
+    return fail(GI_ERR_INVALID, "gi_build: GI_BUILD_LSD and GI_BUILD_HYBRID together");
   if (lay != GI_SORTED && lay != GI_EYTZINGER && lay != GI_EYTZINGER_KARY)
     return fail(GI_ERR_INVALID, "gi_build: unknown layout %d", lay);
   if (lay == GI_EYTZINGER_KARY && (k < 2 || k > 33))
@@ -487,7 +490,7 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
     const uint32_t nontrivial = ~trivial & ((1u << kb) - 1);
     GI_TRY2(gi::hybrid_sort(ck, cv, bk, bv, next_dst, n, kb, nontrivial, hist.data(), scratch,
                             idx->geom, lay == GI_SORTED, lay == GI_EYTZINGER ? 1u : 0u,
-                            idx->dflags, s, &res, &used),
+                            (flags & GI_BUILD_HYBRID) != 0, idx->dflags, s, &res, &used),
             "hybrid sort");
     if (res >= 0) {
       ck = bk[res];

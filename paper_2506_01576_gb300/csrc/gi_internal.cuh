@@ -138,15 +138,19 @@ __host__ __device__ __forceinline__ uint32_t slot_of_rank(uint32_t r, const Slot
   return sm.first[l] + xd * km1 + (x - xd * k) - 1;
 }
 
-// Host: the 32-bit map of a geometry with n < 2^32.
-inline SlotMap make_slot_map(const Geom& g) {
-  SlotMap sm{};
+// The 32-bit map of a geometry with n < 2^32 (host or device; on the device
+// fill_slot_map can write straight into shared memory).
+__host__ __device__ inline void fill_slot_map(SlotMap& sm, const Geom& g) {
   sm.top = (uint32_t)g.top;
   sm.b = (uint32_t)g.b;
   sm.m = g.m;
   sm.k = g.k;
   uint64_t p = 1;
   for (uint32_t l = 0; l < 32 && l <= g.m; ++l, p *= g.k) sm.first[l] = (uint32_t)(p - 1);
+}
+inline SlotMap make_slot_map(const Geom& g) {
+  SlotMap sm{};
+  fill_slot_map(sm, g);
   return sm;
 }
 
@@ -229,6 +233,8 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
                          cudaStream_t s);
 
 // Hybrid sort: stable MSD scatter(s) on the top one or two non-trivial digits,
+// (by default only where it measured faster; force = GI_BUILD_HYBRID: wherever it
+// can run),
 // then every bucket sorted in shared memory and written straight into the final
 // layout (gi_local_sort.cu): slot = rank for the sorted layout, else the k-ary
 // (k = g.k; Eytzinger for k = 2, keys shifted by key_off) slot of the rank.
@@ -240,8 +246,8 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
 cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], uint32_t* bv[2],
                         int first_dst, uint64_t n, int key_bytes, uint32_t nontrivial,
                         const unsigned long long* host_hist, void* scratch, const Geom& g,
-                        bool sorted_layout, uint32_t key_off, uint32_t* dflags, cudaStream_t s,
-                        int* result, bool* used);
+                        bool sorted_layout, uint32_t key_off, bool force, uint32_t* dflags,
+                        cudaStream_t s, int* result, bool* used);
 // Shared-memory sort of buckets of at most local_sort_capacity() pairs that
 // agree on every digit outside local_mask, written into the layout (see above).
 uint32_t local_sort_capacity();

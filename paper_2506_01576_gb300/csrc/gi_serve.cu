@@ -211,15 +211,18 @@ __global__ void __launch_bounds__(256) k_serve_fill(const ServeIndex* __restrict
                                                     uint32_t nitems, uint64_t nwork,
                                                     unsigned char* __restrict__ arena) {
   __shared__ uint32_t s_item;
+  __shared__ SlotMap sm;  // the item's 32-bit rank -> slot map
   const int lane = threadIdx.x & 31;
   for (uint64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
     if (threadIdx.x == 0) s_item = find_item(items, nitems, w);
     __syncthreads();
     const ServeItem it = items[s_item];
-    __syncthreads();
-    if (it.kind != kItemFill) continue;
     const ServeIndex d = idx[it.index];
     const Geom g = device_geom(d.n, KF > 1 ? (uint32_t)KF : 2u);
+    const bool narrow = d.n < (1ull << 32);
+    if (threadIdx.x == 0 && it.kind == kItemFill && KF > 0 && narrow) fill_slot_map(sm, g);
+    __syncthreads();
+    if (it.kind != kItemFill) continue;
     const uint64_t* offs = (const uint64_t*)(arena + it.out_off);
     const uint64_t* lo_rank = (const uint64_t*)(arena + it.aux_off);
     uint32_t* out = (uint32_t*)(arena + it.rows_off);
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(256) k_serve_fill(const ServeIndex* __restrict
         r0 = lo_rank[i];
       }
       auto slot = [&](uint64_t r) -> uint64_t {
-        if constexpr (KF > 0) return rank_to_slot<KF>(r, g);
+        if constexpr (KF > 0) return narrow ? slot_of_rank<KF>((uint32_t)r, sm) : rank_to_slot<KF>(r, g);
         else return r;
       };
       const bool big = cnt >= 32;

@@ -803,16 +803,21 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
 cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], uint32_t* bv[2],
                         int first_dst, uint64_t n, int key_bytes, uint32_t nontrivial,
                         const unsigned long long* host_hist, void* scratch, const Geom& g,
-                        bool sorted_layout, uint32_t key_off, uint32_t* dflags, cudaStream_t s,
-                        int* result, bool* used) {
+                        bool sorted_layout, uint32_t key_off, bool force, uint32_t* dflags,
+                        cudaStream_t s, int* result, bool* used) {
   *used = false;
   *result = -1;
   // digits from the most significant down
   int digits[8], nd = 0;
   for (int p = key_bytes - 1; p >= 0; --p)
     if (nontrivial & (1u << p)) digits[nd++] = p;
-  // the bucket sort's slot map is 32-bit: larger indexes take the LSD sort
-  if (nd < 2 || n < (1ull << 20) || n >= (1ull << 32)) return cudaSuccess;
+  // The bucket sort's slot map is 32-bit: larger indexes take the LSD sort.
+  if (nd < 2 || n >= (1ull << 32)) return cudaSuccess;
+  // Measured crossovers (GB300, u64 keys): below 2^24 pairs the buckets are too
+  // small to pay for the extra passes and the host round trip; with four
+  // non-trivial digits or fewer (u32 keys) the two MSD passes save at most two
+  // LSD passes and measured no faster.
+  if (!force && (nd < 5 || n < (1ull << 24))) return cudaSuccess;
   const uint64_t cap = local_sort_capacity();
   const int d1 = digits[0];
   const bool two = nd >= 3 && n / 256 > cap / 4;  // a second MSD digit keeps buckets small

@@ -324,9 +324,9 @@ def test_local_lookup_reordering_changes_nothing(dtype, layout, k):
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
 @pytest.mark.parametrize("dist", ["uniform", "narrow", "dups", "cluster", "skewed"])
 def test_hybrid_msd_build_equals_plain_lsd_build(dtype, dist):
-    # The default build scatters by the top digit(s) and sorts each bucket in shared
-    # memory; GI_BUILD_LSD forces the plain LSD passes.  Both must give the oracle's
-    # layout.  narrow: the top digits are trivial; dups: 16 copies of every key
+    # GI_BUILD_HYBRID scatters by the top digit(s) and sorts each bucket in shared
+    # memory (the default does so only from 2^24 u64 keys up); GI_BUILD_LSD forces
+    # the plain LSD passes.  Both must give the oracle's layout.  narrow: the top digits are trivial; dups: 16 copies of every key
     # (stability); cluster: 20000 keys share their top 16 bits, so one level-2 bucket
     # is too big for a CTA and the build falls back to LSD after the first scatter;
     # skewed: 70% of the keys below 2^16, so the hybrid sort is not tried at all.
@@ -357,7 +357,7 @@ def test_hybrid_msd_build_equals_plain_lsd_build(dtype, dist):
     unique = bool(np.all(sk[1:] != sk[:-1]))
     for layout, k in ((gi.GI_SORTED, 0), (gi.GI_EYTZINGER_KARY, 5)):
         ok, orr = _oracle_layout(keys, rows, layout, k)
-        for flag in (0, gi.GI_BUILD_LSD):
+        for flag in (gi.GI_BUILD_HYBRID, gi.GI_BUILD_LSD):
             idx = build(keys, rows, layout | flag, k)
             lk, lr = layout_arrays(idx, n, dtype)
             assert np.array_equal(lk, ok) and np.array_equal(lr, orr), (layout, flag)
@@ -385,10 +385,37 @@ def test_hybrid_build_writes_every_layout(dtype, layout, k):
     keys = keys[rng.permutation(n)]
     rows = rng.permutation(n).astype(np.uint32)
     ok, orr = _oracle_layout(keys, rows, layout, k)
-    for flag in (0, gi.GI_BUILD_LSD):
+    for flag in (gi.GI_BUILD_HYBRID, gi.GI_BUILD_LSD):
         idx = build(keys, rows, layout | flag, k)
         lk, lr = layout_arrays(idx, n, dtype)
         assert np.array_equal(lk, ok) and np.array_equal(lr, orr), flag
         info = gi.gi_get_info(idx)
         assert info.unique == 1
         gi.gi_destroy(idx)
+
+
+@pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER_KARY, 5), (gi.GI_SORTED, 0)])
+def test_default_build_takes_the_hybrid_sort_at_2e24_u64(layout, k):
+    # the default path at the size where it starts to pay: 2^24 u64 keys.  The
+    # launch count shows which sort ran (hybrid: histogram, scan, two MSD passes,
+    # one per-bucket histogram + scan, the bucket sort = 7 kernels; LSD: histogram,
+    # scan, 8 passes and the permutation or duplicate check = 11).
+    n = 1 << 24
+    keys = W.unique_keys(n, 64, 77)
+    rows = np.random.default_rng(3).permutation(n).astype(np.uint32)
+    ok, orr = _oracle_layout(keys, rows, layout, k)
+    for flag, launches in ((0, 7), (gi.GI_BUILD_LSD, 11)):
+        c0 = gi.gi_launch_count()
+        idx = build(keys, rows, layout | flag, k)
+        assert gi.gi_launch_count() - c0 == launches, flag
+        lk, lr = layout_arrays(idx, n, np.uint64)
+        assert np.array_equal(lk, ok) and np.array_equal(lr, orr), flag
+        gi.gi_destroy(idx)
+
+
+def test_build_flags_are_exclusive():
+    keys = np.arange(10, dtype=np.uint64)
+    rows = np.arange(10, dtype=np.uint32)
+    with pytest.raises(gi.GIError) as e:
+        build(keys, rows, gi.GI_SORTED | gi.GI_BUILD_LSD | gi.GI_BUILD_HYBRID, 0)
+    assert e.value.code == gi.GI_ERR_INVALID

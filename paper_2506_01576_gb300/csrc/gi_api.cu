@@ -18,6 +18,7 @@
 struct GiStaging {
   cudaStream_t st[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t ev = nullptr;
+  cudaEvent_t cev[8] = {};  // one per range-fill chunk
   void* q[3] = {nullptr, nullptr, nullptr};
   uint32_t* out[3] = {nullptr, nullptr, nullptr};
   uint64_t chunk = 0;  // probes per chunk
@@ -101,6 +102,17 @@ PtrKind pointer_kind(const void* p) {
   }
   if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return kDevice;
   return kHost;
+}
+
+// The device's view of page-locked (registered or cudaHostAlloc'ed) host memory,
+// or NULL for pageable memory.
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -192,20 +204,26 @@ cudaError_t launch_point(const gi_index* idx, const gi::LookupCfg& c, const void
   return gi::point_lookup_u64(idx->keys, idx->rows, idx->geom, c, q, m, out, idx->dflags, s);
 }
 
+void free_staging(gi_index* idx) {
+  GiStaging* st = idx->stage;
+  if (!st) return;
+  cudaStreamSynchronize(idx->stream);
+  for (int i = 0; i < 3; ++i) {
+    if (st->st[i]) cudaStreamSynchronize(st->st[i]);
+    cudaFree(st->q[i]);
+    cudaFree(st->out[i]);
+    if (st->st[i]) cudaStreamDestroy(st->st[i]);
+  }
+  if (st->ev) cudaEventDestroy(st->ev);
+  for (cudaEvent_t e : st->cev)
+    if (e) cudaEventDestroy(e);
+  delete st;
+  idx->stage = nullptr;
+}
+
 int ensure_staging(gi_index* idx, uint64_t chunk) {
   if (idx->stage && idx->stage->chunk >= chunk) return GI_OK;
-  if (idx->stage) {
-    cudaStreamSynchronize(idx->stream);
-    for (int i = 0; i < 3; ++i) {
-      if (idx->stage->st[i]) cudaStreamSynchronize(idx->stage->st[i]);
-      cudaFree(idx->stage->q[i]);
-      cudaFree(idx->stage->out[i]);
-      if (idx->stage->st[i]) cudaStreamDestroy(idx->stage->st[i]);
-    }
-    if (idx->stage->ev) cudaEventDestroy(idx->stage->ev);
-    delete idx->stage;
-    idx->stage = nullptr;
-  }
+  free_staging(idx);
   GiStaging* st = new GiStaging();
   st->chunk = chunk;
   idx->stage = st;
@@ -215,6 +233,7 @@ int ensure_staging(gi_index* idx, uint64_t chunk) {
     GI_CUDA(cudaMalloc((void**)&st->out[i], chunk * 4), "staging buffer");
   }
   GI_CUDA(cudaEventCreateWithFlags(&st->ev, cudaEventDisableTiming), "staging event");
+  for (cudaEvent_t& e : st->cev) GI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "staging event");
   return GI_OK;
 }
 
@@ -360,16 +379,7 @@ static void destroy_impl(gi_index* idx) {
   if (!idx) return;
   DeviceScope ds(idx->device);
   cudaStreamSynchronize(idx->stream);
-  if (idx->stage) {
-    for (int i = 0; i < 3; ++i) {
-      if (idx->stage->st[i]) cudaStreamSynchronize(idx->stage->st[i]);
-      cudaFree(idx->stage->q[i]);
-      cudaFree(idx->stage->out[i]);
-      if (idx->stage->st[i]) cudaStreamDestroy(idx->stage->st[i]);
-    }
-    if (idx->stage->ev) cudaEventDestroy(idx->stage->ev);
-    delete idx->stage;
-  }
+  free_staging(idx);
   dfree(idx->keys, idx->stream);
   dfree(idx->rows, idx->stream);
   dfree(idx->dflags, idx->stream);
@@ -458,24 +468,38 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
     GI_TRY2(dalloc(&bk[i], kbytes, s), "sort buffer");
     GI_TRY2(dalloc((void**)&bv[i], rbytes, s), "sort buffer");
   }
+  // Host inputs.  Page-locked memory is read by the kernels over the bus: the
+  // histogram pass copies the keys into bk[0] as it counts them, and the first
+  // sort pass reads the rowIDs where they are (each crosses the bus once, and
+  // the copies overlap the histogram and the first pass).  Pageable memory is
+  // copied first.
   const void* src_k = keys;
   const uint32_t* src_v = rowids;
+  const void* keys_bus = nullptr;  // page-locked host keys, device view
   bool staged = false;
   if (kk == kHost) {
-    GI_TRY2(cudaMemcpyAsync(bk[0], keys, n * kb, cudaMemcpyHostToDevice, s), "copying keys");
+    keys_bus = mapped_host(keys);
+    if (!keys_bus)
+      GI_TRY2(cudaMemcpyAsync(bk[0], keys, n * kb, cudaMemcpyHostToDevice, s), "copying keys");
     src_k = bk[0];
     staged = true;
   }
   if (rk == kHost) {
-    GI_TRY2(cudaMemcpyAsync(bv[0], rowids, n * 4, cudaMemcpyHostToDevice, s), "copying rowids");
-    src_v = bv[0];
-    staged = true;
+    const void* rows_bus = mapped_host(rowids);
+    if (rows_bus) {
+      src_v = (const uint32_t*)rows_bus;
+    } else {
+      GI_TRY2(cudaMemcpyAsync(bv[0], rowids, n * 4, cudaMemcpyHostToDevice, s), "copying rowids");
+      src_v = bv[0];
+      staged = true;
+    }
   }
   const size_t sbytes = gi::sort_scratch_bytes(n, kb);
   GI_TRY2(dalloc(&scratch, sbytes, s), "sort scratch");
   uint32_t trivial = 0;
   std::vector<unsigned long long> hist(8 * 256);
-  GI_TRY2(gi::sort_prepare(src_k, src_v, n, kb, scratch, idx->dflags, s, &trivial, hist.data()),
+  GI_TRY2(gi::sort_prepare(keys_bus ? keys_bus : src_k, keys_bus ? bk[0] : nullptr, n, kb, scratch,
+                           idx->dflags, s, &trivial, hist.data()),
           "histogram");
   // Ping-pong between the two buffers; the first pass writes the buffer that does
   // not hold a staged copy of the input.
@@ -503,12 +527,15 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   for (int p = 0; p < kb && !sorted_done; ++p) {
     if (trivial & (1u << p)) continue;  // every key has the same digit here
     const int dst = next_dst;
-    GI_TRY2(gi::sort_pass(ck, cv, bk[dst], bv[dst], n, kb, p, scratch, idx->dflags, s), "radix pass");
+    // the pass that reads the input rowIDs checks them for the reserved value
+    GI_TRY2(gi::sort_pass(ck, cv, bk[dst], bv[dst], n, kb, p, scratch, idx->dflags, cur < 0, s),
+            "radix pass");
     ck = bk[dst];
     cv = bv[dst];
     cur = dst;
     next_dst = 1 - dst;
   }
+  if (cur < 0) GI_TRY2(gi::check_rowids(cv, n, idx->dflags, s), "rowID check");  // no pass ran
   if (sorted_done) {
     idx->keys = bk[cur];
     idx->rows = bv[cur];
@@ -633,6 +660,8 @@ int gi_range_lookup(const gi_index* cidx, const void* lo, const void* hi, uint64
   uint64_t* doff = nullptr;
   uint32_t* drows = nullptr;
   auto cleanup = [&]() {
+    if (idx->stage)  // copies of a pipelined fill may still read the staged rows
+      for (int i = 0; i < 3; ++i) cudaStreamSynchronize(idx->stage->st[i]);
     if (lk == kHost) dfree(dlo, s);
     if (hk == kHost) dfree(dhi, s);
     if (ofk == kHost) dfree(doff, s);
@@ -676,9 +705,37 @@ int gi_range_lookup(const gi_index* cidx, const void* lo, const void* hi, uint64
     } else {
       drows = out_rowids;
     }
-    GI_TRY3(run(dlo, dhi, doff, drows, true), "range fill");
-    if (rk == kHost && total)
-      GI_TRY3(cudaMemcpyAsync(out_rowids, drows, total * 4, cudaMemcpyDeviceToHost, s), "copying rows");
+    constexpr int kChunks = 8;  // fill chunk c while chunk c-1's rows go to the host
+    if (rk == kHost && total >= (1ull << 22) && m >= (uint64_t)kChunks) {
+      rc = ensure_staging(idx, std::min<uint64_t>(m, 1ull << 22));
+      if (rc != GI_OK) {
+        cleanup();
+        return rc;
+      }
+      GiStaging* st = idx->stage;
+      uint64_t first[kChunks + 1], row0[kChunks + 1];
+      for (int i = 0; i <= kChunks; ++i) first[i] = m * i / kChunks;
+      for (int i = 0; i < kChunks; ++i)  // each chunk's first row
+        GI_TRY3(cudaMemcpyAsync(&row0[i], doff + first[i], 8, cudaMemcpyDeviceToHost, s), "reading offsets");
+      GI_TRY3(cudaStreamSynchronize(s), "range lookup");
+      row0[kChunks] = total;
+      const uint64_t* lo_rank = (const uint64_t*)idx->rscratch;
+      for (int i = 0; i < kChunks; ++i) {
+        GI_TRY3(gi::range_fill_rows(idx->rows, idx->geom, c, doff + first[i], lo_rank + first[i],
+                                    first[i + 1] - first[i], drows, s), "range fill");
+        GI_TRY3(cudaEventRecord(st->cev[i], s), "staging event");
+        cudaStream_t cs = st->st[i % 3];
+        GI_TRY3(cudaStreamWaitEvent(cs, st->cev[i], 0), "staging wait");
+        if (row0[i + 1] > row0[i])
+          GI_TRY3(cudaMemcpyAsync(out_rowids + row0[i], drows + row0[i], (row0[i + 1] - row0[i]) * 4,
+                                  cudaMemcpyDeviceToHost, cs), "copying rows");
+      }
+      for (int i = 0; i < 3; ++i) GI_TRY3(cudaStreamSynchronize(st->st[i]), "copying rows");
+    } else {
+      GI_TRY3(run(dlo, dhi, doff, drows, true), "range fill");
+      if (rk == kHost && total)
+        GI_TRY3(cudaMemcpyAsync(out_rowids, drows, total * 4, cudaMemcpyDeviceToHost, s), "copying rows");
+    }
   }
   if (ofk == kHost)
     GI_TRY3(cudaMemcpyAsync(out_offsets, doff, (m + 1) * 8, cudaMemcpyDeviceToHost, s), "copying offsets");

@@ -194,14 +194,18 @@ struct SortBuffers {
   size_t scratch_bytes;
 };
 size_t sort_scratch_bytes(uint64_t n, int key_bytes);
-// Histogram all digits, check rowIDs; fills hist scan on device; host reads trivial mask.
-cudaError_t sort_prepare(const void* keys, const uint32_t* vals, uint64_t n, int key_bytes,
+// Histogram all digits and scan them on the device; the host gets the trivial
+// mask (and the counts).  copy_to != NULL: `keys` is page-locked host memory,
+// copied to copy_to by the same pass.
+cudaError_t sort_prepare(const void* keys, void* copy_to, uint64_t n, int key_bytes,
                          void* scratch, uint32_t* dflags, cudaStream_t s,
                          uint32_t* host_trivial_mask /* pinned or pageable, sync inside */,
                          unsigned long long* host_hist /* [key_bytes][256], may be NULL */);
+// check_rows: this pass reads the caller's rowIDs; flag any equal to GI_MISS.
 cudaError_t sort_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
                       uint64_t n, int key_bytes, int pass, void* scratch, uint32_t* dflags,
-                      cudaStream_t s);
+                      bool check_rows, cudaStream_t s);
+cudaError_t check_rowids(const uint32_t* rows, uint64_t n, uint32_t* dflags, cudaStream_t s);
 cudaError_t layout_gather(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
                           const Geom& g, int key_bytes, uint32_t key_off, uint32_t* dflags,
                           cudaStream_t s);
@@ -319,6 +323,12 @@ cudaError_t range_lookup_u64(const void* keys, const uint32_t* rows, const Geom&
                              const LookupCfg& c, const void* lo, const void* hi, uint64_t m,
                              uint64_t* offsets, uint32_t* out_rows, void* scratch,
                              bool counts_ready, cudaStream_t s);
+// The fill alone (any key width): ranges [0, m) of `offsets` / `lo_rank` (the
+// scratch's first m words after the count pass); offsets are absolute, so
+// offsets + a, lo_rank + a, m = b - a fill ranges [a, b).
+cudaError_t range_fill_rows(const uint32_t* rows, const Geom& g, const LookupCfg& c,
+                            const uint64_t* offsets, const uint64_t* lo_rank, uint64_t m,
+                            uint32_t* out_rows, cudaStream_t s);
 
 // Probes (gi_probe.cu).
 cudaError_t probe_random_sectors(const void* buf, uint64_t bytes, uint32_t chunk_bytes,

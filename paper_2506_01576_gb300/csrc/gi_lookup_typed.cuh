@@ -15,6 +15,51 @@ inline int range_group(uint32_t k) {
   return g;
 }
 
+// Range fill: rows of ranges [0, m) at their CSR offsets (absolute, so a caller
+// may fill a sub-range by passing offsets + a and lo_rank + a with m = its count).
+inline cudaError_t range_fill(const uint32_t* rows, const Geom& g, const LookupCfg& c,
+                              const uint64_t* offsets, const uint64_t* lo_rank, uint64_t m,
+                              uint32_t* out_rows, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  const int block = 256;
+  uint64_t gr = (m + block - 1) / block;  // one lane per range
+  if (gr > 0x7fffffffull) gr = 0x7fffffffull;
+  const unsigned grid = (unsigned)(gr ? gr : 1);
+  const SlotMap sm = make_slot_map(g);
+  const bool narrow = g.n < (1ull << 32);  // 32-bit rank -> slot map
+#define GI_F(L, KF)                                                                              \
+  do {                                                                                        \
+    if (narrow)                                                                               \
+      k_range_fill<L, KF, uint32_t><<<grid, block, 0, s>>>(rows, g, sm, offsets, lo_rank, m,  \
+                                                           out_rows);                         \
+    else                                                                                      \
+      k_range_fill<L, KF, uint64_t><<<grid, block, 0, s>>>(rows, g, sm, offsets, lo_rank, m,  \
+                                                           out_rows);                         \
+  } while (0)
+  if (c.layout == GI_SORTED) {
+    k_range_fill<0, 0, uint64_t><<<grid, block, 0, s>>>(rows, g, sm, offsets, lo_rank, m, out_rows);
+  } else if (c.range_fill == 1) {  // level runs (Section 5)
+    switch (c.layout == GI_EYTZINGER ? 2u : g.k) {
+#define GI_RL(KF) case KF: k_range_fill_levels<KF><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows); break;
+      GI_RL(2) GI_RL(3) GI_RL(4) GI_RL(5) GI_RL(8) GI_RL(9) GI_RL(16) GI_RL(17) GI_RL(32) GI_RL(33)
+#undef GI_RL
+      default: k_range_fill_levels<0><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows); break;
+    }
+  } else if (c.layout == GI_EYTZINGER) {
+    GI_F(1, 2);
+  } else {
+    switch (g.k) {
+#define GI_RF(KF) case KF: GI_F(2, KF); break;
+      GI_RF(3) GI_RF(4) GI_RF(5) GI_RF(8) GI_RF(9) GI_RF(16) GI_RF(17) GI_RF(32) GI_RF(33)
+#undef GI_RF
+      default: GI_F(2, 0); break;
+    }
+  }
+#undef GI_F
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <class K>
 cudaError_t range_lookup_typed(const K* keys, const uint32_t* rows, const Geom& g,
                                const LookupCfg& c, const K* lo, const K* hi, uint64_t m,
@@ -60,42 +105,7 @@ cudaError_t range_lookup_typed(const K* keys, const uint32_t* rows, const Geom& 
                                     cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
   }
-  if (out_rows) {
-    const int block = 256;
-    uint64_t gr = (m + block - 1) / block;  // one lane per range
-    if (gr > 0x7fffffffull) gr = 0x7fffffffull;
-    const unsigned grid = (unsigned)(gr ? gr : 1);
-    const SlotMap sm = make_slot_map(g);
-    const bool narrow = g.n < (1ull << 32);  // 32-bit rank -> slot map
-#define GI_F(L, KF)                                                                              \
-  do {                                                                                           \
-    if (narrow)                                                                                  \
-      k_range_fill<L, KF, uint32_t><<<grid, block, 0, s>>>(rows, g, sm, offsets, lo_rank, m, out_rows); \
-    else                                                                                         \
-      k_range_fill<L, KF, uint64_t><<<grid, block, 0, s>>>(rows, g, sm, offsets, lo_rank, m, out_rows); \
-  } while (0)
-    if (c.layout == GI_SORTED) {
-      k_range_fill<0, 0, uint64_t><<<grid, block, 0, s>>>(rows, g, sm, offsets, lo_rank, m, out_rows);
-    } else if (c.range_fill == 1) {  // level runs (Section 5)
-      switch (c.layout == GI_EYTZINGER ? 2u : g.k) {
-#define GI_RL(KF) case KF: k_range_fill_levels<KF><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows); break;
-        GI_RL(2) GI_RL(3) GI_RL(4) GI_RL(5) GI_RL(8) GI_RL(9) GI_RL(16) GI_RL(17) GI_RL(32) GI_RL(33)
-#undef GI_RL
-        default: k_range_fill_levels<0><<<grid, block, 0, s>>>(rows, g, offsets, lo_rank, m, out_rows); break;
-      }
-    } else if (c.layout == GI_EYTZINGER) {
-      GI_F(1, 2);
-    } else {
-      switch (g.k) {
-#define GI_RF(KF) case KF: GI_F(2, KF); break;
-        GI_RF(3) GI_RF(4) GI_RF(5) GI_RF(8) GI_RF(9) GI_RF(16) GI_RF(17) GI_RF(32) GI_RF(33)
-#undef GI_RF
-        default: GI_F(2, 0); break;
-      }
-    }
-#undef GI_F
-    count_launch();
-  }
+  if (out_rows) return range_fill(rows, g, c, offsets, lo_rank, m, out_rows, s);
   return cudaGetLastError();
 }
 

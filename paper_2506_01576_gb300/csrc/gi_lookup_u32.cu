@@ -19,4 +19,10 @@ cudaError_t range_lookup_u32(const void* keys, const uint32_t* rows, const Geom&
                                         counts_ready, s);
 }
 
+cudaError_t range_fill_rows(const uint32_t* rows, const Geom& g, const LookupCfg& c,
+                            const uint64_t* offsets, const uint64_t* lo_rank, uint64_t m,
+                            uint32_t* out_rows, cudaStream_t s) {
+  return rg::range_fill(rows, g, c, offsets, lo_rank, m, out_rows, s);
+}
+
 }  // namespace gi

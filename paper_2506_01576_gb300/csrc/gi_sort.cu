@@ -104,29 +104,40 @@ inline size_t header_bytes(int key_bytes) {
 }
 
 // ---------------------------------------------------------------- histogram
+// All digit histograms in one read of the keys.  With copy_to set, the keys are
+// read from page-locked host memory and written to copy_to on the way (the
+// host-to-device copy and the histogram in one pass over the bus).
 template <class K>
 __global__ void __launch_bounds__(256) k_histogram(const K* __restrict__ keys,
-                                                   const uint32_t* __restrict__ rows, uint64_t n,
-                                                   unsigned long long* __restrict__ hist,
-                                                   uint32_t* __restrict__ flags) {
+                                                   K* __restrict__ copy_to, uint64_t n,
+                                                   unsigned long long* __restrict__ hist) {
   constexpr int P = sizeof(K);
   __shared__ uint32_t sh[P][kRadix];
   for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
   __syncthreads();
-  bool bad = false;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const K key = keys[i];
+    if (copy_to) copy_to[i] = key;
 #pragma unroll
     for (int p = 0; p < P; ++p) atomicAdd(&sh[p][(uint32_t)(key >> (8 * p)) & 0xFF], 1u);
-    bad |= rows[i] == GI_MISS;
   }
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagReservedRowid);
   __syncthreads();
   for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) {
     const uint32_t c = (&sh[0][0])[i];
     if (c) atomicAdd(&hist[i], (unsigned long long)c);
   }
+}
+
+// The reserved-rowID check on its own, for a build in which no sort pass reads
+// the input rowIDs (every key equal).
+__global__ void __launch_bounds__(256) k_check_rows(const uint32_t* __restrict__ rows, uint64_t n,
+                                                    uint32_t* __restrict__ flags) {
+  bool bad = false;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    bad |= rows[i] == GI_MISS;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagReservedRowid);
 }
 
 // One block per pass: exclusive scan of the 256 digit counts.
@@ -161,7 +172,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
     const K* __restrict__ src_k, const uint32_t* __restrict__ src_v, K* __restrict__ dst_k,
     uint32_t* __restrict__ dst_v, uint64_t n, uint32_t shift,
     const unsigned long long* __restrict__ digit_off, uint64_t* __restrict__ status,
-    uint32_t* __restrict__ tile_counter, uint32_t epoch, uint32_t* __restrict__ flags) {
+    uint32_t* __restrict__ tile_counter, uint32_t epoch, uint32_t* __restrict__ flags,
+    uint32_t check_rows) {
   constexpr int ITEMS = SortTile<K>::kItems;
   constexpr int TILE = kSortThreads * ITEMS;
   // keys and rowIDs have their own exchange arrays, so one final loop writes both;
@@ -278,11 +290,15 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
     s_keys[rnk[i]] = key[i];
   }
   __syncthreads();  // the digit counters are dead: their space takes the rowIDs
+  bool bad = false;  // a rowID equal to the reserved miss value (first pass only)
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint64_t idx = wbase + (uint64_t)i * 32;
-    hv.vals[rnk[i]] = idx < n ? src_v[idx] : 0u;
+    const uint32_t v = idx < n ? src_v[idx] : 0u;
+    bad |= check_rows && idx < n && v == GI_MISS;
+    hv.vals[rnk[i]] = v;
   }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, kFlagReservedRowid);
   __syncthreads();
 
   // Consecutive threads take consecutive local positions: each digit run goes
@@ -606,17 +622,19 @@ size_t sort_scratch_bytes(uint64_t n, int key_bytes) {
          align256(sizeof(uint64_t) * kRadix * (tiles_for(n, key_bytes) + kRadix + 1));
 }
 
-cudaError_t sort_prepare(const void* keys, const uint32_t* vals, uint64_t n, int key_bytes,
+cudaError_t sort_prepare(const void* keys, void* copy_to, uint64_t n, int key_bytes,
                          void* scratch, uint32_t* dflags, cudaStream_t s,
                          uint32_t* host_trivial_mask, unsigned long long* host_hist) {
+  (void)dflags;
   ScratchView v = view(scratch, key_bytes);
   cudaError_t e = cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, key_bytes), s);
   if (e != cudaSuccess) return e;
-  const int grid = grid_for(n, 256, 4);
+  // reading host memory over the bus wants more loads in flight than HBM does
+  const int grid = grid_for(n, 256, copy_to ? 8 : 4);
   if (key_bytes == 4)
-    k_histogram<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)keys, vals, n, v.hist, dflags);
+    k_histogram<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)keys, (uint32_t*)copy_to, n, v.hist);
   else
-    k_histogram<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)keys, vals, n, v.hist, dflags);
+    k_histogram<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)keys, (uint64_t*)copy_to, n, v.hist);
   k_scan_hist<<<key_bytes, 256, 0, s>>>(v.hist, v.offs, v.trivial, n);
   count_launch(2);
   uint32_t triv[8] = {0};
@@ -637,7 +655,7 @@ cudaError_t sort_prepare(const void* keys, const uint32_t* vals, uint64_t n, int
 
 cudaError_t sort_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
                       uint64_t n, int key_bytes, int pass, void* scratch, uint32_t* dflags,
-                      cudaStream_t s) {
+                      bool check_rows, cudaStream_t s) {
   ScratchView v = view(scratch, key_bytes);
   const uint64_t tiles = tiles_for(n, key_bytes);
   if (tiles == 0) return cudaSuccess;
@@ -646,11 +664,20 @@ cudaError_t sort_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uin
   if (key_bytes == 4)
     k_sort_pass<uint32_t><<<(unsigned)tiles, kSortThreads, 0, s>>>(
         (const uint32_t*)src_k, src_v, (uint32_t*)dst_k, dst_v, n, 8u * pass,
-        v.offs + pass * kRadix, v.status, v.counter + pass, (uint32_t)pass + 1, dflags);
+        v.offs + pass * kRadix, v.status, v.counter + pass, (uint32_t)pass + 1, dflags,
+        check_rows ? 1u : 0u);
   else
     k_sort_pass<uint64_t><<<(unsigned)tiles, kSortThreads, 0, s>>>(
         (const uint64_t*)src_k, src_v, (uint64_t*)dst_k, dst_v, n, 8u * pass,
-        v.offs + pass * kRadix, v.status, v.counter + pass, (uint32_t)pass + 1, dflags);
+        v.offs + pass * kRadix, v.status, v.counter + pass, (uint32_t)pass + 1, dflags,
+        check_rows ? 1u : 0u);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t check_rowids(const uint32_t* rows, uint64_t n, uint32_t* dflags, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_check_rows<<<grid_for(n, 256, 8), 256, 0, s>>>(rows, n, dflags);
   count_launch();
   return cudaGetLastError();
 }
@@ -843,11 +870,11 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
   if (key_bytes == 4)
     k_sort_pass<uint32_t><<<(unsigned)tiles_for(n, 4), kSortThreads, 0, s>>>(
         (const uint32_t*)src_k, src_v, (uint32_t*)bk[dst1], bv[dst1], n, 8u * d1,
-        v.offs + d1 * kRadix, v.status, v.counter + d1, 20u + d1, dflags);
+        v.offs + d1 * kRadix, v.status, v.counter + d1, 20u + d1, dflags, 1u);
   else
     k_sort_pass<uint64_t><<<(unsigned)tiles_for(n, 8), kSortThreads, 0, s>>>(
         (const uint64_t*)src_k, src_v, (uint64_t*)bk[dst1], bv[dst1], n, 8u * d1,
-        v.offs + d1 * kRadix, v.status, v.counter + d1, 20u + d1, dflags);
+        v.offs + d1 * kRadix, v.status, v.counter + d1, 20u + d1, dflags, 1u);
   count_launch();
   int cur = dst1;
   std::vector<BatchTile> segs;  // the buckets the shared-memory sort takes

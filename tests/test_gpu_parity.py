@@ -219,6 +219,36 @@ def test_host_buffers_equal_device_buffers():
     gi.gi_destroy(idx)
 
 
+@pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER_KARY, 5), (gi.GI_SORTED, 0), (gi.GI_EYTZINGER, 0)])
+def test_host_range_fill_pipeline(layout, k):
+    # more than 2^22 rows into host memory: the fill runs in 8 chunks of ranges, each
+    # chunk's rows copied back while the next is filled; a ragged range count,
+    # empty ranges and one range bigger than a chunk
+    n = (1 << 21) + 5
+    keys = W.unique_keys(n, 64, 41)
+    rows = np.random.default_rng(4).permutation(n).astype(np.uint32)
+    sk, sr = oracle.sort_pairs(keys, rows)
+    m = 40003
+    lo, hi, _ = W.ranges_with_expected_rows(n, m, 160, 64, 43)
+    lo[7], hi[7] = hi[7], lo[7]          # lo > hi: empty
+    lo[9], hi[9] = 0, np.uint64(1 << 62)  # about half of all keys
+    woff, wrr = oracle.range_lookup(sk, sr, lo, hi)
+    assert woff[-1] > (1 << 22)
+    idx = build(keys, rows, layout, k)
+    for pinned in (False, True):
+        alloc = (lambda a: torch.from_numpy(a).pin_memory().numpy()) if pinned else (lambda a: a)
+        off = alloc(np.zeros(m + 1, dtype=np.uint64))
+        out = alloc(np.zeros(int(woff[-1]), dtype=np.uint32))
+        gi.gi_range_lookup(idx, alloc(lo.copy()), alloc(hi.copy()), off, out)
+        assert np.array_equal(off, woff) and np.array_equal(out, wrr), pinned
+        # device offsets, host rows
+        offd = torch.empty(m + 1, dtype=torch.int64, device=DEV)
+        out2 = alloc(np.zeros(int(woff[-1]), dtype=np.uint32))
+        gi.gi_range_lookup(idx, to_dev(lo), to_dev(hi), offd, out2)
+        assert np.array_equal(out2, wrr), pinned
+    gi.gi_destroy(idx)
+
+
 def test_reserved_rowid_rejected_and_streams():
     keys = np.arange(100, dtype=np.uint32)
     rows = np.arange(100, dtype=np.uint32)
@@ -242,6 +272,48 @@ def test_reserved_rowid_rejected_and_streams():
         gi.gi_destroy(idx)
     finally:
         gi.gi_set_stream(None, None)
+
+
+def _pin(a):
+    return torch.from_numpy(a).pin_memory().numpy()
+
+
+@pytest.mark.parametrize("sizes", [(1 << 24) + 11, 300007])
+def test_build_from_page_locked_host_memory(sizes):
+    # page-locked keys: the histogram pass copies them over the bus as it counts;
+    # page-locked rowIDs: the first sort pass reads them where they are.  Every
+    # combination of pinned / pageable / device inputs gives the oracle's layout;
+    # 2^24 + 11 u64 keys take the hybrid sort, 300007 the LSD sort.
+    n = sizes
+    keys = W.unique_keys(n, 64, 13)
+    rows = np.random.default_rng(8).permutation(n).astype(np.uint32)
+    ok, orr = _oracle_layout(keys, rows, gi.GI_EYTZINGER_KARY, 5)
+    kinds = {"pinned": _pin, "pageable": lambda a: a.copy(), "device": to_dev}
+    for kk, rk in (("pinned", "pinned"), ("pinned", "pageable"), ("pageable", "pinned"),
+                   ("device", "pinned"), ("pinned", "device")):
+        idx = gi.gi_build(kinds[kk](keys), kinds[rk](rows), gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 5)
+        lk, lr = layout_arrays(idx, n, np.uint64)
+        assert np.array_equal(lk, ok) and np.array_equal(lr, orr), (kk, rk)
+        gi.gi_destroy(idx)
+
+
+@pytest.mark.parametrize("equal_keys", [False, True])
+def test_reserved_rowid_rejected_from_page_locked_rows(equal_keys):
+    # the check runs in the pass that reads the input rowIDs (or on its own when
+    # every key is equal and no pass runs), also when they are read over the bus
+    n = 5000
+    keys = np.full(n, 7, np.uint64) if equal_keys else W.unique_keys(n, 64, 3)
+    rows = np.arange(n, dtype=np.uint32)
+    rows[n - 1] = gi.GI_MISS
+    for lay, k in ((gi.GI_SORTED, 0), (gi.GI_EYTZINGER_KARY, 5)):
+        for src in (_pin, lambda a: a.copy(), to_dev):
+            with pytest.raises(gi.GIError) as e:
+                gi.gi_build(src(keys), src(rows), lay | gi.GI_KEY_U64, k)
+            assert e.value.code == gi.GI_ERR_INVALID
+    rows[n - 1] = n - 1
+    idx = gi.gi_build(_pin(keys), _pin(rows), gi.GI_SORTED | gi.GI_KEY_U64, 0)
+    assert gi.gi_get_info(idx).unique == (0 if equal_keys else 1)
+    gi.gi_destroy(idx)
 
 
 def test_probes_roofline_kernels_run():

@@ -108,19 +108,53 @@ inline size_t header_bytes(int key_bytes) {
 // read from page-locked host memory and written to copy_to on the way (the
 // host-to-device copy and the histogram in one pass over the bus).
 template <class K>
+__device__ __forceinline__ void count_digits(uint32_t (*sh)[kRadix], K key) {
+#pragma unroll
+  for (int p = 0; p < (int)sizeof(K); ++p) atomicAdd(&sh[p][(uint32_t)(key >> (8 * p)) & 0xFF], 1u);
+}
+
+template <class K>
 __global__ void __launch_bounds__(256) k_histogram(const K* __restrict__ keys,
                                                    K* __restrict__ copy_to, uint64_t n,
                                                    unsigned long long* __restrict__ hist) {
   constexpr int P = sizeof(K);
+  constexpr int V = 16 / sizeof(K);  // keys per 16-byte load
   __shared__ uint32_t sh[P][kRadix];
   for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
   __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const K key = keys[i];
-    if (copy_to) copy_to[i] = key;
+  const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // 16-byte loads, two in flight per thread, when both pointers allow them
+  const bool vec = ((uintptr_t)keys % 16 == 0) && ((uintptr_t)copy_to % 16 == 0);
+  const uint64_t nv = vec ? n / V : 0;
+  const uint4* kv = (const uint4*)keys;
+  uint4* cv = (uint4*)copy_to;
+  uint64_t i = gtid;
+  for (; i + stride < nv; i += 2 * stride) {
+    const uint4 a = kv[i], b = kv[i + stride];
+    if (copy_to) {
+      cv[i] = a;
+      cv[i + stride] = b;
+    }
+    const K* ka = (const K*)&a;
+    const K* kb = (const K*)&b;
 #pragma unroll
-    for (int p = 0; p < P; ++p) atomicAdd(&sh[p][(uint32_t)(key >> (8 * p)) & 0xFF], 1u);
+    for (int j = 0; j < V; ++j) {
+      count_digits<K>(sh, ka[j]);
+      count_digits<K>(sh, kb[j]);
+    }
+  }
+  for (; i < nv; i += stride) {
+    const uint4 a = kv[i];
+    if (copy_to) cv[i] = a;
+    const K* ka = (const K*)&a;
+#pragma unroll
+    for (int j = 0; j < V; ++j) count_digits<K>(sh, ka[j]);
+  }
+  for (uint64_t t = nv * V + gtid; t < n; t += stride) {  // the rest one key at a time
+    const K key = keys[t];
+    if (copy_to) copy_to[t] = key;
+    count_digits<K>(sh, key);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) {
@@ -604,8 +638,16 @@ __global__ void __launch_bounds__(256) k_seg_hist1(const K* __restrict__ keys,
     const BatchTile t = chunks[c];
     sh[threadIdx.x] = 0;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < t.count; i += blockDim.x)
-      atomicAdd(&sh[(uint32_t)(keys[t.start + i] >> shift) & 0xFF], 1u);
+    const K* kp = keys + t.start;
+    uint32_t i = threadIdx.x;
+    for (; i + 3 * blockDim.x < t.count; i += 4 * blockDim.x) {  // four loads in flight
+      const K a = kp[i], b = kp[i + blockDim.x], c = kp[i + 2 * blockDim.x], d = kp[i + 3 * blockDim.x];
+      atomicAdd(&sh[(uint32_t)(a >> shift) & 0xFF], 1u);
+      atomicAdd(&sh[(uint32_t)(b >> shift) & 0xFF], 1u);
+      atomicAdd(&sh[(uint32_t)(c >> shift) & 0xFF], 1u);
+      atomicAdd(&sh[(uint32_t)(d >> shift) & 0xFF], 1u);
+    }
+    for (; i < t.count; i += blockDim.x) atomicAdd(&sh[(uint32_t)(kp[i] >> shift) & 0xFF], 1u);
     __syncthreads();
     const uint32_t v = sh[threadIdx.x];
     if (v) atomicAdd(&hist[(uint64_t)t.seg * kRadix + threadIdx.x], (unsigned long long)v);
@@ -629,8 +671,7 @@ cudaError_t sort_prepare(const void* keys, void* copy_to, uint64_t n, int key_by
   ScratchView v = view(scratch, key_bytes);
   cudaError_t e = cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, key_bytes), s);
   if (e != cudaSuccess) return e;
-  // reading host memory over the bus wants more loads in flight than HBM does
-  const int grid = grid_for(n, 256, copy_to ? 8 : 4);
+  const int grid = grid_for(n, 256, 8);
   if (key_bytes == 4)
     k_histogram<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)keys, (uint32_t*)copy_to, n, v.hist);
   else

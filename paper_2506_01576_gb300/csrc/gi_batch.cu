@@ -238,6 +238,8 @@ struct gi_batch {
   void* scratch = nullptr;
   uint32_t* dflags = nullptr;
   uint64_t* d_cs = nullptr;  // B+1 chunk starts of the last lookup
+  void* hy_mem = nullptr;    // tables of the hybrid build
+  gi::BatchHybrid hy{};
   int result = -1;
   uint32_t chunk = 1024;       // probes per work item
   uint32_t smem_budget = 16384;  // bytes of pinned levels per CTA
@@ -296,7 +298,7 @@ void free_batch(gi_batch* b) {
   cudaStreamSynchronize(b->stream);
   void* ptrs[] = {b->d_seg_start, b->d_seg_base, b->d_desc, b->d_tiles, b->d_chunks, b->keys,
                   b->rows, b->tmp_k[0], b->tmp_k[1], b->tmp_v[0], b->tmp_v[1], b->scratch,
-                  b->dflags, b->d_cs};
+                  b->dflags, b->d_cs, b->hy_mem};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaGetLastError();
@@ -358,13 +360,16 @@ int gi_batch_create(const uint64_t* key_offsets, uint32_t B, int layout, uint32_
   // tiles (radix) and chunks (histogram), host-built once
   const uint32_t tile = gi::batch_sort_tile(kb);
   std::vector<gi::BatchTile> tiles, chunks;
+  std::vector<uint32_t> tile0(B + 1);  // first tile of every index
   for (uint32_t i = 0; i < B; ++i) {
     const uint64_t s0 = key_offsets[i], n = key_offsets[i + 1] - s0;
+    tile0[i] = (uint32_t)tiles.size();
     for (uint64_t t = 0, l = 0; t < n; t += tile, ++l)
       tiles.push_back(gi::BatchTile{s0 + t, i, (uint32_t)std::min<uint64_t>(tile, n - t), (uint32_t)l, 0});
     for (uint64_t t = 0, l = 0; t < n; t += gi::kBatchChunk, ++l)
       chunks.push_back(gi::BatchTile{s0 + t, i, (uint32_t)std::min<uint64_t>(gi::kBatchChunk, n - t), (uint32_t)l, 0});
   }
+  tile0[B] = (uint32_t)tiles.size();  // device memory bounds the keys far below 2^32 tiles
   b->ntiles = tiles.size();
   b->nchunks = chunks.size();
   auto bail = [&](int rc) {
@@ -392,6 +397,26 @@ int gi_batch_create(const uint64_t* key_offsets, uint32_t B, int layout, uint32_
   GI_B(cudaMalloc((void**)&b->d_cs, (B + 1) * 8), "batch tables");
   GI_B(cudaMalloc((void**)&b->dflags, 256), "batch status");
   GI_B(cudaMemset(b->dflags, 0, 256), "batch status");
+  {  // tables of the hybrid build: per-index plans and slot maps, MSD window counts
+    GI_B(cudaMalloc(&b->hy_mem, gi::batch_hybrid_bytes(B)), "batch tables");
+    char* q = (char*)b->hy_mem;
+    auto take = [&](size_t bytes) { char* r = q; q += (bytes + 255) & ~size_t(255); return r; };
+    b->hy.plan = (gi::BatchPlan*)take(sizeof(gi::BatchPlan) * B);
+    b->hy.slot_maps = (gi::SlotMap*)take(sizeof(gi::SlotMap) * B);
+    b->hy.hist_w = (unsigned long long*)take(sizeof(uint64_t) * (uint64_t)B * 256);
+    b->hy.offs_w = (unsigned long long*)take(sizeof(uint64_t) * (uint64_t)B * 256);
+    b->hy.counter = (uint32_t*)take(sizeof(uint32_t));
+    uint32_t* d_tile0 = (uint32_t*)take(sizeof(uint32_t) * (B + 1));
+    b->hy.tile0 = d_tile0;
+    b->hy.prefix_msd = (uint32_t*)take(sizeof(uint32_t) * (B + 1));
+    b->hy.prefix_lsd = (uint32_t*)take(sizeof(uint32_t) * (B + 1));
+    GI_B(cudaMemcpy(d_tile0, tile0.data(), sizeof(uint32_t) * (B + 1), cudaMemcpyHostToDevice), "batch tables");
+    b->hy.out_k = b->keys;
+    b->hy.out_v = b->rows;
+    b->hy.seg_base = b->d_seg_base;
+    b->hy.k = layout == GI_SORTED ? 0u : k;
+    GI_B(gi::batch_local_sort_setup(kb, b->hy.k), "batch bucket sort");
+  }
   GI_B(cudaMemcpy(b->d_seg_start, key_offsets, (B + 1) * 8, cudaMemcpyHostToDevice), "batch tables");
   GI_B(cudaMemcpy(b->d_seg_base, base.data(), B * 8, cudaMemcpyHostToDevice), "batch tables");
   GI_B(cudaMemcpy(b->d_desc, b->desc_host.data(), B * sizeof(gi::BatchDesc), cudaMemcpyHostToDevice), "batch tables");
@@ -419,15 +444,17 @@ int gi_batch_build(gi_batch* b, const void* keys, const uint32_t* rowids) {
   if (b->n && (!is_device_ptr(keys) || !is_device_ptr(rowids)))
     return bfail(GI_ERR_INVALID, "gi_batch_build: keys and rowids must be device memory");
   cudaStream_t s = b->stream;
-  cudaError_t e = gi::batch_sort(keys, rowids, b->tmp_k, b->tmp_v, b->n, b->key_bytes, b->d_seg_start,
-                                 b->B, b->d_tiles, b->ntiles, b->d_chunks, b->nchunks, b->scratch,
-                                 b->dflags, s, &b->result);
-  if (e != cudaSuccess) return bcuda(e, "gi_batch_build: sort");
-  e = cudaMemsetAsync(b->keys, 0xFF, b->keys_bytes, s);  // max-key padding after every index
+  // max-key padding after every index first: the bucket sort writes the layouts
+  cudaError_t e = cudaMemsetAsync(b->keys, 0xFF, b->keys_bytes, s);
   if (e != cudaSuccess) return bcuda(e, "gi_batch_build: padding");
-  if (b->result >= 0) {
+  e = gi::batch_sort(keys, rowids, b->tmp_k, b->tmp_v, b->n, b->key_bytes, b->d_seg_start, b->B,
+                     b->d_tiles, b->ntiles, b->d_chunks, b->nchunks, b->scratch, b->dflags, s,
+                     &b->result, &b->hy);
+  if (e != cudaSuccess) return bcuda(e, "gi_batch_build: sort");
+  if (b->result >= 0) {  // indexes whose plan fell back to the LSD passes
     e = gi::batch_gather(b->tmp_k[b->result], b->tmp_v[b->result], b->keys, b->rows, b->d_tiles,
-                         b->ntiles, b->d_seg_start, b->d_seg_base, b->k, b->key_bytes, b->dflags, s);
+                         b->ntiles, b->d_seg_start, b->d_seg_base, b->k, b->key_bytes, b->dflags, s,
+                         &b->hy, b->B);
     if (e != cudaSuccess) return bcuda(e, "gi_batch_build: permutation");
   }
   return GI_OK;

@@ -224,17 +224,61 @@ struct BatchTile {
 constexpr uint32_t kBatchChunk = 65536;  // elements per histogram work item
 uint32_t batch_sort_tile(int key_bytes);  // elements per radix tile
 size_t batch_sort_scratch_bytes(uint64_t ntiles, uint32_t nseg, int key_bytes);
-// hist/offsets/status/counters live in `scratch` (batch_sort_scratch_bytes); no host sync
+
+// How one index of a batch is sorted; written on the device from its digit
+// histograms, so the whole build stays free of host round trips.
+enum : uint32_t {
+  kPlanEmpty = 0,  // no keys
+  kPlanWhole = 1,  // at most local_sort_capacity() pairs: one CTA sorts the index
+  kPlanMsd = 2,    // one stable scatter on its top 8 significant bits, then buckets
+  kPlanLsd = 3,    // a bucket would be too large: the segmented LSD passes
+};
+struct BatchPlan {
+  uint32_t mode;
+  uint32_t s1;        // shift of the MSD window (kPlanMsd)
+  uint32_t ts;        // shift of the bucket sort's top window
+  uint32_t lsd_mask;  // bytes that differ between the index's keys
+};
+// Device tables of the hybrid batch build (allocated with the batch).
+struct BatchHybrid {
+  BatchPlan* plan;              // [nseg]
+  SlotMap* slot_maps;           // [nseg] (k-ary layouts)
+  unsigned long long* hist_w;   // [nseg][256] counts of the MSD window
+  unsigned long long* offs_w;   // [nseg][256] their absolute starts
+  uint32_t* counter;            // tile tickets of the MSD pass
+  void* out_k;                  // the batch's padded key / rowID arrays
+  uint32_t* out_v;
+  const uint64_t* seg_base;     // slot 0 of every index in out_k / out_v
+  const uint32_t* tile0;        // [nseg + 1] first radix tile of every index
+  uint32_t* prefix_msd;         // [nseg + 1] tiles of the kPlanMsd indexes before index s
+  uint32_t* prefix_lsd;         // [nseg + 1] same for kPlanLsd
+  uint32_t k;                   // fan-out; 0 = sorted layout
+};
+size_t batch_hybrid_bytes(uint32_t nseg);  // device bytes of the tables
+// hist/offsets/status/counters live in `scratch` (batch_sort_scratch_bytes); no host
+// sync.  hy != NULL: indexes are sorted per their plan (whole / MSD + buckets, written
+// straight into hy->out_k / out_v), and only kPlanLsd indexes take the LSD passes
+// (their result then needs batch_gather with the same plan).
 cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], uint32_t* tmp_v[2],
                        uint64_t n, int key_bytes, const uint64_t* seg_start, uint32_t nseg,
                        const BatchTile* tiles, uint64_t ntiles, const BatchTile* chunks,
                        uint64_t nchunks, void* scratch, uint32_t* dflags, cudaStream_t s,
-                       int* result_buf);
-// permute every index into k-ary order (k = 0: sorted) at out + seg_base[s]
+                       int* result_buf, const BatchHybrid* hy);
+// The bucket sort of a batch: every index of plan kPlanWhole, and every MSD bucket
+// of the kPlanMsd indexes (in src_k / src_v after the MSD pass).
+cudaError_t batch_local_sort(const void* keys, const uint32_t* vals, const void* src_k,
+                             const uint32_t* src_v, const uint64_t* seg_start, uint32_t nseg,
+                             int key_bytes, const BatchHybrid& hy, uint32_t* dflags,
+                             cudaStream_t s);
+// Raises the bucket-sort kernels' shared-memory limit (once, before any capture).
+cudaError_t batch_local_sort_setup(int key_bytes, uint32_t k);
+// hy != NULL: only the tiles of the kPlanLsd indexes (of nseg)
 cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t* ov,
                          const BatchTile* tiles, uint64_t ntiles, const uint64_t* seg_start,
                          const uint64_t* seg_base, uint32_t k, int key_bytes, uint32_t* dflags,
-                         cudaStream_t s);
+                         cudaStream_t s, const BatchHybrid* hy, uint32_t nseg);
+// permute every index into k-ary order (k = 0: sorted) at out + seg_base[s]
+
 
 // Hybrid sort: stable MSD scatter(s) on the top one or two non-trivial digits,
 // (by default only where it measured faster; force = GI_BUILD_HYBRID: wherever it

@@ -122,94 +122,180 @@ __device__ __forceinline__ void digit_pass(K* s_k, uint32_t* s_v, uint32_t (*h)[
   __syncthreads();
 }
 
+// Shared-memory views of one CTA's bucket (dynamic shared memory, LocalSmem::bytes).
+template <class K, int ITEMS>
+struct BucketSmem {
+  static constexpr int TILE = kThreads * ITEMS;
+  K* s_k;
+  uint32_t* s_v;
+  uint32_t (*h)[kRadix];  // [warps][256]
+  uint32_t* s_start;
+  uint32_t* s_end;
+  uint32_t* s_wt;
+  uint16_t* s_src;  // sorted position -> position in s_k / s_v
+  __device__ explicit BucketSmem(unsigned char* raw) {
+    s_k = (K*)raw;
+    s_v = (uint32_t*)(s_k + TILE);
+    h = (uint32_t (*)[kRadix])(s_v + TILE);
+    s_start = (uint32_t*)(h + kWarps);
+    s_end = s_start + kRadix;
+    s_wt = s_end + kRadix;
+    s_src = (uint16_t*)(s_wt + kWarps);
+  }
+};
+
+// Sorts the `count` pairs at src + start (count <= kThreads * ITEMS) in shared
+// memory.  top_shift: the window (8 bits at that shift) that splits the bucket
+// into sub-buckets for count ranking; lsd_mask: the bytes that may differ inside
+// the bucket, sorted one ballot pass each (LSD order) when a sub-bucket is larger
+// than `limit`; single: the top window alone orders the bucket.  Returns true if
+// s_k / s_v end in sorted order, false if s_src holds it.  Block-uniform.
+template <class K, int ITEMS>
+__device__ __forceinline__ bool sort_bucket(const BucketSmem<K, ITEMS>& m,
+                                            const K* __restrict__ src_k,
+                                            const uint32_t* __restrict__ src_v, uint64_t start,
+                                            uint32_t count, uint32_t top_shift, uint32_t lsd_mask,
+                                            bool single, uint32_t limit) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t items = (count + kThreads - 1) / kThreads;  // <= ITEMS
+  const uint32_t used = items * kThreads;
+  for (uint32_t j = tid; j < used; j += kThreads) {
+    const bool in = j < count;
+    m.s_k[j] = in ? src_k[start + j] : ~K(0);  // padding sorts last, stably
+    m.s_v[j] = in ? src_v[start + j] : 0u;
+  }
+  __syncthreads();
+  // the top window first; if a sub-bucket is too big for count ranking, every
+  // byte of lsd_mask again in LSD order (one pass loop keeps one copy of the
+  // pass's code and its registers).  The top pass then sorts on top_shift with
+  // todo's bit standing for it.
+  bool first = lsd_mask != 0, direct = single || lsd_mask == 0;
+  uint32_t todo = first ? 1u : 0u;
+  while (todo) {
+    const uint32_t shift = first ? top_shift : 8u * (uint32_t)(__ffs(todo) - 1);
+    todo &= todo - 1;
+    digit_pass<K, ITEMS>(m.s_k, m.s_v, m.h, m.s_start, m.s_wt, items, shift);
+    if (first) {
+      first = false;
+      if (!single) {
+        // sub-bucket d covers [s_start[d], s_end[d]) of real keys (padding sits
+        // after count: it has the largest window value and came last)
+        const uint32_t st = m.s_start[tid];
+        const uint32_t en = tid < kRadix - 1 ? m.s_start[tid + 1] : used;
+        const uint32_t en_real = en < count ? en : count;
+        m.s_end[tid] = en_real;
+        const bool big = (en_real > st ? en_real - st : 0u) > limit;
+        if (__syncthreads_or(big)) {
+          todo = lsd_mask;
+          direct = true;
+        }
+      }
+    }
+  }
+  if (!direct) {
+    const uint32_t wofs = (uint32_t)warp * 32 * items + lane;
+#pragma unroll 1
+    for (uint32_t i = 0; i < items; ++i) {
+      const uint32_t p = wofs + i * 32;
+      if (p < count) {
+        const K x = m.s_k[p];
+        const uint32_t d = (uint32_t)(x >> top_shift) & 0xFF;
+        const uint32_t b = m.s_start[d], e = m.s_end[d];
+        uint32_t r = 0;
+        for (uint32_t j = b; j < e; ++j) {
+          const K y = m.s_k[j];
+          r += (y < x || (y == x && j < p)) ? 1u : 0u;
+        }
+        m.s_src[b + r] = (uint16_t)p;
+      }
+    }
+    __syncthreads();
+  }
+  return direct;
+}
+
 // KF: 1 = sorted layout (slot = rank); >= 2 = k-ary Eytzinger with that fan-out
-// (2 = Eytzinger); 0 = k-ary with the fan-out g.k read at run time.
+// (2 = Eytzinger); 0 = k-ary with the fan-out read at run time.
 template <class K, int ITEMS, int MINB, int KF>
 __global__ void __launch_bounds__(kThreads, MINB) k_local_sort(
     const K* __restrict__ src_k, const uint32_t* __restrict__ src_v, K* __restrict__ dst_k,
     uint32_t* __restrict__ dst_v, const BatchTile* __restrict__ segs, uint64_t nseg,
     uint32_t local_mask, uint32_t limit, SlotMap sm, uint32_t key_off, uint32_t* __restrict__ flags) {
-  constexpr int TILE = kThreads * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  K* s_k = (K*)smem_raw;
-  uint32_t* s_v = (uint32_t*)(s_k + TILE);
-  uint32_t (*h)[kRadix] = (uint32_t (*)[kRadix])(s_v + TILE);  // [warps][256]
-  uint32_t* s_start = (uint32_t*)(h + kWarps);
-  uint32_t* s_end = s_start + kRadix;
-  uint32_t* s_wt = s_end + kRadix;
-  uint16_t* s_src = (uint16_t*)(s_wt + kWarps);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const BucketSmem<K, ITEMS> m(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t top = local_mask ? 31u - (uint32_t)__clz(local_mask) : 0u;
-  const uint32_t top_shift = 8u * top;
   const bool single = __popc(local_mask) <= 1;  // the top pass alone sorts the bucket
   bool dup = false;
   for (uint64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
     const BatchTile seg = segs[sg];
-    const uint32_t items = (seg.count + kThreads - 1) / kThreads;  // <= ITEMS
-    const uint32_t used = items * kThreads;
-    for (uint32_t j = tid; j < used; j += kThreads) {
-      const bool in = j < seg.count;
-      s_k[j] = in ? src_k[seg.start + j] : ~K(0);  // padding sorts last, stably
-      s_v[j] = in ? src_v[seg.start + j] : 0u;
-    }
-    __syncthreads();
-    // the top local digit first; if a sub-bucket is too big for count ranking,
-    // every local digit again in LSD order (one pass loop keeps one copy of the
-    // pass's code and its registers)
-    uint32_t todo = local_mask ? 1u << top : 0u;
-    bool first = true, direct = single;
-    while (todo) {
-      const uint32_t shift = 8u * (uint32_t)(__ffs(todo) - 1);
-      todo &= todo - 1;
-      digit_pass<K, ITEMS>(s_k, s_v, h, s_start, s_wt, items, shift);
-      if (first && !single) {
-        first = false;
-        // sub-bucket d covers [s_start[d], s_end[d]) of real keys (padding sits
-        // after seg.count: it has the largest digit and came last)
-        const uint32_t st = s_start[tid];
-        const uint32_t en = tid < kRadix - 1 ? s_start[tid + 1] : used;
-        const uint32_t en_real = en < seg.count ? en : seg.count;
-        s_end[tid] = en_real;
-        const bool big = (en_real > st ? en_real - st : 0u) > limit;
-        if (__syncthreads_or(big)) {
-          todo = local_mask;
-          direct = true;
-        }
-      }
-    }
-    if (!direct) {
-      const uint32_t wofs = (uint32_t)warp * 32 * items + lane;
-#pragma unroll 1
-      for (uint32_t i = 0; i < items; ++i) {
-        const uint32_t p = wofs + i * 32;
-        if (p < seg.count) {
-          const K x = s_k[p];
-          const uint32_t d = (uint32_t)(x >> top_shift) & 0xFF;
-          const uint32_t b = s_start[d], e = s_end[d];
-          uint32_t r = 0;
-          for (uint32_t j = b; j < e; ++j) {
-            const K y = s_k[j];
-            r += (y < x || (y == x && j < p)) ? 1u : 0u;
-          }
-          s_src[b + r] = (uint16_t)p;
-        }
-      }
-      __syncthreads();
-    }
+    const bool direct = sort_bucket<K, ITEMS>(m, src_k, src_v, seg.start, seg.count, 8u * top,
+                                              local_mask, single, limit);
     // sorted position j -> rank seg.start + j -> its slot in the layout
     for (uint32_t j = tid; j < seg.count; j += kThreads) {
-      const uint32_t p = direct ? j : s_src[j];
-      const K key = s_k[p];
-      if (j > 0) dup |= s_k[direct ? j - 1 : s_src[j - 1]] == key;
+      const uint32_t p = direct ? j : m.s_src[j];
+      const K key = m.s_k[p];
+      if (j > 0) dup |= m.s_k[direct ? j - 1 : m.s_src[j - 1]] == key;
       const uint32_t r = (uint32_t)(seg.start + j);
       uint32_t t = r;
       if constexpr (KF != 1) t = slot_of_rank<KF>(r, sm);
       dst_k[t + key_off] = key;
-      dst_v[t] = s_v[p];
+      dst_v[t] = m.s_v[p];
     }
     __syncthreads();
   }
   if (key_off && blockIdx.x == 0 && tid == 0) dst_k[0] = K(0);  // Eytzinger's empty slot
+  if (__any_sync(0xffffffffu, dup) && lane == 0) atomicOr(flags, kFlagDuplicate);
+}
+
+// The batch's buckets: logical bucket id < nseg * 256 is window value (id & 255)
+// of index id >> 8 (indexes of plan kPlanMsd, sorted pairs in src after the MSD
+// pass); id >= nseg * 256 is the whole index id - nseg * 256 (plan kPlanWhole,
+// pairs still in the input).  A launch takes the buckets of (lo_count, hi_count]
+// pairs.  Each writes its index's layout at out + seg_base[i].
+template <class K, int ITEMS, int MINB, int KF>
+__global__ void __launch_bounds__(kThreads, MINB) k_batch_local_sort(
+    const K* __restrict__ keys, const uint32_t* __restrict__ vals, const K* __restrict__ src_k,
+    const uint32_t* __restrict__ src_v, const uint64_t* __restrict__ seg_start, uint32_t nseg,
+    const BatchPlan* __restrict__ plan, const SlotMap* __restrict__ maps,
+    const unsigned long long* __restrict__ hist_w, const unsigned long long* __restrict__ offs_w,
+    K* __restrict__ out_k, uint32_t* __restrict__ out_v, const uint64_t* __restrict__ seg_base,
+    uint32_t lo_count, uint32_t hi_count, uint32_t* __restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BucketSmem<K, ITEMS> m(smem_raw);
+  __shared__ SlotMap s_map;
+  const int tid = threadIdx.x, lane = tid & 31;
+  bool dup = false;
+  const uint64_t total = (uint64_t)nseg * kRadix + nseg;
+  for (uint64_t id = blockIdx.x; id < total; id += gridDim.x) {
+    const bool msd = id < (uint64_t)nseg * kRadix;
+    const uint32_t i = msd ? (uint32_t)(id >> 8) : (uint32_t)(id - (uint64_t)nseg * kRadix);
+    const BatchPlan pl = plan[i];
+    if (pl.mode != (msd ? kPlanMsd : kPlanWhole)) continue;
+    const uint64_t s0 = seg_start[i];
+    const uint64_t start = msd ? offs_w[id] : s0;
+    const uint32_t count = (uint32_t)(msd ? hist_w[id] : seg_start[i + 1] - s0);
+    if (count <= lo_count || count > hi_count) continue;  // another launch's size class
+    if constexpr (KF != 1) {
+      if (tid < (int)(sizeof(SlotMap) / 4)) ((uint32_t*)&s_map)[tid] = ((const uint32_t*)&maps[i])[tid];
+    }
+    const uint32_t limit = 8u * (uint32_t)__popc(pl.lsd_mask) + 8u;
+    const bool direct = sort_bucket<K, ITEMS>(m, msd ? src_k : keys, msd ? src_v : vals, start,
+                                              count, pl.ts, pl.lsd_mask, false, limit);
+    const uint64_t base = seg_base[i];
+    const uint32_t r0 = (uint32_t)(start - s0);
+    for (uint32_t j = tid; j < count; j += kThreads) {
+      const uint32_t p = direct ? j : m.s_src[j];
+      const K key = m.s_k[p];
+      if (j > 0) dup |= m.s_k[direct ? j - 1 : m.s_src[j - 1]] == key;
+      const uint32_t r = r0 + j;
+      uint32_t t = r;
+      if constexpr (KF != 1) t = slot_of_rank<KF>(r, s_map);
+      out_k[base + t] = key;
+      out_v[base + t] = m.s_v[p];
+    }
+    __syncthreads();
+  }
   if (__any_sync(0xffffffffu, dup) && lane == 0) atomicOr(flags, kFlagDuplicate);
 }
 
@@ -276,6 +362,73 @@ cudaError_t local_sort(const void* sk, const uint32_t* sv, void* dk, uint32_t* d
                                sorted_layout, key_off, dflags, s);
   return launch_kf<uint64_t>(sk, sv, dk, dv, segs, nseg, max_count, local_mask, limit, g,
                              sorted_layout, key_off, dflags, s);
+}
+
+namespace {
+
+// setup: only raise the kernels' dynamic shared-memory limit (done when the batch
+// is created, so that builds launch kernels only and can be captured in a graph)
+template <class K, int KF>
+cudaError_t launch_batch(const void* keys, const uint32_t* vals, const void* src_k,
+                         const uint32_t* src_v, const uint64_t* seg_start, uint32_t nseg,
+                         const BatchHybrid& hy, uint32_t* dflags, cudaStream_t s, bool setup) {
+#define GI_BLS(IT, MB, LO, HI)                                                                 \
+  do {                                                                                         \
+    auto kern = k_batch_local_sort<K, IT, MB, KF>;                                             \
+    const size_t smem = LocalSmem::bytes<K>(IT);                                               \
+    if (setup) {                                                                               \
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                           (int)smem);                                         \
+      if (e != cudaSuccess) return e;                                                          \
+      break;                                                                                   \
+    }                                                                                          \
+    const unsigned grid = (unsigned)sm_count() * MB * 4;                                       \
+    kern<<<grid, kThreads, smem, s>>>((const K*)keys, vals, (const K*)src_k, src_v, seg_start, \
+                                      nseg, hy.plan, hy.slot_maps, hy.hist_w, hy.offs_w,       \
+                                      (K*)hy.out_k, hy.out_v, hy.seg_base, LO, HI, dflags);    \
+    count_launch();                                                                            \
+  } while (0)
+  // two size classes: up to 12 pairs per thread (3 CTAs per SM), then up to 16
+  GI_BLS(12, 3, 0u, kThreads * 12u);
+  GI_BLS(16, 2, kThreads * 12u, kThreads * 16u);
+#undef GI_BLS
+  return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_batch_kf(const void* keys, const uint32_t* vals, const void* src_k,
+                            const uint32_t* src_v, const uint64_t* seg_start, uint32_t nseg,
+                            const BatchHybrid& hy, uint32_t* dflags, cudaStream_t s, bool setup) {
+#define GI_B(KF) launch_batch<K, KF>(keys, vals, src_k, src_v, seg_start, nseg, hy, dflags, s, setup)
+  switch (hy.k) {
+    case 0: return GI_B(1);
+    case 3: return GI_B(3);
+    case 5: return GI_B(5);
+    case 9: return GI_B(9);
+    case 17: return GI_B(17);
+    default: return GI_B(0);
+  }
+#undef GI_B
+}
+
+}  // namespace
+
+cudaError_t batch_local_sort(const void* keys, const uint32_t* vals, const void* src_k,
+                             const uint32_t* src_v, const uint64_t* seg_start, uint32_t nseg,
+                             int key_bytes, const BatchHybrid& hy, uint32_t* dflags,
+                             cudaStream_t s) {
+  if (nseg == 0) return cudaSuccess;
+  if (key_bytes == 4)
+    return launch_batch_kf<uint32_t>(keys, vals, src_k, src_v, seg_start, nseg, hy, dflags, s, false);
+  return launch_batch_kf<uint64_t>(keys, vals, src_k, src_v, seg_start, nseg, hy, dflags, s, false);
+}
+
+cudaError_t batch_local_sort_setup(int key_bytes, uint32_t k) {
+  BatchHybrid hy{};
+  hy.k = k;
+  if (key_bytes == 4)
+    return launch_batch_kf<uint32_t>(nullptr, nullptr, nullptr, nullptr, nullptr, 0, hy, nullptr, 0, true);
+  return launch_batch_kf<uint64_t>(nullptr, nullptr, nullptr, nullptr, nullptr, 0, hy, nullptr, 0, true);
 }
 
 }  // namespace gi

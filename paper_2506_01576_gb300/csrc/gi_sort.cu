@@ -51,6 +51,15 @@ constexpr uint64_t kStatAggregate = 1ull << 62;
 constexpr uint64_t kStatInclusive = 2ull << 62;
 constexpr uint64_t kValueMask = (1ull << 40) - 1;
 
+// Tickets -> tiles of a subset of a batch's indexes: ticket t is tile
+// tile0[s] + t - prefix[s] of the index s with prefix[s] <= t < prefix[s + 1]
+// (prefix counts only the listed indexes' tiles).  prefix == NULL: tile = ticket.
+struct TileMap {
+  const uint32_t* prefix;
+  const uint32_t* tile0;
+  uint32_t nseg;
+};
+
 __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p) {
   uint64_t v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -408,11 +417,29 @@ __global__ void __launch_bounds__(256) k_batch_histogram(const K* __restrict__ k
     const BatchTile t = chunks[c];
     for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < t.count; i += blockDim.x) {
-      const K key = keys[t.start + i];
+    const K* kp = keys + t.start;
+    const uint32_t* rp = rows + t.start;
+    uint32_t i = threadIdx.x;
+    for (; i + 3 * blockDim.x < t.count; i += 4 * blockDim.x) {  // four keys in flight
+      K kk[4];
+      uint32_t rr[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        kk[u] = kp[i + u * blockDim.x];
+        rr[u] = rp[i + u * blockDim.x];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) atomicAdd(&sh[p][(uint32_t)(kk[u] >> (8 * p)) & 0xFF], 1u);
+        bad |= rr[u] == GI_MISS;
+      }
+    }
+    for (; i < t.count; i += blockDim.x) {
+      const K key = kp[i];
 #pragma unroll
       for (int p = 0; p < P; ++p) atomicAdd(&sh[p][(uint32_t)(key >> (8 * p)) & 0xFF], 1u);
-      bad |= rows[t.start + i] == GI_MISS;
+      bad |= rp[i] == GI_MISS;
     }
     __syncthreads();
     unsigned long long* h = hist + (uint64_t)t.seg * P * kRadix;
@@ -457,7 +484,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_batch_sort_pass(
     uint32_t* __restrict__ dst_v, uint64_t n, uint32_t shift, const BatchTile* __restrict__ tiles,
     const unsigned long long* __restrict__ offs, int pass, int passes,
     uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter, uint32_t epoch,
-    uint32_t* __restrict__ flags) {
+    uint32_t* __restrict__ flags, const BatchPlan* __restrict__ plan, uint32_t want,
+    uint32_t window, TileMap map) {
   constexpr int ITEMS = SortTile<K>::kItems;
   constexpr int TILE = kSortThreads * ITEMS;
   union HistOrVals {
@@ -472,11 +500,35 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_batch_sort_pass(
   __shared__ uint32_t s_tile;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t shift0 = shift;
+  // Tickets are taken in order; with a map, ticket t is the t-th tile of the
+  // indexes the map lists and the grid is persistent (a CTA takes tickets until
+  // none is left), else one ticket per CTA.  A CTA waits in the look-back only
+  // on tiles of lower tickets, held by CTAs that are running, so it always ends.
+  for (;;) {
   if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
   for (int i = lane; i < kRadix; i += 32) hv.h[warp][i] = 0;
   __syncthreads();
-  const uint64_t tile = s_tile;
+  const uint32_t ticket = s_tile;
+  uint64_t tile = ticket;
+  if (map.prefix) {
+    if (ticket >= map.prefix[map.nseg]) return;
+    uint32_t lo = 0, hi = map.nseg;  // prefix[lo] <= ticket < prefix[hi]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (map.prefix[mid] <= ticket) lo = mid; else hi = mid;
+    }
+    tile = map.tile0[lo] + (ticket - map.prefix[lo]);
+  }
   const BatchTile desc = tiles[tile];
+  // with a plan, only the indexes sorted this way take part (a whole index is
+  // skipped, so no tile of it is ever waited for)
+  if (plan && plan[desc.seg].mode != want) {
+    if (!map.prefix) return;
+    __syncthreads();
+    continue;
+  }
+  shift = (plan && window) ? plan[desc.seg].s1 : shift0;  // the index's MSD window
   const uint64_t tile_base = desc.start;
   const uint32_t valid = desc.count;
   const unsigned long long* digit_off = offs + ((uint64_t)desc.seg * passes + pass) * kRadix;
@@ -588,6 +640,9 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_batch_sort_pass(
       }
     }
   }
+  if (!map.prefix) return;
+  __syncthreads();  // shared memory is reused by the next ticket
+  }
 }
 
 // slot t of index s <- sorted position slot_to_rank(t); k = 0: the sorted order itself
@@ -599,10 +654,23 @@ __global__ void __launch_bounds__(256) k_batch_gather(const K* __restrict__ sk,
                                                       uint64_t ntiles,
                                                       const uint64_t* __restrict__ seg_start,
                                                       const uint64_t* __restrict__ seg_base,
-                                                      uint32_t k, uint32_t* __restrict__ flags) {
+                                                      uint32_t k, uint32_t* __restrict__ flags,
+                                                      const BatchPlan* __restrict__ plan,
+                                                      TileMap map) {
   bool dup = false;
-  for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-    const BatchTile t = tiles[ti];
+  const uint64_t total = map.prefix ? map.prefix[map.nseg] : ntiles;
+  for (uint64_t ti = blockIdx.x; ti < total; ti += gridDim.x) {
+    uint64_t tix = ti;
+    if (map.prefix) {  // the ti-th tile of the listed indexes
+      uint32_t lo = 0, hi = map.nseg;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (map.prefix[mid] <= ti) lo = mid; else hi = mid;
+      }
+      tix = map.tile0[lo] + (ti - map.prefix[lo]);
+    }
+    const BatchTile t = tiles[tix];
+    if (plan && plan[t.seg].mode != kPlanLsd) continue;
     const uint64_t s0 = seg_start[t.seg];
     const uint64_t n = seg_start[t.seg + 1] - s0;
     const uint64_t out0 = seg_base[t.seg];
@@ -620,6 +688,175 @@ __global__ void __launch_bounds__(256) k_batch_gather(const K* __restrict__ sk,
     }
   }
   if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagDuplicate);
+}
+
+// ---------------------------------------------------------------- hybrid batch build
+// One CTA per index: from its digit histograms, the bytes in which its keys differ,
+// the highest such bit hb, and the plan: at most `cap` pairs -> one CTA sorts the
+// whole index (top window = its 8 highest significant bits); more -> one stable
+// scatter on bits [hb-7, hb] (the MSD window), then buckets with the next 8 bits as
+// their top window.  The k-ary slot map of the index goes to maps[i].
+__global__ void __launch_bounds__(256) k_batch_plan(const unsigned long long* __restrict__ hist,
+                                                    const uint64_t* __restrict__ seg_start,
+                                                    int key_bytes, uint32_t k, uint32_t cap,
+                                                    BatchPlan* __restrict__ plan,
+                                                    SlotMap* __restrict__ maps) {
+  __shared__ int s_lo[8], s_hi[8];
+  const uint32_t i = blockIdx.x;
+  const int d = threadIdx.x;
+  if (d < 8) {
+    s_lo[d] = kRadix;
+    s_hi[d] = -1;
+  }
+  __syncthreads();
+  for (int p = 0; p < key_bytes; ++p) {
+    if (hist[((uint64_t)i * key_bytes + p) * kRadix + d]) {
+      atomicMin(&s_lo[p], d);
+      atomicMax(&s_hi[p], d);
+    }
+  }
+  __syncthreads();
+  if (d != 0) return;
+  const uint64_t n = seg_start[i + 1] - seg_start[i];
+  BatchPlan pl{};
+  int hb = -1;  // highest bit in which two keys differ
+  for (int p = key_bytes - 1; p >= 0; --p) {
+    if (s_hi[p] > s_lo[p]) {
+      pl.lsd_mask |= 1u << p;
+      if (hb < 0) hb = 8 * p + (31 - __clz((uint32_t)(s_lo[p] ^ s_hi[p])));
+    }
+  }
+  if (n == 0) {
+    pl.mode = kPlanEmpty;
+  } else if (n <= cap) {
+    pl.mode = kPlanWhole;
+    pl.ts = hb >= 7 ? (uint32_t)hb - 7 : 0u;
+  } else {
+    // MSD window of w bits, w just large enough for buckets of about 2048 pairs
+    // (more buckets only add per-bucket work); bits above hb are common to all
+    // keys, so an 8-bit digit at s1 = hb + 1 - w takes 2^w values
+    pl.mode = kPlanMsd;  // kPlanLsd if a window bucket turns out larger than cap
+    uint32_t w = 1;
+    while (w < 8 && (n >> w) > 2048) ++w;
+    pl.s1 = hb + 1 >= (int)w ? (uint32_t)(hb + 1 - (int)w) : 0u;
+    pl.ts = pl.s1 >= 8 ? pl.s1 - 8 : 0u;
+  }
+  plan[i] = pl;
+  if (k >= 2 && n > 0 && n < (1ull << 32)) fill_slot_map(maps[i], device_geom(n, k));
+}
+
+// Counts of the MSD window per index (indexes of plan kPlanMsd only).
+template <class K>
+__global__ void __launch_bounds__(256) k_batch_window_hist(const K* __restrict__ keys,
+                                                           const BatchTile* __restrict__ chunks,
+                                                           uint64_t nchunks,
+                                                           const BatchPlan* __restrict__ plan,
+                                                           unsigned long long* __restrict__ hist) {
+  __shared__ uint32_t sh[kRadix];
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const BatchTile t = chunks[c];
+    const BatchPlan pl = plan[t.seg];
+    if (pl.mode != kPlanMsd) continue;
+    sh[threadIdx.x] = 0;
+    __syncthreads();
+    const K* kp = keys + t.start;
+    uint32_t i = threadIdx.x;
+    for (; i + 3 * blockDim.x < t.count; i += 4 * blockDim.x) {  // four loads in flight
+      const K a = kp[i], b = kp[i + blockDim.x], c2 = kp[i + 2 * blockDim.x], d = kp[i + 3 * blockDim.x];
+      atomicAdd(&sh[(uint32_t)(a >> pl.s1) & 0xFF], 1u);
+      atomicAdd(&sh[(uint32_t)(b >> pl.s1) & 0xFF], 1u);
+      atomicAdd(&sh[(uint32_t)(c2 >> pl.s1) & 0xFF], 1u);
+      atomicAdd(&sh[(uint32_t)(d >> pl.s1) & 0xFF], 1u);
+    }
+    for (; i < t.count; i += blockDim.x) atomicAdd(&sh[(uint32_t)(kp[i] >> pl.s1) & 0xFF], 1u);
+    __syncthreads();
+    const uint32_t v = sh[threadIdx.x];
+    if (v) atomicAdd(&hist[(uint64_t)t.seg * kRadix + threadIdx.x], (unsigned long long)v);
+    __syncthreads();
+  }
+}
+
+// One CTA: tile-count prefixes of the kPlanMsd and of the kPlanLsd indexes (the
+// ticket maps of the MSD pass and of the LSD passes / permutation).
+__global__ void __launch_bounds__(1024) k_batch_mode_prefix(const BatchPlan* __restrict__ plan,
+                                                            const uint32_t* __restrict__ tile0,
+                                                            uint32_t nseg,
+                                                            uint32_t* __restrict__ prefix_msd,
+                                                            uint32_t* __restrict__ prefix_lsd) {
+  __shared__ uint32_t warp_tot[2][32];
+  __shared__ uint32_t carry[2];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) carry[0] = carry[1] = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < nseg; base += blockDim.x) {
+    const uint32_t s = base + tid;
+    uint32_t v[2] = {0, 0};
+    if (s < nseg) {
+      const uint32_t nt = tile0[s + 1] - tile0[s];
+      const uint32_t mode = plan[s].mode;
+      v[0] = mode == kPlanMsd ? nt : 0u;
+      v[1] = mode == kPlanLsd ? nt : 0u;
+    }
+    uint32_t x[2] = {v[0], v[1]};
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x[c], o);
+        if (lane >= o) x[c] += y;
+      }
+    }
+    if (lane == 31) {
+      warp_tot[0][w] = x[0];
+      warp_tot[1][w] = x[1];
+    }
+    __syncthreads();
+    uint32_t pre[2] = {carry[0], carry[1]};
+    for (int j = 0; j < w; ++j) {
+      pre[0] += warp_tot[0][j];
+      pre[1] += warp_tot[1][j];
+    }
+    if (s < nseg) {
+      prefix_msd[s] = pre[0] + x[0] - v[0];
+      prefix_lsd[s] = pre[1] + x[1] - v[1];
+    }
+    __syncthreads();
+    if (tid == (int)blockDim.x - 1) {  // the block total carries to the next chunk
+      carry[0] = pre[0] + x[0];
+      carry[1] = pre[1] + x[1];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    prefix_msd[nseg] = carry[0];
+    prefix_lsd[nseg] = carry[1];
+  }
+}
+
+// One CTA per index of plan kPlanMsd: absolute starts of its window buckets, and
+// the fallback to the LSD passes if one of them is larger than cap.
+__global__ void __launch_bounds__(256) k_batch_window_scan(const unsigned long long* __restrict__ hist,
+                                                           unsigned long long* __restrict__ offs,
+                                                           const uint64_t* __restrict__ seg_start,
+                                                           uint32_t cap, BatchPlan* __restrict__ plan) {
+  __shared__ unsigned long long warp_tot[8];
+  const uint32_t i = blockIdx.x;
+  const int d = threadIdx.x, lane = d & 31, w = d >> 5;
+  if (plan[i].mode != kPlanMsd) return;
+  const uint64_t at = (uint64_t)i * kRadix + d;
+  const unsigned long long c = hist[at];
+  unsigned long long x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  unsigned long long base = 0;
+  for (int j = 0; j < w; ++j) base += warp_tot[j];
+  offs[at] = seg_start[i] + base + x - c;
+  if (__syncthreads_or(c > cap) && d == 0) plan[i].mode = kPlanLsd;
 }
 
 // ================================================================= hybrid MSD + bucket sort
@@ -781,11 +1018,17 @@ size_t batch_sort_scratch_bytes(uint64_t ntiles, uint32_t nseg, int key_bytes) {
          align256(sizeof(uint64_t) * kRadix * (ntiles + 1));
 }
 
+size_t batch_hybrid_bytes(uint32_t nseg) {
+  return align256(sizeof(BatchPlan) * nseg) + align256(sizeof(SlotMap) * nseg) +
+         2 * align256(sizeof(uint64_t) * (uint64_t)nseg * kRadix) + 256 +
+         3 * align256(sizeof(uint32_t) * (nseg + 1));
+}
+
 cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], uint32_t* tmp_v[2],
                        uint64_t n, int key_bytes, const uint64_t* seg_start, uint32_t nseg,
                        const BatchTile* tiles, uint64_t ntiles, const BatchTile* chunks,
                        uint64_t nchunks, void* scratch, uint32_t* dflags, cudaStream_t s,
-                       int* result_buf) {
+                       int* result_buf, const BatchHybrid* hy) {
   const int passes = key_bytes;
   char* p = (char*)scratch;
   unsigned long long* hist = (unsigned long long*)p;
@@ -802,27 +1045,64 @@ cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], u
     return cudaSuccess;
   }
   const int hgrid = (int)std::min<uint64_t>(nchunks, (uint64_t)sm_count() * 8);
+  // persistent radix grids: the 4 CTAs per SM the pass fits
+  const unsigned pgrid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count() * 4);
   if (key_bytes == 4)
     k_batch_histogram<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)keys, vals, chunks, nchunks, hist, dflags);
   else
     k_batch_histogram<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)keys, vals, chunks, nchunks, hist, dflags);
   k_batch_scan_hist<<<nseg, 256, 0, s>>>(hist, offs, seg_start, passes);
   count_launch(2);
+  const BatchPlan* plan = nullptr;
+  if (hy) {
+    // per-index plans, the MSD window counts, the MSD scatter into tmp[1] and the
+    // bucket sort, which writes the layouts of those indexes
+    plan = hy->plan;
+    const uint32_t cap = local_sort_capacity();
+    e = cudaMemsetAsync(hy->hist_w, 0, sizeof(uint64_t) * (uint64_t)nseg * kRadix, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hy->counter, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_batch_plan<<<nseg, 256, 0, s>>>(hist, seg_start, key_bytes, hy->k, cap, hy->plan, hy->slot_maps);
+    if (key_bytes == 4)
+      k_batch_window_hist<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)keys, chunks, nchunks, hy->plan, hy->hist_w);
+    else
+      k_batch_window_hist<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)keys, chunks, nchunks, hy->plan, hy->hist_w);
+    k_batch_window_scan<<<nseg, 256, 0, s>>>(hy->hist_w, hy->offs_w, seg_start, cap, hy->plan);
+    k_batch_mode_prefix<<<1, 1024, 0, s>>>(hy->plan, hy->tile0, nseg, hy->prefix_msd, hy->prefix_lsd);
+    count_launch(4);
+    // persistent grid over the tiles of the kPlanMsd indexes only; the status
+    // array is shared with the LSD passes: a distinct epoch (9)
+    const TileMap msd_map{hy->prefix_msd, hy->tile0, nseg};
+    if (key_bytes == 4)
+      k_batch_sort_pass<uint32_t><<<pgrid, kSortThreads, 0, s>>>(
+          (const uint32_t*)keys, vals, (uint32_t*)tmp_k[1], tmp_v[1], n, 0u, tiles, hy->offs_w, 0,
+          1, status, hy->counter, 9u, dflags, hy->plan, kPlanMsd, 1u, msd_map);
+    else
+      k_batch_sort_pass<uint64_t><<<pgrid, kSortThreads, 0, s>>>(
+          (const uint64_t*)keys, vals, (uint64_t*)tmp_k[1], tmp_v[1], n, 0u, tiles, hy->offs_w, 0,
+          1, status, hy->counter, 9u, dflags, hy->plan, kPlanMsd, 1u, msd_map);
+    count_launch();
+    e = batch_local_sort(keys, vals, tmp_k[1], tmp_v[1], seg_start, nseg, key_bytes, *hy, dflags, s);
+    if (e != cudaSuccess) return e;
+  }
   // every pass runs (no host round trip to skip trivial digits, so the whole
-  // build can be captured in a graph)
+  // build can be captured in a graph); with a plan, only for kPlanLsd indexes,
+  // on a persistent grid over their tiles (usually none)
+  const TileMap lsd_map = hy ? TileMap{hy->prefix_lsd, hy->tile0, nseg} : TileMap{};
+  const unsigned grid = hy ? pgrid : (unsigned)ntiles;
   const void* ck = keys;
   const uint32_t* cv = vals;
   int cur = -1;
   for (int ps = 0; ps < passes; ++ps) {
     const int dst = cur == 0 ? 1 : 0;
     if (key_bytes == 4)
-      k_batch_sort_pass<uint32_t><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
+      k_batch_sort_pass<uint32_t><<<grid, kSortThreads, 0, s>>>(
           (const uint32_t*)ck, cv, (uint32_t*)tmp_k[dst], tmp_v[dst], n, 8u * ps, tiles, offs, ps,
-          passes, status, counter + ps, (uint32_t)ps + 1, dflags);
+          passes, status, counter + ps, (uint32_t)ps + 1, dflags, plan, kPlanLsd, 0u, lsd_map);
     else
-      k_batch_sort_pass<uint64_t><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
+      k_batch_sort_pass<uint64_t><<<grid, kSortThreads, 0, s>>>(
           (const uint64_t*)ck, cv, (uint64_t*)tmp_k[dst], tmp_v[dst], n, 8u * ps, tiles, offs, ps,
-          passes, status, counter + ps, (uint32_t)ps + 1, dflags);
+          passes, status, counter + ps, (uint32_t)ps + 1, dflags, plan, kPlanLsd, 0u, lsd_map);
     count_launch();
     ck = tmp_k[dst];
     cv = tmp_v[dst];
@@ -836,11 +1116,11 @@ template <class K>
 static void launch_batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t* ov,
                                 const BatchTile* tiles, uint64_t ntiles, const uint64_t* seg_start,
                                 const uint64_t* seg_base, uint32_t k, uint32_t* dflags,
-                                cudaStream_t s) {
+                                cudaStream_t s, const BatchPlan* plan, TileMap map) {
   const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)sm_count() * 16);
   const K* a = (const K*)sk;
   K* b = (K*)ok;
-#define GI_BG(KF) k_batch_gather<K, KF><<<grid, 256, 0, s>>>(a, sv, b, ov, tiles, ntiles, seg_start, seg_base, k, dflags)
+#define GI_BG(KF) k_batch_gather<K, KF><<<grid, 256, 0, s>>>(a, sv, b, ov, tiles, ntiles, seg_start, seg_base, k, dflags, plan, map)
   switch (k) {
     case 0: GI_BG(1); break;  // sorted order: rank == slot
     case 2: GI_BG(2); break;
@@ -857,12 +1137,14 @@ static void launch_batch_gather(const void* sk, const uint32_t* sv, void* ok, ui
 cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t* ov,
                          const BatchTile* tiles, uint64_t ntiles, const uint64_t* seg_start,
                          const uint64_t* seg_base, uint32_t k, int key_bytes, uint32_t* dflags,
-                         cudaStream_t s) {
+                         cudaStream_t s, const BatchHybrid* hy, uint32_t nseg) {
   if (ntiles == 0) return cudaSuccess;
+  const BatchPlan* plan = hy ? hy->plan : nullptr;
+  const TileMap map = hy ? TileMap{hy->prefix_lsd, hy->tile0, nseg} : TileMap{};
   if (key_bytes == 4)
-    launch_batch_gather<uint32_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s);
+    launch_batch_gather<uint32_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s, plan, map);
   else
-    launch_batch_gather<uint64_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s);
+    launch_batch_gather<uint64_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s, plan, map);
   return cudaGetLastError();
 }
 
@@ -989,11 +1271,11 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
     if (key_bytes == 4)
       k_batch_sort_pass<uint32_t><<<(unsigned)tiles.size(), kSortThreads, 0, s>>>(
           (const uint32_t*)bk[cur], bv[cur], (uint32_t*)bk[dst2], bv[dst2], n, 8u * d2, d_tiles,
-          d_offs, 0, 1, v.status, d_counter, 40u, dflags);
+          d_offs, 0, 1, v.status, d_counter, 40u, dflags, nullptr, 0u, 0u, TileMap{});
     else
       k_batch_sort_pass<uint64_t><<<(unsigned)tiles.size(), kSortThreads, 0, s>>>(
           (const uint64_t*)bk[cur], bv[cur], (uint64_t*)bk[dst2], bv[dst2], n, 8u * d2, d_tiles,
-          d_offs, 0, 1, v.status, d_counter, 40u, dflags);
+          d_offs, 0, 1, v.status, d_counter, 40u, dflags, nullptr, 0u, 0u, TileMap{});
     count_launch();
     cur = dst2;
     cudaFreeAsync(blob, s);

@@ -182,3 +182,38 @@ def test_batched_workload_shape_sampled():
     _check(batch, keys, rows, qs, qoff, out, gi.GI_EYTZINGER_KARY, 5, check_layout=True, which=which)
     assert gi.gi_batch_footprint_bytes(batch) == int(off[-1]) * 12
     gi.gi_batch_destroy(batch)
+
+
+@pytest.mark.parametrize("bits", [64, 32])
+@pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER_KARY, 5), (gi.GI_SORTED, 0), (gi.GI_EYTZINGER_KARY, 17)])
+def test_batch_build_plans_every_path(bits, layout, k):
+    # the build sorts each index by a plan chosen on the device from its digit
+    # histograms: whole index in one CTA (<= 4096 pairs), one MSD scatter on its 8
+    # highest significant bits + bucket sort, or the LSD passes when a bucket would
+    # exceed 4096 pairs.  One batch holds every case: tiny, uniform, skewed (almost
+    # all keys in one MSD bucket), all keys equal, heavy duplicates, narrow ranges.
+    dt = np.uint64 if bits == 64 else np.uint32
+    top = np.iinfo(dt).max
+    rng = np.random.default_rng(bits + k)
+    keys = [
+        W.unique_keys(4000, bits, 1),                                        # whole
+        W.unique_keys(60000, bits, 2),                                       # MSD
+        np.concatenate([np.arange(9000, dtype=dt), np.array([top], dt)]),    # skewed: LSD
+        np.full(6000, 12345, dt),                                            # all equal: LSD
+        W.duplicate_keys(1500, 8, bits, 3)[:12000].astype(dt),               # duplicates: MSD
+        rng.integers(0, 1 << 10, size=20000).astype(dt),                     # narrow: MSD on low bits
+        np.zeros(0, dt), np.array([7], dt), W.unique_keys(4097, bits, 4),    # empty, one, just above
+        W.unique_keys(100000, bits, 5),
+    ]
+    rows = [rng.permutation(len(x)).astype(np.uint32) for x in keys]
+    off = np.zeros(len(keys) + 1, dtype=np.uint64)
+    np.cumsum(np.array([len(x) for x in keys], dtype=np.uint64), out=off[1:])
+    qs, qoff = _probes(keys, bits, [3000] * len(keys), 17)
+    flag = gi.GI_KEY_U64 if bits == 64 else gi.GI_KEY_U32
+    batch = gi.gi_batch_create(off, layout | flag, k)
+    gi.gi_batch_build(batch, to_dev(np.concatenate(keys)), to_dev(np.concatenate(rows)))
+    out = torch.full((int(qoff[-1]),), -5, dtype=torch.int32, device=DEV)
+    gi.gi_batch_point_lookup(batch, to_dev(np.concatenate(qs)), to_dev(qoff), out)
+    gi.gi_batch_sync(batch)
+    _check(batch, keys, rows, qs, qoff, out, layout, k)
+    gi.gi_batch_destroy(batch)

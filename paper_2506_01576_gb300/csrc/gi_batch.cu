@@ -398,7 +398,7 @@ int gi_batch_create(const uint64_t* key_offsets, uint32_t B, int layout, uint32_
   GI_B(cudaMalloc((void**)&b->dflags, 256), "batch status");
   GI_B(cudaMemset(b->dflags, 0, 256), "batch status");
   {  // tables of the hybrid build: per-index plans and slot maps, MSD window counts
-    GI_B(cudaMalloc(&b->hy_mem, gi::batch_hybrid_bytes(B)), "batch tables");
+    GI_B(cudaMalloc(&b->hy_mem, gi::batch_hybrid_bytes(B, b->ntiles)), "batch tables");
     char* q = (char*)b->hy_mem;
     auto take = [&](size_t bytes) { char* r = q; q += (bytes + 255) & ~size_t(255); return r; };
     b->hy.plan = (gi::BatchPlan*)take(sizeof(gi::BatchPlan) * B);
@@ -410,6 +410,8 @@ int gi_batch_create(const uint64_t* key_offsets, uint32_t B, int layout, uint32_
     b->hy.tile0 = d_tile0;
     b->hy.prefix_msd = (uint32_t*)take(sizeof(uint32_t) * (B + 1));
     b->hy.prefix_lsd = (uint32_t*)take(sizeof(uint32_t) * (B + 1));
+    b->hy.list_msd = (uint32_t*)take(sizeof(uint32_t) * (b->ntiles + 1));
+    b->hy.list_lsd = (uint32_t*)take(sizeof(uint32_t) * (b->ntiles + 1));
     GI_B(cudaMemcpy(d_tile0, tile0.data(), sizeof(uint32_t) * (B + 1), cudaMemcpyHostToDevice), "batch tables");
     b->hy.out_k = b->keys;
     b->hy.out_v = b->rows;

@@ -252,9 +252,11 @@ struct BatchHybrid {
   const uint32_t* tile0;        // [nseg + 1] first radix tile of every index
   uint32_t* prefix_msd;         // [nseg + 1] tiles of the kPlanMsd indexes before index s
   uint32_t* prefix_lsd;         // [nseg + 1] same for kPlanLsd
+  uint32_t* list_msd;           // [ntiles] tiles of the kPlanMsd indexes, in order
+  uint32_t* list_lsd;           // [ntiles] tiles of the kPlanLsd indexes, in order
   uint32_t k;                   // fan-out; 0 = sorted layout
 };
-size_t batch_hybrid_bytes(uint32_t nseg);  // device bytes of the tables
+size_t batch_hybrid_bytes(uint32_t nseg, uint64_t ntiles);  // device bytes of the tables
 // hist/offsets/status/counters live in `scratch` (batch_sort_scratch_bytes); no host
 // sync.  hy != NULL: indexes are sorted per their plan (whole / MSD + buckets, written
 // straight into hy->out_k / out_v), and only kPlanLsd indexes take the LSD passes

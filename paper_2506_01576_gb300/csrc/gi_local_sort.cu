@@ -33,17 +33,19 @@ namespace {
 
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
-constexpr int kThreads = 256;  // == kRadix: thread d owns digit d in the scans
-constexpr int kWarps = kThreads / 32;
+// CTA widths: 256 threads (thread d owns digit d in the scans) or 512 (the second
+// half only ranks and moves keys) for the largest buckets.
+constexpr uint32_t kCapacity = 5120;  // pairs per bucket: 512 threads x 10
 
+template <int T>
 struct LocalSmem {
   template <class K>
   static size_t bytes(int items) {
-    const size_t tile = (size_t)kThreads * items;
-    return tile * sizeof(K) + tile * 4 +            // keys, rowIDs
-           sizeof(uint32_t) * kRadix * kWarps +     // per-warp digit counts
-           sizeof(uint32_t) * (2 * kRadix + kWarps) +  // sub-bucket starts / ends, warp totals
-           sizeof(uint16_t) * tile;                 // sorted position -> current position
+    const size_t tile = (size_t)T * items;
+    return tile * sizeof(K) + tile * 4 +              // keys, rowIDs
+           sizeof(uint32_t) * kRadix * (T / 32) +     // per-warp digit counts
+           sizeof(uint32_t) * (2 * kRadix + T / 32) +  // sub-bucket starts / ends, warp totals
+           sizeof(uint16_t) * tile;                   // sorted position -> current position
   }
 };
 
@@ -51,10 +53,11 @@ struct LocalSmem {
 // Warp w holds the contiguous run [w * 32 * items, (w + 1) * 32 * items), so the
 // order inside a warp (item-major, then lane) and across warps is the input order.
 // On return s_start[d] is the first position of digit d.
-template <class K, int ITEMS>
+template <class K, int ITEMS, int T>
 __device__ __forceinline__ void digit_pass(K* s_k, uint32_t* s_v, uint32_t (*h)[kRadix],
                                            uint32_t* s_start, uint32_t* s_wt, uint32_t items,
                                            uint32_t shift) {
+  constexpr int W = T / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const uint32_t wofs = (uint32_t)warp * 32 * items + lane;
@@ -87,34 +90,37 @@ __device__ __forceinline__ void digit_pass(K* s_k, uint32_t* s_v, uint32_t (*h)[
     }
   }
   __syncthreads();
-  {  // thread d: digit d's count over warps, then a block scan over digits
-    const uint32_t d = tid;
-    uint32_t cnt = 0;
+  // threads d < 256: digit d's count over warps, then a scan over digits
+  const uint32_t d = tid;
+  uint32_t cnt = 0, x = 0;
+  if (tid < kRadix) {
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < W; ++w) {
       const uint32_t c = h[w][d];
       h[w][d] = cnt;
       cnt += c;
     }
-    uint32_t x = cnt;
+    x = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) s_wt[warp] = x;
-    __syncthreads();
+  }
+  __syncthreads();
+  if (tid < kRadix) {
     uint32_t wpre = 0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) wpre += (w < warp) ? s_wt[w] : 0u;
+    for (int w = 0; w < kRadix / 32; ++w) wpre += (w < warp) ? s_wt[w] : 0u;
     s_start[d] = wpre + x - cnt;
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     if (i < (int)items) {
-      const uint32_t d = (uint32_t)(key[i] >> shift) & 0xFF;
-      const uint32_t pos = s_start[d] + h[warp][d] + rnk[i];
+      const uint32_t dd = (uint32_t)(key[i] >> shift) & 0xFF;
+      const uint32_t pos = s_start[dd] + h[warp][dd] + rnk[i];
       s_k[pos] = key[i];
       s_v[pos] = val[i];
     }
@@ -123,9 +129,9 @@ __device__ __forceinline__ void digit_pass(K* s_k, uint32_t* s_v, uint32_t (*h)[
 }
 
 // Shared-memory views of one CTA's bucket (dynamic shared memory, LocalSmem::bytes).
-template <class K, int ITEMS>
+template <class K, int ITEMS, int T>
 struct BucketSmem {
-  static constexpr int TILE = kThreads * ITEMS;
+  static constexpr int TILE = T * ITEMS;
   K* s_k;
   uint32_t* s_v;
   uint32_t (*h)[kRadix];  // [warps][256]
@@ -137,29 +143,29 @@ struct BucketSmem {
     s_k = (K*)raw;
     s_v = (uint32_t*)(s_k + TILE);
     h = (uint32_t (*)[kRadix])(s_v + TILE);
-    s_start = (uint32_t*)(h + kWarps);
+    s_start = (uint32_t*)(h + T / 32);
     s_end = s_start + kRadix;
     s_wt = s_end + kRadix;
-    s_src = (uint16_t*)(s_wt + kWarps);
+    s_src = (uint16_t*)(s_wt + T / 32);
   }
 };
 
-// Sorts the `count` pairs at src + start (count <= kThreads * ITEMS) in shared
-// memory.  top_shift: the window (8 bits at that shift) that splits the bucket
-// into sub-buckets for count ranking; lsd_mask: the bytes that may differ inside
-// the bucket, sorted one ballot pass each (LSD order) when a sub-bucket is larger
-// than `limit`; single: the top window alone orders the bucket.  Returns true if
-// s_k / s_v end in sorted order, false if s_src holds it.  Block-uniform.
-template <class K, int ITEMS>
-__device__ __forceinline__ bool sort_bucket(const BucketSmem<K, ITEMS>& m,
+// Sorts the `count` pairs at src + start (count <= T * ITEMS) in shared memory.
+// top_shift: the window (8 bits at that shift) that splits the bucket into
+// sub-buckets for count ranking; lsd_mask: the bytes that may differ inside the
+// bucket, sorted one ballot pass each (LSD order) when a sub-bucket is larger than
+// `limit`; single: the top window alone orders the bucket.  Returns true if s_k /
+// s_v end in sorted order, false if s_src holds it.  Block-uniform.
+template <class K, int ITEMS, int T>
+__device__ __forceinline__ bool sort_bucket(const BucketSmem<K, ITEMS, T>& m,
                                             const K* __restrict__ src_k,
                                             const uint32_t* __restrict__ src_v, uint64_t start,
                                             uint32_t count, uint32_t top_shift, uint32_t lsd_mask,
                                             bool single, uint32_t limit) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t items = (count + kThreads - 1) / kThreads;  // <= ITEMS
-  const uint32_t used = items * kThreads;
-  for (uint32_t j = tid; j < used; j += kThreads) {
+  const uint32_t items = (count + T - 1) / T;  // <= ITEMS
+  const uint32_t used = items * T;
+  for (uint32_t j = tid; j < used; j += T) {
     const bool in = j < count;
     m.s_k[j] = in ? src_k[start + j] : ~K(0);  // padding sorts last, stably
     m.s_v[j] = in ? src_v[start + j] : 0u;
@@ -167,24 +173,26 @@ __device__ __forceinline__ bool sort_bucket(const BucketSmem<K, ITEMS>& m,
   __syncthreads();
   // the top window first; if a sub-bucket is too big for count ranking, every
   // byte of lsd_mask again in LSD order (one pass loop keeps one copy of the
-  // pass's code and its registers).  The top pass then sorts on top_shift with
-  // todo's bit standing for it.
+  // pass's code and its registers)
   bool first = lsd_mask != 0, direct = single || lsd_mask == 0;
   uint32_t todo = first ? 1u : 0u;
   while (todo) {
     const uint32_t shift = first ? top_shift : 8u * (uint32_t)(__ffs(todo) - 1);
     todo &= todo - 1;
-    digit_pass<K, ITEMS>(m.s_k, m.s_v, m.h, m.s_start, m.s_wt, items, shift);
+    digit_pass<K, ITEMS, T>(m.s_k, m.s_v, m.h, m.s_start, m.s_wt, items, shift);
     if (first) {
       first = false;
       if (!single) {
         // sub-bucket d covers [s_start[d], s_end[d]) of real keys (padding sits
         // after count: it has the largest window value and came last)
-        const uint32_t st = m.s_start[tid];
-        const uint32_t en = tid < kRadix - 1 ? m.s_start[tid + 1] : used;
-        const uint32_t en_real = en < count ? en : count;
-        m.s_end[tid] = en_real;
-        const bool big = (en_real > st ? en_real - st : 0u) > limit;
+        bool big = false;
+        if (tid < kRadix) {
+          const uint32_t st = m.s_start[tid];
+          const uint32_t en = tid < kRadix - 1 ? m.s_start[tid + 1] : used;
+          const uint32_t en_real = en < count ? en : count;
+          m.s_end[tid] = en_real;
+          big = (en_real > st ? en_real - st : 0u) > limit;
+        }
         if (__syncthreads_or(big)) {
           todo = lsd_mask;
           direct = true;
@@ -216,23 +224,23 @@ __device__ __forceinline__ bool sort_bucket(const BucketSmem<K, ITEMS>& m,
 
 // KF: 1 = sorted layout (slot = rank); >= 2 = k-ary Eytzinger with that fan-out
 // (2 = Eytzinger); 0 = k-ary with the fan-out read at run time.
-template <class K, int ITEMS, int MINB, int KF>
-__global__ void __launch_bounds__(kThreads, MINB) k_local_sort(
+template <class K, int ITEMS, int T, int MINB, int KF>
+__global__ void __launch_bounds__(T, MINB) k_local_sort(
     const K* __restrict__ src_k, const uint32_t* __restrict__ src_v, K* __restrict__ dst_k,
     uint32_t* __restrict__ dst_v, const BatchTile* __restrict__ segs, uint64_t nseg,
     uint32_t local_mask, uint32_t limit, SlotMap sm, uint32_t key_off, uint32_t* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const BucketSmem<K, ITEMS> m(smem_raw);
+  const BucketSmem<K, ITEMS, T> m(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t top = local_mask ? 31u - (uint32_t)__clz(local_mask) : 0u;
   const bool single = __popc(local_mask) <= 1;  // the top pass alone sorts the bucket
   bool dup = false;
   for (uint64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
     const BatchTile seg = segs[sg];
-    const bool direct = sort_bucket<K, ITEMS>(m, src_k, src_v, seg.start, seg.count, 8u * top,
-                                              local_mask, single, limit);
+    const bool direct = sort_bucket<K, ITEMS, T>(m, src_k, src_v, seg.start, seg.count, 8u * top,
+                                                 local_mask, single, limit);
     // sorted position j -> rank seg.start + j -> its slot in the layout
-    for (uint32_t j = tid; j < seg.count; j += kThreads) {
+    for (uint32_t j = tid; j < seg.count; j += T) {
       const uint32_t p = direct ? j : m.s_src[j];
       const K key = m.s_k[p];
       if (j > 0) dup |= m.s_k[direct ? j - 1 : m.s_src[j - 1]] == key;
@@ -253,8 +261,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_local_sort(
 // pass); id >= nseg * 256 is the whole index id - nseg * 256 (plan kPlanWhole,
 // pairs still in the input).  A launch takes the buckets of (lo_count, hi_count]
 // pairs.  Each writes its index's layout at out + seg_base[i].
-template <class K, int ITEMS, int MINB, int KF>
-__global__ void __launch_bounds__(kThreads, MINB) k_batch_local_sort(
+template <class K, int ITEMS, int T, int MINB, int KF>
+__global__ void __launch_bounds__(T, MINB) k_batch_local_sort(
     const K* __restrict__ keys, const uint32_t* __restrict__ vals, const K* __restrict__ src_k,
     const uint32_t* __restrict__ src_v, const uint64_t* __restrict__ seg_start, uint32_t nseg,
     const BatchPlan* __restrict__ plan, const SlotMap* __restrict__ maps,
@@ -262,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_batch_local_sort(
     K* __restrict__ out_k, uint32_t* __restrict__ out_v, const uint64_t* __restrict__ seg_base,
     uint32_t lo_count, uint32_t hi_count, uint32_t* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const BucketSmem<K, ITEMS> m(smem_raw);
+  const BucketSmem<K, ITEMS, T> m(smem_raw);
   __shared__ SlotMap s_map;
   const int tid = threadIdx.x, lane = tid & 31;
   bool dup = false;
@@ -280,11 +288,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_batch_local_sort(
       if (tid < (int)(sizeof(SlotMap) / 4)) ((uint32_t*)&s_map)[tid] = ((const uint32_t*)&maps[i])[tid];
     }
     const uint32_t limit = 8u * (uint32_t)__popc(pl.lsd_mask) + 8u;
-    const bool direct = sort_bucket<K, ITEMS>(m, msd ? src_k : keys, msd ? src_v : vals, start,
-                                              count, pl.ts, pl.lsd_mask, false, limit);
+    const bool direct = sort_bucket<K, ITEMS, T>(m, msd ? src_k : keys, msd ? src_v : vals, start,
+                                                 count, pl.ts, pl.lsd_mask, false, limit);
     const uint64_t base = seg_base[i];
     const uint32_t r0 = (uint32_t)(start - s0);
-    for (uint32_t j = tid; j < count; j += kThreads) {
+    for (uint32_t j = tid; j < count; j += T) {
       const uint32_t p = direct ? j : m.s_src[j];
       const K key = m.s_k[p];
       if (j > 0) dup |= m.s_k[direct ? j - 1 : m.s_src[j - 1]] == key;
@@ -299,26 +307,29 @@ __global__ void __launch_bounds__(kThreads, MINB) k_batch_local_sort(
   if (__any_sync(0xffffffffu, dup) && lane == 0) atomicOr(flags, kFlagDuplicate);
 }
 
+// Size classes of the bucket sort: up to 3072 pairs (256 threads x 12, 3 CTAs per
+// SM), up to 4096 (256 x 16, 2 per SM), up to 5120 (512 x 10, 2 per SM).
+#define GI_LOCAL_CLASSES(X) X(12, 256, 3, 0u, 3072u) X(16, 256, 2, 3072u, 4096u) X(10, 512, 2, 4096u, 5120u)
+
 template <class K, int KF>
 cudaError_t launch(const K* sk, const uint32_t* sv, K* dk, uint32_t* dv, const BatchTile* segs,
                    uint64_t nseg, uint64_t max_count, uint32_t mask, uint32_t limit,
                    const SlotMap& sm, uint32_t key_off, uint32_t* dflags, cudaStream_t s) {
-#define GI_LS(IT, MB)                                                                          \
-  do {                                                                                         \
-    auto kern = k_local_sort<K, IT, MB, KF>;                                                   \
-    const size_t smem = LocalSmem::bytes<K>(IT);                                               \
+  bool done = false;
+#define GI_LS(IT, T, MB, LO, HI)                                                               \
+  if (!done && max_count <= HI) {                                                              \
+    auto kern = k_local_sort<K, IT, T, MB, KF>;                                                \
+    const size_t smem = LocalSmem<T>::template bytes<K>(IT);                                   \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                          (int)smem);                                           \
     if (e != cudaSuccess) return e;                                                            \
     const unsigned grid = (unsigned)std::min<uint64_t>(nseg, (uint64_t)sm_count() * MB * 4);   \
-    kern<<<grid, kThreads, smem, s>>>(sk, sv, dk, dv, segs, nseg, mask, limit, sm, key_off,    \
-                                      dflags);                                                 \
-  } while (0)
-  if (max_count <= (uint64_t)kThreads * 12)
-    GI_LS(12, 3);
-  else
-    GI_LS(16, 2);
+    kern<<<grid, T, smem, s>>>(sk, sv, dk, dv, segs, nseg, mask, limit, sm, key_off, dflags);  \
+    done = true;                                                                               \
+  }
+  GI_LOCAL_CLASSES(GI_LS)
 #undef GI_LS
+  if (!done) return cudaErrorInvalidValue;
   count_launch();
   return cudaGetLastError();
 }
@@ -344,9 +355,52 @@ cudaError_t launch_kf(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv
 #undef GI_L
 }
 
+// setup: only raise the kernels' dynamic shared-memory limit (done when the batch
+// is created, so that builds launch kernels only and can be captured in a graph)
+template <class K, int KF>
+cudaError_t launch_batch(const void* keys, const uint32_t* vals, const void* src_k,
+                         const uint32_t* src_v, const uint64_t* seg_start, uint32_t nseg,
+                         const BatchHybrid& hy, uint32_t* dflags, cudaStream_t s, bool setup) {
+#define GI_BLS(IT, T, MB, LO, HI)                                                              \
+  {                                                                                            \
+    auto kern = k_batch_local_sort<K, IT, T, MB, KF>;                                          \
+    const size_t smem = LocalSmem<T>::template bytes<K>(IT);                                   \
+    if (setup) {                                                                               \
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                           (int)smem);                                         \
+      if (e != cudaSuccess) return e;                                                          \
+    } else {                                                                                   \
+      const unsigned grid = (unsigned)sm_count() * MB * 4;                                     \
+      kern<<<grid, T, smem, s>>>((const K*)keys, vals, (const K*)src_k, src_v, seg_start, nseg, \
+                                 hy.plan, hy.slot_maps, hy.hist_w, hy.offs_w, (K*)hy.out_k,    \
+                                 hy.out_v, hy.seg_base, LO, HI, dflags);                       \
+      count_launch();                                                                          \
+    }                                                                                          \
+  }
+  GI_LOCAL_CLASSES(GI_BLS)
+#undef GI_BLS
+  return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_batch_kf(const void* keys, const uint32_t* vals, const void* src_k,
+                            const uint32_t* src_v, const uint64_t* seg_start, uint32_t nseg,
+                            const BatchHybrid& hy, uint32_t* dflags, cudaStream_t s, bool setup) {
+#define GI_B(KF) launch_batch<K, KF>(keys, vals, src_k, src_v, seg_start, nseg, hy, dflags, s, setup)
+  switch (hy.k) {
+    case 0: return GI_B(1);
+    case 3: return GI_B(3);
+    case 5: return GI_B(5);
+    case 9: return GI_B(9);
+    case 17: return GI_B(17);
+    default: return cudaErrorInvalidValue;  // the batch takes k = 3, 5, 9, 17 only
+  }
+#undef GI_B
+}
+
 }  // namespace
 
-uint32_t local_sort_capacity() { return kThreads * 16; }
+uint32_t local_sort_capacity() { return kCapacity; }
 
 cudaError_t local_sort(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
                        const BatchTile* segs, uint64_t nseg, uint64_t max_count,
@@ -363,55 +417,6 @@ cudaError_t local_sort(const void* sk, const uint32_t* sv, void* dk, uint32_t* d
   return launch_kf<uint64_t>(sk, sv, dk, dv, segs, nseg, max_count, local_mask, limit, g,
                              sorted_layout, key_off, dflags, s);
 }
-
-namespace {
-
-// setup: only raise the kernels' dynamic shared-memory limit (done when the batch
-// is created, so that builds launch kernels only and can be captured in a graph)
-template <class K, int KF>
-cudaError_t launch_batch(const void* keys, const uint32_t* vals, const void* src_k,
-                         const uint32_t* src_v, const uint64_t* seg_start, uint32_t nseg,
-                         const BatchHybrid& hy, uint32_t* dflags, cudaStream_t s, bool setup) {
-#define GI_BLS(IT, MB, LO, HI)                                                                 \
-  do {                                                                                         \
-    auto kern = k_batch_local_sort<K, IT, MB, KF>;                                             \
-    const size_t smem = LocalSmem::bytes<K>(IT);                                               \
-    if (setup) {                                                                               \
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                           (int)smem);                                         \
-      if (e != cudaSuccess) return e;                                                          \
-      break;                                                                                   \
-    }                                                                                          \
-    const unsigned grid = (unsigned)sm_count() * MB * 4;                                       \
-    kern<<<grid, kThreads, smem, s>>>((const K*)keys, vals, (const K*)src_k, src_v, seg_start, \
-                                      nseg, hy.plan, hy.slot_maps, hy.hist_w, hy.offs_w,       \
-                                      (K*)hy.out_k, hy.out_v, hy.seg_base, LO, HI, dflags);    \
-    count_launch();                                                                            \
-  } while (0)
-  // two size classes: up to 12 pairs per thread (3 CTAs per SM), then up to 16
-  GI_BLS(12, 3, 0u, kThreads * 12u);
-  GI_BLS(16, 2, kThreads * 12u, kThreads * 16u);
-#undef GI_BLS
-  return cudaGetLastError();
-}
-
-template <class K>
-cudaError_t launch_batch_kf(const void* keys, const uint32_t* vals, const void* src_k,
-                            const uint32_t* src_v, const uint64_t* seg_start, uint32_t nseg,
-                            const BatchHybrid& hy, uint32_t* dflags, cudaStream_t s, bool setup) {
-#define GI_B(KF) launch_batch<K, KF>(keys, vals, src_k, src_v, seg_start, nseg, hy, dflags, s, setup)
-  switch (hy.k) {
-    case 0: return GI_B(1);
-    case 3: return GI_B(3);
-    case 5: return GI_B(5);
-    case 9: return GI_B(9);
-    case 17: return GI_B(17);
-    default: return GI_B(0);
-  }
-#undef GI_B
-}
-
-}  // namespace
 
 cudaError_t batch_local_sort(const void* keys, const uint32_t* vals, const void* src_k,
                              const uint32_t* src_v, const uint64_t* seg_start, uint32_t nseg,

@@ -51,13 +51,12 @@ constexpr uint64_t kStatAggregate = 1ull << 62;
 constexpr uint64_t kStatInclusive = 2ull << 62;
 constexpr uint64_t kValueMask = (1ull << 40) - 1;
 
-// Tickets -> tiles of a subset of a batch's indexes: ticket t is tile
-// tile0[s] + t - prefix[s] of the index s with prefix[s] <= t < prefix[s + 1]
-// (prefix counts only the listed indexes' tiles).  prefix == NULL: tile = ticket.
+// Tickets -> tiles of a subset of a batch's indexes: ticket t < *count is tile
+// list[t] (the listed indexes' tiles in index order, written on the device).
+// list == NULL: tile = ticket.
 struct TileMap {
-  const uint32_t* prefix;
-  const uint32_t* tile0;
-  uint32_t nseg;
+  const uint32_t* list;
+  const uint32_t* count;
 };
 
 __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p) {
@@ -511,20 +510,15 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_batch_sort_pass(
   __syncthreads();
   const uint32_t ticket = s_tile;
   uint64_t tile = ticket;
-  if (map.prefix) {
-    if (ticket >= map.prefix[map.nseg]) return;
-    uint32_t lo = 0, hi = map.nseg;  // prefix[lo] <= ticket < prefix[hi]
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (map.prefix[mid] <= ticket) lo = mid; else hi = mid;
-    }
-    tile = map.tile0[lo] + (ticket - map.prefix[lo]);
+  if (map.list) {
+    if (ticket >= *map.count) return;
+    tile = map.list[ticket];
   }
   const BatchTile desc = tiles[tile];
   // with a plan, only the indexes sorted this way take part (a whole index is
   // skipped, so no tile of it is ever waited for)
   if (plan && plan[desc.seg].mode != want) {
-    if (!map.prefix) return;
+    if (!map.list) return;
     __syncthreads();
     continue;
   }
@@ -640,7 +634,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_batch_sort_pass(
       }
     }
   }
-  if (!map.prefix) return;
+  if (!map.list) return;
   __syncthreads();  // shared memory is reused by the next ticket
   }
 }
@@ -658,18 +652,9 @@ __global__ void __launch_bounds__(256) k_batch_gather(const K* __restrict__ sk,
                                                       const BatchPlan* __restrict__ plan,
                                                       TileMap map) {
   bool dup = false;
-  const uint64_t total = map.prefix ? map.prefix[map.nseg] : ntiles;
+  const uint64_t total = map.list ? *map.count : ntiles;
   for (uint64_t ti = blockIdx.x; ti < total; ti += gridDim.x) {
-    uint64_t tix = ti;
-    if (map.prefix) {  // the ti-th tile of the listed indexes
-      uint32_t lo = 0, hi = map.nseg;
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (map.prefix[mid] <= ti) lo = mid; else hi = mid;
-      }
-      tix = map.tile0[lo] + (ti - map.prefix[lo]);
-    }
-    const BatchTile t = tiles[tix];
+    const BatchTile t = tiles[map.list ? map.list[ti] : ti];
     if (plan && plan[t.seg].mode != kPlanLsd) continue;
     const uint64_t s0 = seg_start[t.seg];
     const uint64_t n = seg_start[t.seg + 1] - s0;
@@ -831,6 +816,21 @@ __global__ void __launch_bounds__(1024) k_batch_mode_prefix(const BatchPlan* __r
     prefix_msd[nseg] = carry[0];
     prefix_lsd[nseg] = carry[1];
   }
+}
+
+// One CTA per index: its tiles into the ticket list of its plan (MSD or LSD).
+__global__ void __launch_bounds__(256) k_batch_mode_lists(const BatchPlan* __restrict__ plan,
+                                                          const uint32_t* __restrict__ tile0,
+                                                          const uint32_t* __restrict__ prefix_msd,
+                                                          const uint32_t* __restrict__ prefix_lsd,
+                                                          uint32_t* __restrict__ list_msd,
+                                                          uint32_t* __restrict__ list_lsd) {
+  const uint32_t s = blockIdx.x;
+  const uint32_t mode = plan[s].mode;
+  if (mode != kPlanMsd && mode != kPlanLsd) return;
+  uint32_t* out = mode == kPlanMsd ? list_msd + prefix_msd[s] : list_lsd + prefix_lsd[s];
+  const uint32_t t0 = tile0[s], nt = tile0[s + 1] - t0;
+  for (uint32_t j = threadIdx.x; j < nt; j += blockDim.x) out[j] = t0 + j;
 }
 
 // One CTA per index of plan kPlanMsd: absolute starts of its window buckets, and
@@ -1018,10 +1018,10 @@ size_t batch_sort_scratch_bytes(uint64_t ntiles, uint32_t nseg, int key_bytes) {
          align256(sizeof(uint64_t) * kRadix * (ntiles + 1));
 }
 
-size_t batch_hybrid_bytes(uint32_t nseg) {
+size_t batch_hybrid_bytes(uint32_t nseg, uint64_t ntiles) {
   return align256(sizeof(BatchPlan) * nseg) + align256(sizeof(SlotMap) * nseg) +
          2 * align256(sizeof(uint64_t) * (uint64_t)nseg * kRadix) + 256 +
-         3 * align256(sizeof(uint32_t) * (nseg + 1));
+         3 * align256(sizeof(uint32_t) * (nseg + 1)) + 2 * align256(sizeof(uint32_t) * (ntiles + 1));
 }
 
 cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], uint32_t* tmp_v[2],
@@ -1069,10 +1069,12 @@ cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], u
       k_batch_window_hist<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)keys, chunks, nchunks, hy->plan, hy->hist_w);
     k_batch_window_scan<<<nseg, 256, 0, s>>>(hy->hist_w, hy->offs_w, seg_start, cap, hy->plan);
     k_batch_mode_prefix<<<1, 1024, 0, s>>>(hy->plan, hy->tile0, nseg, hy->prefix_msd, hy->prefix_lsd);
-    count_launch(4);
+    k_batch_mode_lists<<<nseg, 256, 0, s>>>(hy->plan, hy->tile0, hy->prefix_msd, hy->prefix_lsd,
+                                            hy->list_msd, hy->list_lsd);
+    count_launch(5);
     // persistent grid over the tiles of the kPlanMsd indexes only; the status
     // array is shared with the LSD passes: a distinct epoch (9)
-    const TileMap msd_map{hy->prefix_msd, hy->tile0, nseg};
+    const TileMap msd_map{hy->list_msd, hy->prefix_msd + nseg};
     if (key_bytes == 4)
       k_batch_sort_pass<uint32_t><<<pgrid, kSortThreads, 0, s>>>(
           (const uint32_t*)keys, vals, (uint32_t*)tmp_k[1], tmp_v[1], n, 0u, tiles, hy->offs_w, 0,
@@ -1088,7 +1090,7 @@ cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], u
   // every pass runs (no host round trip to skip trivial digits, so the whole
   // build can be captured in a graph); with a plan, only for kPlanLsd indexes,
   // on a persistent grid over their tiles (usually none)
-  const TileMap lsd_map = hy ? TileMap{hy->prefix_lsd, hy->tile0, nseg} : TileMap{};
+  const TileMap lsd_map = hy ? TileMap{hy->list_lsd, hy->prefix_lsd + nseg} : TileMap{};
   const unsigned grid = hy ? pgrid : (unsigned)ntiles;
   const void* ck = keys;
   const uint32_t* cv = vals;
@@ -1140,7 +1142,7 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
                          cudaStream_t s, const BatchHybrid* hy, uint32_t nseg) {
   if (ntiles == 0) return cudaSuccess;
   const BatchPlan* plan = hy ? hy->plan : nullptr;
-  const TileMap map = hy ? TileMap{hy->prefix_lsd, hy->tile0, nseg} : TileMap{};
+  const TileMap map = hy ? TileMap{hy->list_lsd, hy->prefix_lsd + nseg} : TileMap{};
   if (key_bytes == 4)
     launch_batch_gather<uint32_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s, plan, map);
   else

@@ -491,3 +491,23 @@ def test_build_flags_are_exclusive():
     with pytest.raises(gi.GIError) as e:
         build(keys, rows, gi.GI_SORTED | gi.GI_BUILD_LSD | gi.GI_BUILD_HYBRID, 0)
     assert e.value.code == gi.GI_ERR_INVALID
+
+
+@pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER_KARY, 5), (gi.GI_SORTED, 0)])
+def test_hybrid_buckets_above_4096_take_the_512_thread_sort(layout, k):
+    # 6 values in the top byte x 16 in the next: 96 MSD buckets of ~4600 pairs, the
+    # bucket sort's 512-thread class (up to 5120 pairs); random low 48 bits
+    n = 96 * 4600
+    rng = np.random.default_rng(23)
+    hi = (rng.integers(0, 6, size=n).astype(np.uint64) << np.uint64(56)) | \
+         (rng.integers(0, 16, size=n).astype(np.uint64) << np.uint64(48))
+    keys = hi | rng.integers(0, 1 << 48, size=n, dtype=np.uint64)
+    rows = rng.permutation(n).astype(np.uint32)
+    ok, orr = _oracle_layout(keys, rows, layout, k)
+    for flag, launches in ((gi.GI_BUILD_HYBRID, 7), (gi.GI_BUILD_LSD, 11)):
+        c0 = gi.gi_launch_count()
+        idx = build(keys, rows, layout | flag, k)
+        assert gi.gi_launch_count() - c0 == launches, flag  # the hybrid sort did run
+        lk, lr = layout_arrays(idx, n, np.uint64)
+        assert np.array_equal(lk, ok) and np.array_equal(lr, orr), flag
+        gi.gi_destroy(idx)

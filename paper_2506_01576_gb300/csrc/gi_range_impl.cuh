@@ -310,6 +310,12 @@ __device__ __forceinline__ uint32_t row_at(const uint32_t* __restrict__ rows, ui
   return s < g.n ? __ldg(rows + s) : GI_MISS;  // ranks are < n; the bound is a guard
 }
 
+// Rows of 32 consecutive ranges per warp.  Ranges of 32 rows or more are filled by
+// the whole warp, one at a time (coalesced, the switch of Section 5.1).  The short
+// ones are filled cooperatively: their rows, concatenated, are dealt to the lanes
+// (32 independent loads in flight), each lane finding its row's range by a 5-step
+// search over the lanes' running counts (the last range starting at or before the
+// row; an empty range shares its start with the next one, which wins).
 template <int LAYOUT, int KF, class IDX>
 __global__ void __launch_bounds__(256) k_range_fill(const uint32_t* __restrict__ rows, Geom g,
                                                     SlotMap sm,
@@ -337,8 +343,27 @@ __global__ void __launch_bounds__(256) k_range_fill(const uint32_t* __restrict__
       const uint64_t br = __shfl_sync(0xffffffffu, r0, b);
       for (uint64_t j = lane; j < bc; j += 32) out[bo + j] = row_at<LAYOUT, KF, IDX>(rows, br + j, g, sm);
     }
-    if (!big) {
-      for (uint64_t j = 0; j < cnt; ++j) out[off + j] = row_at<LAYOUT, KF, IDX>(rows, r0 + j, g, sm);
+    // short ranges: running count of their rows over the lanes
+    uint32_t c = big ? 0u : (uint32_t)cnt, x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const uint32_t rel = x - c;  // rows of the short ranges before this lane's
+    const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+    for (uint32_t row0 = 0; row0 < total; row0 += 32) {  // warp-uniform: the shuffles need all lanes
+      const uint32_t row = row0 + lane;
+      int src = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t v = __shfl_sync(0xffffffffu, rel, src + step);
+        if (v <= row) src += step;
+      }
+      const uint32_t k = row - __shfl_sync(0xffffffffu, rel, src);
+      const uint64_t o = __shfl_sync(0xffffffffu, off, src) + k;
+      const uint64_t r = __shfl_sync(0xffffffffu, r0, src) + k;
+      if (row < total) out[o] = row_at<LAYOUT, KF, IDX>(rows, r, g, sm);
     }
   }
 }

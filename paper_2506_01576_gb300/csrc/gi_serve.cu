@@ -250,8 +250,29 @@ __global__ void __launch_bounds__(256) k_serve_fill(const ServeIndex* __restrict
         const uint64_t br = __shfl_sync(0xffffffffu, r0, b);
         for (uint64_t j = lane; j < bc; j += 32) out[bo + j] = __ldg(d.rows + slot(br + j));
       }
-      if (!big)
-        for (uint64_t j = 0; j < cnt; ++j) out[off + j] = __ldg(d.rows + slot(r0 + j));
+      // short ranges: their rows dealt to the lanes (coalesced, 32 loads in flight);
+      // a 5-step search over the lanes' running counts finds each row's range
+      uint32_t c = big ? 0u : (uint32_t)cnt, x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      const uint32_t rel = x - c;
+      const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+      for (uint32_t row0 = 0; row0 < total; row0 += 32) {  // warp-uniform for the shuffles
+        const uint32_t row = row0 + lane;
+        int src = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t v = __shfl_sync(0xffffffffu, rel, src + step);
+          if (v <= row) src += step;
+        }
+        const uint32_t k = row - __shfl_sync(0xffffffffu, rel, src);
+        const uint64_t o = __shfl_sync(0xffffffffu, off, src) + k;
+        const uint64_t r = __shfl_sync(0xffffffffu, r0, src) + k;
+        if (row < total) out[o] = __ldg(d.rows + slot(r));
+      }
     }
   }
 }

@@ -217,3 +217,20 @@ def test_batch_build_plans_every_path(bits, layout, k):
     gi.gi_batch_sync(batch)
     _check(batch, keys, rows, qs, qoff, out, layout, k)
     gi.gi_batch_destroy(batch)
+
+
+@pytest.mark.parametrize("sizes", [[100000], [0], [0, 0, 7000, 0], [1]])
+def test_batch_degenerate_shapes(sizes):
+    # one index, only empty indexes, empty indexes around one: every plan kernel and
+    # ticket map must cope with indexes that have no tiles
+    keys, rows, off = _make_batch(sizes, 64, 61)
+    qs, qoff = _probes(keys, 64, [700] * len(sizes), 19)
+    batch = gi.gi_batch_create(off, gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 9)
+    kd = to_dev(np.concatenate(keys)) if off[-1] else torch.empty(0, dtype=torch.int64, device=DEV)
+    rd = to_dev(np.concatenate(rows)) if off[-1] else torch.empty(0, dtype=torch.int32, device=DEV)
+    gi.gi_batch_build(batch, kd, rd)
+    out = torch.full((int(qoff[-1]),), -5, dtype=torch.int32, device=DEV)
+    gi.gi_batch_point_lookup(batch, to_dev(np.concatenate(qs)), to_dev(qoff), out)
+    gi.gi_batch_sync(batch)
+    _check(batch, keys, rows, qs, qoff, out, gi.GI_EYTZINGER_KARY, 9)
+    gi.gi_batch_destroy(batch)

@@ -121,6 +121,45 @@ size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t key_alloc_bytes(uint64_t n, int key_bytes) { return round256((n + 1 + 64) * key_bytes + 64); }
 size_t row_alloc_bytes(uint64_t n) { return round256((n + 64) * 4); }
 
+// Page-locked host scratch of the calling thread for the build's small
+// device-to-host reads (digit flags and counts): copies into pageable memory would
+// block the host until the stream drains, before the next kernel is queued.
+struct PinnedScratch {
+  uint32_t* trivial = nullptr;        // [8]
+  unsigned long long* hist = nullptr;  // [8][256]
+  unsigned long long* h2 = nullptr;    // [256][256]
+  cudaEvent_t ev = nullptr;
+  int device = -1;
+  cudaError_t ensure() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (trivial && dev == device) return cudaSuccess;
+    if (trivial) {  // another device: new allocations in its context
+      cudaFreeHost(trivial);
+      cudaEventDestroy(ev);
+      trivial = nullptr;
+    }
+    void* p = nullptr;
+    const size_t bytes = 256 + sizeof(uint64_t) * (8 * 256 + 256 * 256);
+    cudaError_t e = cudaMallocHost(&p, bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaFreeHost(p);
+      return e;
+    }
+    trivial = (uint32_t*)p;
+    hist = (unsigned long long*)((char*)p + 256);
+    h2 = hist + 8 * 256;
+    device = dev;
+    return cudaSuccess;
+  }
+};
+PinnedScratch& pinned_scratch() {
+  static thread_local PinnedScratch t;
+  return t;
+}
+
 // Device memory comes from the device's stream-ordered pool.  The pool's release
 // threshold is raised once per device to 8 GiB (a setting of this process only):
 // the sort buffers a build frees are reused by the next build instead of being
@@ -496,34 +535,62 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   }
   const size_t sbytes = gi::sort_scratch_bytes(n, kb);
   GI_TRY2(dalloc(&scratch, sbytes, s), "sort scratch");
-  uint32_t trivial = 0;
-  std::vector<unsigned long long> hist(8 * 256);
+  // histogram and digit offsets; their copy to the host is waited for only after
+  // the first MSD pass is queued behind them (speculatively on the top byte, where
+  // the hybrid sort starts for keys that use it), so the GPU does not idle while
+  // the host plans
+  PinnedScratch& pin = pinned_scratch();
+  GI_TRY2(pin.ensure(), "page-locked scratch");
   GI_TRY2(gi::sort_prepare(keys_bus ? keys_bus : src_k, keys_bus ? bk[0] : nullptr, n, kb, scratch,
-                           idx->dflags, s, &trivial, hist.data()),
+                           s, pin.trivial, pin.hist),
           "histogram");
+  cudaEvent_t hist_ready = pin.ev;
+  GI_TRY2(cudaEventRecord(hist_ready, s), "histogram");
   // Ping-pong between the two buffers; the first pass writes the buffer that does
   // not hold a staged copy of the input.
   const void* ck = src_k;
   const uint32_t* cv = src_v;
   int cur = -1;  // -1: the data is still the (caller's or staged) input
   int next_dst = staged ? 1 : 0;
-  bool sorted_done = false;
+  bool speculate = !(flags & GI_BUILD_LSD) && kb == 8 && n < (1ull << 32) &&
+                   (n >= (1ull << 24) || (flags & GI_BUILD_HYBRID));
+  if (speculate)  // skipped on the device if every key has the same top byte
+    GI_TRY2(gi::sort_msd_pass(ck, cv, bk[next_dst], bv[next_dst], n, kb, kb - 1, scratch,
+                              idx->dflags, true, s),
+            "radix pass");
+  GI_TRY2(cudaEventSynchronize(hist_ready), "histogram");
+  uint32_t trivial = 0;
+  for (int p = 0; p < kb; ++p)
+    if (pin.trivial[p]) trivial |= 1u << p;
+  if (trivial & (1u << (kb - 1))) speculate = false;  // that pass wrote nothing
+  bool sorted_done = false, pass1_pending_reset = false;
+  if (speculate) {  // the MSD pass ran: a stable permutation into bk[next_dst]
+    ck = bk[next_dst];
+    cv = bv[next_dst];
+    cur = next_dst;
+    pass1_pending_reset = true;
+  }
   if (!(flags & GI_BUILD_LSD)) {  // hybrid MSD + shared-memory bucket sort where it applies
     int res = -1;
     bool used = false;
     const uint32_t nontrivial = ~trivial & ((1u << kb) - 1);
-    GI_TRY2(gi::hybrid_sort(ck, cv, bk, bv, next_dst, n, kb, nontrivial, hist.data(), scratch,
+    GI_TRY2(gi::hybrid_sort(speculate ? src_k : ck, speculate ? src_v : cv, bk, bv,
+                            speculate ? cur : next_dst, n, kb, nontrivial, pin.hist, scratch,
                             idx->geom, lay == GI_SORTED, lay == GI_EYTZINGER ? 1u : 0u,
-                            (flags & GI_BUILD_HYBRID) != 0, idx->dflags, s, &res, &used),
+                            (flags & GI_BUILD_HYBRID) != 0, speculate, pin.h2, idx->dflags, s,
+                            &res, &used),
             "hybrid sort");
     if (res >= 0) {
       ck = bk[res];
       cv = bv[res];
+      pass1_pending_reset = pass1_pending_reset && res == cur;  // else reset inside
       cur = res;
-      next_dst = 1 - res;
       sorted_done = used;  // bk[res] holds the finished layout, duplicates flagged
     }
   }
+  if (cur >= 0) next_dst = 1 - cur;
+  if (!sorted_done && pass1_pending_reset)  // the LSD passes reuse the MSD pass's ticket
+    GI_TRY2(gi::sort_reset_counters(scratch, kb, s), "radix pass");
   for (int p = 0; p < kb && !sorted_done; ++p) {
     if (trivial & (1u << p)) continue;  // every key has the same digit here
     const int dst = next_dst;

@@ -194,13 +194,22 @@ struct SortBuffers {
   size_t scratch_bytes;
 };
 size_t sort_scratch_bytes(uint64_t n, int key_bytes);
-// Histogram all digits and scan them on the device; the host gets the trivial
-// mask (and the counts).  copy_to != NULL: `keys` is page-locked host memory,
+// Histogram all digits and scan them on the device, then copy the per-digit
+// "one value only" flags and the counts to host_trivial[key_bytes] /
+// host_hist[key_bytes][256] (page-locked; valid once the stream gets there: no
+// synchronisation inside).  copy_to != NULL: `keys` is page-locked host memory,
 // copied to copy_to by the same pass.
 cudaError_t sort_prepare(const void* keys, void* copy_to, uint64_t n, int key_bytes,
-                         void* scratch, uint32_t* dflags, cudaStream_t s,
-                         uint32_t* host_trivial_mask /* pinned or pageable, sync inside */,
-                         unsigned long long* host_hist /* [key_bytes][256], may be NULL */);
+                         void* scratch, cudaStream_t s, uint32_t* host_trivial,
+                         unsigned long long* host_hist);
+// One stable MSD pass on `digit` (offsets from sort_prepare), reading the input
+// rowIDs (checked for the reserved value).  skip_if_trivial: the kernel returns
+// at once (nothing written) if sort_prepare found one value only in that digit.
+cudaError_t sort_msd_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
+                          uint64_t n, int key_bytes, int digit, void* scratch, uint32_t* dflags,
+                          bool skip_if_trivial, cudaStream_t s);
+// Tile tickets back to zero (before LSD passes that follow an MSD pass).
+cudaError_t sort_reset_counters(void* scratch, int key_bytes, cudaStream_t s);
 // check_rows: this pass reads the caller's rowIDs; flag any equal to GI_MISS.
 cudaError_t sort_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
                       uint64_t n, int key_bytes, int pass, void* scratch, uint32_t* dflags,
@@ -288,16 +297,19 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
 // then every bucket sorted in shared memory and written straight into the final
 // layout (gi_local_sort.cu): slot = rank for the sorted layout, else the k-ary
 // (k = g.k; Eytzinger for k = 2, keys shifted by key_off) slot of the rank.
+// pass1_done: the caller already ran the MSD pass on the top byte into
+// bk[first_dst].  host_h2: page-locked room for 256 x 256 counts.
 // *used = true: bk[*result] / bv[*result] hold the finished layout and the
 // duplicate flag is set.  *used = false and *result = -1: not applicable,
-// nothing launched.  *used = false and *result >= 0: a bucket turned out too
-// large after the first MSD pass; bk[*result] holds the data after that stable
-// pass for a full LSD sort.
+// nothing launched.  *used = false and *result >= 0: bk[*result] holds the data
+// after stable MSD scatter(s) (not applicable after a caller's pass 1, or a
+// bucket too large), for a full LSD sort (counters reset only in the latter).
 cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], uint32_t* bv[2],
                         int first_dst, uint64_t n, int key_bytes, uint32_t nontrivial,
                         const unsigned long long* host_hist, void* scratch, const Geom& g,
-                        bool sorted_layout, uint32_t key_off, bool force, uint32_t* dflags,
-                        cudaStream_t s, int* result, bool* used);
+                        bool sorted_layout, uint32_t key_off, bool force, bool pass1_done,
+                        unsigned long long* host_h2, uint32_t* dflags, cudaStream_t s,
+                        int* result, bool* used);
 // Shared-memory sort of buckets of at most local_sort_capacity() pairs that
 // agree on every digit outside local_mask, written into the layout (see above).
 uint32_t local_sort_capacity();

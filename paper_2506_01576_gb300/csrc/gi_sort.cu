@@ -215,9 +215,10 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
     uint32_t* __restrict__ dst_v, uint64_t n, uint32_t shift,
     const unsigned long long* __restrict__ digit_off, uint64_t* __restrict__ status,
     uint32_t* __restrict__ tile_counter, uint32_t epoch, uint32_t* __restrict__ flags,
-    uint32_t check_rows) {
+    uint32_t check_rows, const uint32_t* __restrict__ skip_if) {
   constexpr int ITEMS = SortTile<K>::kItems;
   constexpr int TILE = kSortThreads * ITEMS;
+  if (skip_if && *skip_if) return;  // a speculative pass on a digit that turned out trivial
   // keys and rowIDs have their own exchange arrays, so one final loop writes both;
   // the per-warp digit counters share space with the rowIDs (dead by then)
   union HistOrVals {
@@ -902,9 +903,8 @@ size_t sort_scratch_bytes(uint64_t n, int key_bytes) {
 }
 
 cudaError_t sort_prepare(const void* keys, void* copy_to, uint64_t n, int key_bytes,
-                         void* scratch, uint32_t* dflags, cudaStream_t s,
-                         uint32_t* host_trivial_mask, unsigned long long* host_hist) {
-  (void)dflags;
+                         void* scratch, cudaStream_t s, uint32_t* host_trivial,
+                         unsigned long long* host_hist) {
   ScratchView v = view(scratch, key_bytes);
   cudaError_t e = cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, key_bytes), s);
   if (e != cudaSuccess) return e;
@@ -915,20 +915,35 @@ cudaError_t sort_prepare(const void* keys, void* copy_to, uint64_t n, int key_by
     k_histogram<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)keys, (uint64_t*)copy_to, n, v.hist);
   k_scan_hist<<<key_bytes, 256, 0, s>>>(v.hist, v.offs, v.trivial, n);
   count_launch(2);
-  uint32_t triv[8] = {0};
-  e = cudaMemcpyAsync(triv, v.trivial, sizeof(uint32_t) * key_bytes, cudaMemcpyDeviceToHost, s);
+  e = cudaMemcpyAsync(host_trivial, v.trivial, sizeof(uint32_t) * key_bytes, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return e;
-  if (host_hist) {
-    e = cudaMemcpyAsync(host_hist, v.hist, sizeof(uint64_t) * key_bytes * kRadix, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return e;
-  }
-  e = cudaStreamSynchronize(s);
+  e = cudaMemcpyAsync(host_hist, v.hist, sizeof(uint64_t) * key_bytes * kRadix, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return e;
-  uint32_t mask = 0;
-  for (int p = 0; p < key_bytes; ++p)
-    if (triv[p]) mask |= 1u << p;
-  *host_trivial_mask = mask;
   return cudaGetLastError();
+}
+
+cudaError_t sort_msd_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
+                          uint64_t n, int key_bytes, int digit, void* scratch, uint32_t* dflags,
+                          bool skip_if_trivial, cudaStream_t s) {
+  ScratchView v = view(scratch, key_bytes);
+  const uint32_t* skip = skip_if_trivial ? v.trivial + digit : nullptr;
+  // its own epoch (20 + digit), so a later LSD pass on the same digit, after
+  // sort_reset_counters, never mistakes its status words
+  if (key_bytes == 4)
+    k_sort_pass<uint32_t><<<(unsigned)tiles_for(n, 4), kSortThreads, 0, s>>>(
+        (const uint32_t*)src_k, src_v, (uint32_t*)dst_k, dst_v, n, 8u * digit,
+        v.offs + digit * kRadix, v.status, v.counter + digit, 20u + digit, dflags, 1u, skip);
+  else
+    k_sort_pass<uint64_t><<<(unsigned)tiles_for(n, 8), kSortThreads, 0, s>>>(
+        (const uint64_t*)src_k, src_v, (uint64_t*)dst_k, dst_v, n, 8u * digit,
+        v.offs + digit * kRadix, v.status, v.counter + digit, 20u + digit, dflags, 1u, skip);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t sort_reset_counters(void* scratch, int key_bytes, cudaStream_t s) {
+  ScratchView v = view(scratch, key_bytes);
+  return cudaMemsetAsync(v.counter, 0, align256(sizeof(uint32_t) * key_bytes), s);
 }
 
 cudaError_t sort_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
@@ -943,12 +958,12 @@ cudaError_t sort_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uin
     k_sort_pass<uint32_t><<<(unsigned)tiles, kSortThreads, 0, s>>>(
         (const uint32_t*)src_k, src_v, (uint32_t*)dst_k, dst_v, n, 8u * pass,
         v.offs + pass * kRadix, v.status, v.counter + pass, (uint32_t)pass + 1, dflags,
-        check_rows ? 1u : 0u);
+        check_rows ? 1u : 0u, nullptr);
   else
     k_sort_pass<uint64_t><<<(unsigned)tiles, kSortThreads, 0, s>>>(
         (const uint64_t*)src_k, src_v, (uint64_t*)dst_k, dst_v, n, 8u * pass,
         v.offs + pass * kRadix, v.status, v.counter + pass, (uint32_t)pass + 1, dflags,
-        check_rows ? 1u : 0u);
+        check_rows ? 1u : 0u, nullptr);
   count_launch();
   return cudaGetLastError();
 }
@@ -1155,16 +1170,18 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
 cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], uint32_t* bv[2],
                         int first_dst, uint64_t n, int key_bytes, uint32_t nontrivial,
                         const unsigned long long* host_hist, void* scratch, const Geom& g,
-                        bool sorted_layout, uint32_t key_off, bool force, uint32_t* dflags,
-                        cudaStream_t s, int* result, bool* used) {
+                        bool sorted_layout, uint32_t key_off, bool force, bool pass1_done,
+                        unsigned long long* host_h2, uint32_t* dflags, cudaStream_t s,
+                        int* result, bool* used) {
   *used = false;
-  *result = -1;
+  *result = pass1_done ? first_dst : -1;
   // digits from the most significant down
   int digits[8], nd = 0;
   for (int p = key_bytes - 1; p >= 0; --p)
     if (nontrivial & (1u << p)) digits[nd++] = p;
   // The bucket sort's slot map is 32-bit: larger indexes take the LSD sort.
   if (nd < 2 || n >= (1ull << 32)) return cudaSuccess;
+  if (pass1_done && digits[0] != key_bytes - 1) return cudaSuccess;  // the top byte was trivial
   // Measured crossovers (GB300, u64 keys): below 2^24 pairs the buckets are too
   // small to pay for the extra passes and the host round trip; with four
   // non-trivial digits or fewer (u32 keys) the two MSD passes save at most two
@@ -1190,17 +1207,13 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
 
   ScratchView v = view(scratch, key_bytes);
   cudaError_t e;
-  // pass 1: a plain global pass on digit d1 (its offsets are in v.offs)
+  // pass 1: a plain global pass on digit d1 (its offsets are in v.offs), unless the
+  // caller ran it already, on the top byte, while the histogram came back
   const int dst1 = first_dst;
-  if (key_bytes == 4)
-    k_sort_pass<uint32_t><<<(unsigned)tiles_for(n, 4), kSortThreads, 0, s>>>(
-        (const uint32_t*)src_k, src_v, (uint32_t*)bk[dst1], bv[dst1], n, 8u * d1,
-        v.offs + d1 * kRadix, v.status, v.counter + d1, 20u + d1, dflags, 1u);
-  else
-    k_sort_pass<uint64_t><<<(unsigned)tiles_for(n, 8), kSortThreads, 0, s>>>(
-        (const uint64_t*)src_k, src_v, (uint64_t*)bk[dst1], bv[dst1], n, 8u * d1,
-        v.offs + d1 * kRadix, v.status, v.counter + d1, 20u + d1, dflags, 1u);
-  count_launch();
+  if (!pass1_done) {
+    e = sort_msd_pass(src_k, src_v, bk[dst1], bv[dst1], n, key_bytes, d1, scratch, dflags, false, s);
+    if (e != cudaSuccess) return e;
+  }
   int cur = dst1;
   std::vector<BatchTile> segs;  // the buckets the shared-memory sort takes
   if (two) {
@@ -1253,19 +1266,16 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
       k_seg_hist1<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)bk[cur], d_chunks, chunks.size(), 8u * d2, d_hist);
     k_batch_scan_hist<<<nseg1, 256, 0, s>>>(d_hist, d_offs, d_seg_start, 1);
     count_launch(2);
-    std::vector<unsigned long long> h2((size_t)nseg1 * kRadix);
-    e = cudaMemcpyAsync(h2.data(), d_hist, hbytes, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // the level-2 counts come back while pass 2 runs (it is a correct stable
+    // scatter whatever they show); the host waits on this event only
+    e = cudaMemcpyAsync(host_h2, d_hist, hbytes, cudaMemcpyDeviceToHost, s);
+    cudaEvent_t ev = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, s);
     if (e != cudaSuccess) {
+      if (ev) cudaEventDestroy(ev);
       cudaFreeAsync(blob, s);
       return e;
-    }
-    uint64_t mx = 0;
-    for (auto c : h2) mx = std::max<uint64_t>(mx, c);
-    if (mx > cap) {  // a bucket too large for one CTA: the caller runs the full LSD sort
-      cudaFreeAsync(blob, s);
-      *result = cur;  // the data after the stable d1 pass
-      return cudaMemsetAsync(v.counter, 0, align256(sizeof(uint32_t) * key_bytes), s);
     }
     // pass 2: segmented on d2; tiles.size() <= tiles_for(n) + 256, which the
     // status array is sized for
@@ -1281,8 +1291,18 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
     count_launch();
     cur = dst2;
     cudaFreeAsync(blob, s);
+    e = cudaEventSynchronize(ev);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long* h2 = host_h2;
+    uint64_t mx = 0;
+    for (size_t j = 0; j < (size_t)nseg1 * kRadix; ++j) mx = std::max<uint64_t>(mx, h2[j]);
+    if (mx > cap) {  // a bucket too large for one CTA: the caller runs the full LSD sort
+      *result = cur;  // the data after the stable scatters on d1 and d2
+      return sort_reset_counters(scratch, key_bytes, s);
+    }
     // level-2 buckets, built while pass 2 runs
-    segs.reserve(h2.size());
+    segs.reserve((size_t)nseg1 * kRadix);
     for (uint32_t a = 0; a < nseg1; ++a) {
       uint64_t at = seg_start[a];
       for (int d = 0; d < kRadix; ++d) {

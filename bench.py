@@ -153,6 +153,18 @@ class ClockSampler:
                 "samples": len(inside)}
 
 
+def step_config(a, world):
+    """The benchmark step's workload (the same dict for both arms)."""
+    return {"workload": "build 2^%d unique u64 keys (%s) + 2^%d point probes (hit 0.5, "
+                        "uniform) + 2^%d ranges (%.0f expected rows) per step"
+                        % (a.n_log, "EKS k=%d" % a.k if a.layout == "eks" else a.layout.upper(),
+                           a.m_log, a.ranges_log, a.range_rows),
+            "n_keys": 1 << a.n_log, "point_probes": 1 << a.m_log, "ranges": 1 << a.ranges_log,
+            "layout": a.layout.upper(), "k": a.k if a.layout == "eks" else None,
+            "l2": "inputs larger than L2 (no flush)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def kary_level_sizes(n: int, k: int):
     """Keys per level of the complete k-ary tree of n keys (last level partial)."""
     if n == 0:
@@ -293,7 +305,7 @@ def run_ours(a):
     res = {}
     if rank == 0 and not a.no_extras:
         res = extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, layout,
-                     total_rows)
+                     total_rows, lo, hi)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -303,21 +315,15 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "build 2^%d unique u64 keys (%s) + 2^%d point probes (hit 0.5, "
-                               "uniform) + 2^%d ranges (%.0f expected rows) per step"
-                               % (a.n_log, "EKS k=%d" % a.k if a.layout == "eks" else a.layout.upper(),
-                                  a.m_log, a.ranges_log, a.range_rows),
-                   "n_keys": n, "point_probes": m, "ranges": mr, "range_rows_total": total_rows,
-                   "layout": a.layout.upper(), "k": a.k if a.layout == "eks" else None,
-                   "l2": "inputs larger than L2 (no flush)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": step_config(a, world), "range_rows_total": total_rows,
         "clocks": clk.summary(), "gpu_launches": int(launches),
     }
     line.update(res)
     print(json.dumps(line), flush=True)
 
 
-def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, layout, total_rows):
+def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, layout, total_rows,
+           lo, hi):
     """Lookup-only rates, roofline, e2e through host buffers, CPU oracle."""
     import oracle
     stream = torch.cuda.current_stream()
@@ -436,7 +442,7 @@ def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, 
                       "ms_per_step": dt * 1e3, "host_buffers": "pinned"}
     # ---- CPU oracle on the host cores (bounded sample)
     if not a.no_cpu:
-        res["cpu_baseline"] = cpu_oracle_sample(keys, q, n, m, a)
+        res["cpu_baseline"] = cpu_oracle_sample(keys, q, lo, hi, n, m, a)
     return res
 
 
@@ -468,31 +474,51 @@ def recorded_traffic(a, m, hot_levels):
         return None
 
 
-def cpu_oracle_sample(keys, q, n, m, a, sort_sample=1 << 22, point_sample=1 << 21):
-    """The oracle as it stands on the host cores: a sample of the step, scaled.
+def oracle_step_estimate(oracle, keys, rows, sk, sr, q, lo, hi, threads, rng,
+                         sort_sample, point_sample, range_sample):
+    """Seconds of one benchmark step on the oracle, from timed samples: std::sort of
+    `sort_sample` pairs (one thread) scaled to n by n log n; std::lower_bound of
+    `point_sample` probes over the full sorted index on `threads` threads, scaled
+    to the probe count; the ranges (lower_bound + forward scan, CSR) of
+    `range_sample` ranges on `threads` threads, scaled to the range count."""
+    n, m, mr = len(keys), len(q), len(lo)
+    j = int(rng.integers(0, n - sort_sample + 1))
+    t0 = time.perf_counter()
+    oracle.sort_pairs(keys[j:j + sort_sample], rows[j:j + sort_sample])
+    t_sort = time.perf_counter() - t0
+    i = int(rng.integers(0, m - point_sample + 1))
+    t0 = time.perf_counter()
+    oracle.point_lookup(sk, sr, q[i:i + point_sample], threads)
+    t_pt = time.perf_counter() - t0
+    r = int(rng.integers(0, mr - range_sample + 1))
+    t0 = time.perf_counter()
+    oracle.range_lookup(sk, sr, lo[r:r + range_sample], hi[r:r + range_sample], threads)
+    t_rg = time.perf_counter() - t0
+    return (t_sort * (n / sort_sample) * (math.log2(n) / math.log2(sort_sample))
+            + t_pt * (m / point_sample) + t_rg * (mr / range_sample))
 
-    Sort: std::sort of `sort_sample` pairs (single thread), scaled to n by
-    n log n.  Point lookups: std::lower_bound of `point_sample` probes over the
-    full sorted index on all cores, scaled to m.  Ranges are not timed (the
-    point-lookup metric's step is dominated by the two parts above).
-    """
+
+def oracle_sample_text(n, m, mr, threads, sort_sample, point_sample, range_sample):
+    return ("std::sort of 2^%d pairs (1 thread, scaled n log n to 2^%d) + std::lower_bound of "
+            "2^%d probes on %d threads (scaled to 2^%d) + 2^%d ranges, lower_bound and scan, on "
+            "%d threads (scaled to 2^%d)"
+            % (int(math.log2(sort_sample)), int(math.log2(n)), int(math.log2(point_sample)),
+               threads, int(math.log2(m)), int(math.log2(range_sample)), threads, int(math.log2(mr))))
+
+
+def cpu_oracle_sample(keys, q, lo, hi, n, m, a, sort_sample=1 << 22, point_sample=1 << 21,
+                      range_sample=1 << 17):
+    """The oracle as it stands on the host cores: one sampled step, scaled."""
     import oracle
     threads = oracle.hardware_threads()
     rows = np.arange(n, dtype=np.uint32)
-    t0 = time.perf_counter()
-    oracle.sort_pairs(keys[:sort_sample], rows[:sort_sample])
-    t_sort = time.perf_counter() - t0
     sk, sr = oracle.sort_pairs(keys, rows)  # full index, untimed
-    qs = q[:point_sample]
-    t0 = time.perf_counter()
-    oracle.point_lookup(sk, sr, qs, threads)
-    t_pt = time.perf_counter() - t0
-    est = t_sort * (n / sort_sample) * (math.log2(n) / math.log2(sort_sample)) + t_pt * (m / point_sample)
+    mr = len(lo)
+    range_sample = min(range_sample, mr)
+    est = oracle_step_estimate(oracle, keys, rows, sk, sr, q, lo, hi, threads,
+                               np.random.default_rng(0), sort_sample, point_sample, range_sample)
     return {"value": m / est, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "std::sort of 2^%d pairs (1 thread, scaled n log n to 2^%d) + "
-                      "std::lower_bound of 2^%d probes on %d threads (scaled to 2^%d)"
-                      % (int(math.log2(sort_sample)), int(math.log2(n)),
-                         int(math.log2(point_sample)), threads, int(math.log2(m))),
+            "sample": oracle_sample_text(n, m, mr, threads, sort_sample, point_sample, range_sample),
             "est_step_s": est}
 
 
@@ -503,41 +529,32 @@ def run_reference(a):
         return
     import oracle
     oracle.build()
-    n, m = 1 << a.n_log, 1 << a.m_log
+    n, m, mr = 1 << a.n_log, 1 << a.m_log, 1 << a.ranges_log
     seed = W.seed_for(1, a.n_log, 0)
     keys = W.unique_keys(n, 64, seed)
     q = W.point_probes(keys, m, 0.5, 64, seed, seed + 1)
+    lo, hi, _ = W.ranges_with_expected_rows(n, mr, a.range_rows, 64, seed + 2)
     rows = np.arange(n, dtype=np.uint32)
     threads = oracle.hardware_threads()
     sk, sr = oracle.sort_pairs(keys, rows)
-    sort_sample, point_sample = 1 << 21, 1 << 20
+    sort_sample, point_sample, range_sample = 1 << 21, 1 << 20, min(1 << 16, mr)
     rng = np.random.default_rng(1)
 
     def step():
-        j = int(rng.integers(0, n - sort_sample))
-        t0 = time.perf_counter()
-        oracle.sort_pairs(keys[j:j + sort_sample], rows[j:j + sort_sample])
-        t_sort = time.perf_counter() - t0
-        i = int(rng.integers(0, m - point_sample))
-        t0 = time.perf_counter()
-        oracle.point_lookup(sk, sr, q[i:i + point_sample], threads)
-        t_pt = time.perf_counter() - t0
-        return t_sort * (n / sort_sample) * (math.log2(n) / math.log2(sort_sample)) + t_pt * (m / point_sample)
+        return oracle_step_estimate(oracle, keys, rows, sk, sr, q, lo, hi, threads, rng,
+                                    sort_sample, point_sample, range_sample)
 
     for _ in range(a.warmup):
         step()
     ests = [step() for _ in range(a.steps)]
     est = float(np.mean(ests))
     value = m / est
-    sample = ("per step: std::sort of 2^21 pairs (1 thread, scaled n log n to 2^%d) + "
-              "std::lower_bound of 2^20 probes on %d threads (scaled to 2^%d)" % (a.n_log, threads, a.m_log))
+    sample = "per step: " + oracle_sample_text(n, m, mr, threads, sort_sample, point_sample,
+                                               range_sample)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "impl": "reference",
-            "config": {"workload": "build 2^%d unique u64 keys + 2^%d point probes (hit 0.5, uniform) "
-                                   "per step, estimated from a timed sample" % (a.n_log, a.m_log),
-                       "n_keys": n, "point_probes": m},
+            "impl": "reference", "config": step_config(a, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -511,3 +511,24 @@ def test_hybrid_buckets_above_4096_take_the_512_thread_sort(layout, k):
         lk, lr = layout_arrays(idx, n, np.uint64)
         assert np.array_equal(lk, ok) and np.array_equal(lr, orr), flag
         gi.gi_destroy(idx)
+
+
+def test_default_build_skips_the_speculative_pass_when_the_top_byte_is_trivial():
+    # 2^24 u64 keys below 2^32: the build queues its MSD pass on the top byte before it
+    # sees the histogram; every key has top byte 0, so the kernel returns at once, and
+    # with four differing bytes the LSD passes sort from the input (histogram, scan,
+    # the no-op pass, 4 passes, permutation = 8 launches)
+    n = 1 << 24
+    keys = W.unique_keys(n, 32, 91).astype(np.uint64)
+    rows = np.random.default_rng(3).permutation(n).astype(np.uint32)
+    rows[5] = gi.GI_MISS  # the LSD's first pass still checks the input rowIDs
+    with pytest.raises(gi.GIError):
+        build(keys, rows, gi.GI_EYTZINGER_KARY, 5)
+    rows[5] = n + 7
+    ok, orr = _oracle_layout(keys, rows, gi.GI_EYTZINGER_KARY, 5)
+    c0 = gi.gi_launch_count()
+    idx = build(keys, rows, gi.GI_EYTZINGER_KARY, 5)
+    assert gi.gi_launch_count() - c0 == 8
+    lk, lr = layout_arrays(idx, n, np.uint64)
+    assert np.array_equal(lk, ok) and np.array_equal(lr, orr)
+    gi.gi_destroy(idx)

@@ -123,7 +123,9 @@ size_t row_alloc_bytes(uint64_t n) { return round256((n + 64) * 4); }
 
 // Page-locked host scratch of the calling thread for the build's small
 // device-to-host reads (digit flags and counts): copies into pageable memory would
-// block the host until the stream drains, before the next kernel is queued.
+// block the host until the stream drains, before the next kernel is queued.  It
+// lives as long as the thread (532 KB); it is not freed at thread exit, when the
+// CUDA runtime may already be shutting down.
 struct PinnedScratch {
   uint32_t* trivial = nullptr;        // [8]
   unsigned long long* hist = nullptr;  // [8][256]

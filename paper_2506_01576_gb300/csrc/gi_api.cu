@@ -554,7 +554,12 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   const uint32_t* cv = src_v;
   int cur = -1;  // -1: the data is still the (caller's or staged) input
   int next_dst = staged ? 1 : 0;
-  bool speculate = !(flags & GI_BUILD_LSD) && kb == 8 && n < (1ull << 32) &&
+  // Speculate where the hybrid sort will likely follow: u64 keys from 2^24 pairs up,
+  // and at most 128 x 256 x the bucket capacity pairs (beyond, keys spread over
+  // only half the top byte, as uniform ones below 2^63 do, give buckets too large
+  // for a CTA, and the pass would be redone by the LSD sort).
+  const uint64_t spec_max = 128ull * 256ull * gi::local_sort_capacity();
+  bool speculate = !(flags & GI_BUILD_LSD) && kb == 8 && n < (1ull << 32) && n <= spec_max &&
                    (n >= (1ull << 24) || (flags & GI_BUILD_HYBRID));
   if (speculate)  // skipped on the device if every key has the same top byte
     GI_TRY2(gi::sort_msd_pass(ck, cv, bk[next_dst], bv[next_dst], n, kb, kb - 1, scratch,

@@ -412,6 +412,8 @@ int gi_batch_create(const uint64_t* key_offsets, uint32_t B, int layout, uint32_
     b->hy.prefix_lsd = (uint32_t*)take(sizeof(uint32_t) * (B + 1));
     b->hy.list_msd = (uint32_t*)take(sizeof(uint32_t) * (b->ntiles + 1));
     b->hy.list_lsd = (uint32_t*)take(sizeof(uint32_t) * (b->ntiles + 1));
+    b->hy.buckets = (uint32_t*)take(sizeof(uint32_t) * 3 * (uint64_t)B * 257);
+    b->hy.bucket_count = (uint32_t*)take(3 * sizeof(uint32_t));
     GI_B(cudaMemcpy(d_tile0, tile0.data(), sizeof(uint32_t) * (B + 1), cudaMemcpyHostToDevice), "batch tables");
     b->hy.out_k = b->keys;
     b->hy.out_v = b->rows;

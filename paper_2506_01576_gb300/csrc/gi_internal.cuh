@@ -263,6 +263,8 @@ struct BatchHybrid {
   uint32_t* prefix_lsd;         // [nseg + 1] same for kPlanLsd
   uint32_t* list_msd;           // [ntiles] tiles of the kPlanMsd indexes, in order
   uint32_t* list_lsd;           // [ntiles] tiles of the kPlanLsd indexes, in order
+  uint32_t* buckets;            // [3][nseg * 257] bucket ids per bucket-sort size class
+  uint32_t* bucket_count;       // [3]
   uint32_t k;                   // fan-out; 0 = sorted layout
 };
 size_t batch_hybrid_bytes(uint32_t nseg, uint64_t ntiles);  // device bytes of the tables

@@ -259,11 +259,12 @@ __global__ void __launch_bounds__(T, MINB) k_local_sort(
   if (__any_sync(0xffffffffu, dup) && lane == 0) atomicOr(flags, kFlagDuplicate);
 }
 
-// The batch's buckets: logical bucket id < nseg * 256 is window value (id & 255)
-// of index id >> 8 (indexes of plan kPlanMsd, sorted pairs in src after the MSD
-// pass); id >= nseg * 256 is the whole index id - nseg * 256 (plan kPlanWhole,
-// pairs still in the input).  A launch takes the buckets of (lo_count, hi_count]
-// pairs.  Each writes its index's layout at out + seg_base[i].
+// The batch's buckets: bucket id < nseg * 256 is window value (id & 255) of index
+// id >> 8 (indexes of plan kPlanMsd, sorted pairs in src after the MSD pass);
+// id >= nseg * 256 is the whole index id - nseg * 256 (plan kPlanWhole, pairs still
+// in the input).  A launch takes the ids of one size class, (lo_count, hi_count]
+// pairs, from `list` (written by k_batch_bucket_lists).  Each bucket writes its
+// index's layout at out + seg_base[i].
 template <class K, int ITEMS, int T, int MINB, int KF>
 __global__ void __launch_bounds__(T, MINB) k_batch_local_sort(
     const K* __restrict__ keys, const uint32_t* __restrict__ vals, const K* __restrict__ src_k,
@@ -271,14 +272,16 @@ __global__ void __launch_bounds__(T, MINB) k_batch_local_sort(
     const BatchPlan* __restrict__ plan, const SlotMap* __restrict__ maps,
     const unsigned long long* __restrict__ hist_w, const unsigned long long* __restrict__ offs_w,
     K* __restrict__ out_k, uint32_t* __restrict__ out_v, const uint64_t* __restrict__ seg_base,
-    uint32_t lo_count, uint32_t hi_count, uint32_t* __restrict__ flags) {
+    uint32_t lo_count, uint32_t hi_count, const uint32_t* __restrict__ list,
+    const uint32_t* __restrict__ list_count, uint32_t* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BucketSmem<K, ITEMS, T> m(smem_raw);
   __shared__ SlotMap s_map;
   const int tid = threadIdx.x, lane = tid & 31;
   bool dup = false;
-  const uint64_t total = (uint64_t)nseg * kRadix + nseg;
-  for (uint64_t id = blockIdx.x; id < total; id += gridDim.x) {
+  const uint32_t total = *list_count;
+  for (uint32_t li = blockIdx.x; li < total; li += gridDim.x) {
+    const uint64_t id = list[li];
     const bool msd = id < (uint64_t)nseg * kRadix;
     const uint32_t i = msd ? (uint32_t)(id >> 8) : (uint32_t)(id - (uint64_t)nseg * kRadix);
     const BatchPlan pl = plan[i];
@@ -308,6 +311,36 @@ __global__ void __launch_bounds__(T, MINB) k_batch_local_sort(
     __syncthreads();
   }
   if (__any_sync(0xffffffffu, dup) && lane == 0) atomicOr(flags, kFlagDuplicate);
+}
+
+// One CTA per index: its buckets' ids into the list of their size class (one
+// atomic per class per CTA).
+__global__ void __launch_bounds__(256) k_batch_bucket_lists(
+    const BatchPlan* __restrict__ plan, const unsigned long long* __restrict__ hist_w,
+    const uint64_t* __restrict__ seg_start, uint32_t nseg, uint32_t b0, uint32_t b1, uint32_t b2,
+    uint32_t* __restrict__ lists, uint32_t* __restrict__ counts) {
+  __shared__ uint32_t s_cnt[3], s_base[3];
+  const uint32_t i = blockIdx.x;
+  const int d = threadIdx.x;
+  const uint32_t mode = plan[i].mode;
+  if (mode != kPlanMsd && mode != kPlanWhole) return;
+  if (d < 3) s_cnt[d] = 0;
+  __syncthreads();
+  uint64_t c = 0, id = 0;
+  if (mode == kPlanMsd) {
+    id = (uint64_t)i * kRadix + d;
+    c = hist_w[id];
+  } else if (d == 0) {
+    id = (uint64_t)nseg * kRadix + i;
+    c = seg_start[i + 1] - seg_start[i];
+  }
+  const int cls = c == 0 ? -1 : c <= b0 ? 0 : c <= b1 ? 1 : c <= b2 ? 2 : -1;
+  uint32_t pos = 0;
+  if (cls >= 0) pos = atomicAdd(&s_cnt[cls], 1u);
+  __syncthreads();
+  if (d < 3 && s_cnt[d]) s_base[d] = atomicAdd(&counts[d], s_cnt[d]);
+  __syncthreads();
+  if (cls >= 0) lists[(uint64_t)cls * nseg * (kRadix + 1) + s_base[cls] + pos] = (uint32_t)id;
 }
 
 // Size classes of the bucket sort: up to 3072 pairs (256 threads x 12, 3 CTAs per
@@ -376,12 +409,25 @@ cudaError_t launch_batch(const void* keys, const uint32_t* vals, const void* src
       const unsigned grid = (unsigned)sm_count() * MB * 4;                                     \
       kern<<<grid, T, smem, s>>>((const K*)keys, vals, (const K*)src_k, src_v, seg_start, nseg, \
                                  hy.plan, hy.slot_maps, hy.hist_w, hy.offs_w, (K*)hy.out_k,    \
-                                 hy.out_v, hy.seg_base, LO, HI, dflags);                       \
+                                 hy.out_v, hy.seg_base, LO, HI,                                \
+                                 hy.buckets + (uint64_t)cls * nseg * (kRadix + 1),             \
+                                 hy.bucket_count + cls, dflags);                               \
       count_launch();                                                                          \
     }                                                                                          \
+    ++cls;                                                                                     \
   }
+  int cls = 0;
   GI_LOCAL_CLASSES(GI_BLS)
 #undef GI_BLS
+  return cudaGetLastError();
+}
+
+// ids of the classes (the bounds of GI_LOCAL_CLASSES)
+cudaError_t launch_bucket_lists(const uint64_t* seg_start, uint32_t nseg, const BatchHybrid& hy,
+                                cudaStream_t s) {
+  k_batch_bucket_lists<<<nseg, 256, 0, s>>>(hy.plan, hy.hist_w, seg_start, nseg, 3072u, 4096u,
+                                            5120u, hy.buckets, hy.bucket_count);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -426,6 +472,8 @@ cudaError_t batch_local_sort(const void* keys, const uint32_t* vals, const void*
                              int key_bytes, const BatchHybrid& hy, uint32_t* dflags,
                              cudaStream_t s) {
   if (nseg == 0) return cudaSuccess;
+  cudaError_t e = launch_bucket_lists(seg_start, nseg, hy, s);
+  if (e != cudaSuccess) return e;
   if (key_bytes == 4)
     return launch_batch_kf<uint32_t>(keys, vals, src_k, src_v, seg_start, nseg, hy, dflags, s, false);
   return launch_batch_kf<uint64_t>(keys, vals, src_k, src_v, seg_start, nseg, hy, dflags, s, false);

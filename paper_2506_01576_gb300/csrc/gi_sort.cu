@@ -1036,7 +1036,8 @@ size_t batch_sort_scratch_bytes(uint64_t ntiles, uint32_t nseg, int key_bytes) {
 size_t batch_hybrid_bytes(uint32_t nseg, uint64_t ntiles) {
   return align256(sizeof(BatchPlan) * nseg) + align256(sizeof(SlotMap) * nseg) +
          2 * align256(sizeof(uint64_t) * (uint64_t)nseg * kRadix) + 256 +
-         3 * align256(sizeof(uint32_t) * (nseg + 1)) + 2 * align256(sizeof(uint32_t) * (ntiles + 1));
+         3 * align256(sizeof(uint32_t) * (nseg + 1)) + 2 * align256(sizeof(uint32_t) * (ntiles + 1)) +
+         align256(sizeof(uint32_t) * 3 * (uint64_t)nseg * (kRadix + 1)) + 256;
 }
 
 cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], uint32_t* tmp_v[2],
@@ -1076,6 +1077,7 @@ cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], u
     const uint32_t cap = local_sort_capacity();
     e = cudaMemsetAsync(hy->hist_w, 0, sizeof(uint64_t) * (uint64_t)nseg * kRadix, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(hy->counter, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hy->bucket_count, 0, 3 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     k_batch_plan<<<nseg, 256, 0, s>>>(hist, seg_start, key_bytes, hy->k, cap, hy->plan, hy->slot_maps);
     if (key_bytes == 4)

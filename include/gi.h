@@ -253,7 +253,9 @@ int gi_coalescing_probe(const uint32_t* buf, uint64_t entries, uint32_t threads,
  *   and the per-index closed-form permutation (Sections 4, 6.1).  keys/rowids:
  *   DEVICE memory.  Asynchronous on the batch's stream, no allocation and no host
  *   synchronisation, so it can be captured in a CUDA graph.  Errors found on the
- *   device (reserved rowID, a bounded wait that gave up) come back from gi_batch_sync.
+ *   device (reserved rowID, a bounded wait that gave up) come back from gi_batch_sync,
+ *   which waits for the batch's stream and reports each such status once (the
+ *   status is cleared when it is returned).
  * gi_batch_point_lookup -- one persistent launch over (index, chunk of probes).
  *   queries: DEVICE, m probes; index b's probes are
  *   queries[query_offsets[b] .. query_offsets[b+1]); query_offsets: DEVICE array of

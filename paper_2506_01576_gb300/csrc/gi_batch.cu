@@ -414,6 +414,7 @@ int gi_batch_create(const uint64_t* key_offsets, uint32_t B, int layout, uint32_
     b->hy.list_lsd = (uint32_t*)take(sizeof(uint32_t) * (b->ntiles + 1));
     b->hy.buckets = (uint32_t*)take(sizeof(uint32_t) * 3 * (uint64_t)B * 257);
     b->hy.bucket_count = (uint32_t*)take(3 * sizeof(uint32_t));
+    b->hy.xor_or = (unsigned long long*)take(sizeof(uint64_t) * B);
     GI_B(cudaMemcpy(d_tile0, tile0.data(), sizeof(uint32_t) * (B + 1), cudaMemcpyHostToDevice), "batch tables");
     b->hy.out_k = b->keys;
     b->hy.out_v = b->rows;
@@ -511,6 +512,11 @@ int gi_batch_sync(gi_batch* b) {
   cudaError_t e = cudaMemcpyAsync(&f, b->dflags, 4, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(e, "gi_batch_sync");
+  if (f) {  // reported once: the next build starts from a clean status
+    e = cudaMemsetAsync(b->dflags, 0, 4, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(e, "gi_batch_sync: status reset");
+  }
   if (f & gi::kFlagTimeout) return bfail(GI_ERR_TIMEOUT, "a bounded device-side wait gave up");
   if (f & gi::kFlagReservedRowid) return bfail(GI_ERR_INVALID, "a rowID equals the reserved value GI_MISS");
   return GI_OK;

@@ -265,6 +265,7 @@ struct BatchHybrid {
   uint32_t* list_lsd;           // [ntiles] tiles of the kPlanLsd indexes, in order
   uint32_t* buckets;            // [3][nseg * 257] bucket ids per bucket-sort size class
   uint32_t* bucket_count;       // [3]
+  unsigned long long* xor_or;   // [nseg] OR over the index of key ^ (its first key)
   uint32_t k;                   // fan-out; 0 = sorted layout
 };
 size_t batch_hybrid_bytes(uint32_t nseg, uint64_t ntiles);  // device bytes of the tables

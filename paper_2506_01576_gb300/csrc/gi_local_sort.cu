@@ -161,15 +161,20 @@ __device__ __forceinline__ bool sort_bucket(const BucketSmem<K, ITEMS, T>& m,
                                             const K* __restrict__ src_k,
                                             const uint32_t* __restrict__ src_v, uint64_t start,
                                             uint32_t count, uint32_t top_shift, uint32_t lsd_mask,
-                                            bool single, uint32_t limit) {
+                                            bool single, uint32_t limit, bool check_rows,
+                                            uint32_t* __restrict__ flags) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t items = (count + T - 1) / T;  // <= ITEMS
   const uint32_t used = items * T;
+  bool bad = false;  // an input rowID equal to the reserved miss value
   for (uint32_t j = tid; j < used; j += T) {
     const bool in = j < count;
     m.s_k[j] = in ? src_k[start + j] : ~K(0);  // padding sorts last, stably
-    m.s_v[j] = in ? src_v[start + j] : 0u;
+    const uint32_t v = in ? src_v[start + j] : 0u;
+    bad |= check_rows && in && v == GI_MISS;
+    m.s_v[j] = v;
   }
+  if (check_rows && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, kFlagReservedRowid);
   __syncthreads();
   // the top window first; if a sub-bucket is too big for count ranking, every
   // byte of lsd_mask again in LSD order (one pass loop keeps one copy of the
@@ -241,7 +246,7 @@ __global__ void __launch_bounds__(T, MINB) k_local_sort(
   for (uint64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
     const BatchTile seg = segs[sg];
     const bool direct = sort_bucket<K, ITEMS, T>(m, src_k, src_v, seg.start, seg.count, 8u * top,
-                                                 local_mask, single, limit);
+                                                 local_mask, single, limit, false, flags);
     // sorted position j -> rank seg.start + j -> its slot in the layout
     for (uint32_t j = tid; j < seg.count; j += T) {
       const uint32_t p = direct ? j : m.s_src[j];
@@ -294,8 +299,10 @@ __global__ void __launch_bounds__(T, MINB) k_batch_local_sort(
       if (tid < (int)(sizeof(SlotMap) / 4)) ((uint32_t*)&s_map)[tid] = ((const uint32_t*)&maps[i])[tid];
     }
     const uint32_t limit = 8u * (uint32_t)__popc(pl.lsd_mask) + 8u;
+    // a whole index is read straight from the input: its rowIDs are checked here
     const bool direct = sort_bucket<K, ITEMS, T>(m, msd ? src_k : keys, msd ? src_v : vals, start,
-                                                 count, pl.ts, pl.lsd_mask, false, limit);
+                                                 count, pl.ts, pl.lsd_mask, false, limit, !msd,
+                                                 flags);
     const uint64_t base = seg_base[i];
     const uint32_t r0 = (uint32_t)(start - s0);
     for (uint32_t j = tid; j < count; j += T) {

@@ -403,18 +403,22 @@ inline int grid_for(uint64_t work, int block, int per_sm = 8) {
 // look-back stops at its index's first tile, and each index has its own digit
 // offsets, so keys never leave their index (a segmented LSD sort).
 
+// plan != NULL: only the indexes of plan kPlanLsd, and no rowID check (their
+// first LSD pass checks them)
 template <class K>
 __global__ void __launch_bounds__(256) k_batch_histogram(const K* __restrict__ keys,
                                                          const uint32_t* __restrict__ rows,
                                                          const BatchTile* __restrict__ chunks,
                                                          uint64_t nchunks,
                                                          unsigned long long* __restrict__ hist,
-                                                         uint32_t* __restrict__ flags) {
+                                                         uint32_t* __restrict__ flags,
+                                                         const BatchPlan* __restrict__ plan) {
   constexpr int P = sizeof(K);
   __shared__ uint32_t sh[P][kRadix];
   bool bad = false;
   for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const BatchTile t = chunks[c];
+    if (plan && plan[t.seg].mode != kPlanLsd) continue;
     for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
     __syncthreads();
     const K* kp = keys + t.start;
@@ -426,7 +430,7 @@ __global__ void __launch_bounds__(256) k_batch_histogram(const K* __restrict__ k
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         kk[u] = kp[i + u * blockDim.x];
-        rr[u] = rp[i + u * blockDim.x];
+        rr[u] = plan ? 0u : rp[i + u * blockDim.x];
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -439,7 +443,7 @@ __global__ void __launch_bounds__(256) k_batch_histogram(const K* __restrict__ k
       const K key = kp[i];
 #pragma unroll
       for (int p = 0; p < P; ++p) atomicAdd(&sh[p][(uint32_t)(key >> (8 * p)) & 0xFF], 1u);
-      bad |= rp[i] == GI_MISS;
+      bad |= !plan && rp[i] == GI_MISS;
     }
     __syncthreads();
     unsigned long long* h = hist + (uint64_t)t.seg * P * kRadix;
@@ -485,7 +489,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_batch_sort_pass(
     const unsigned long long* __restrict__ offs, int pass, int passes,
     uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter, uint32_t epoch,
     uint32_t* __restrict__ flags, const BatchPlan* __restrict__ plan, uint32_t want,
-    uint32_t window, TileMap map) {
+    uint32_t window, TileMap map, uint32_t check_rows) {
   constexpr int ITEMS = SortTile<K>::kItems;
   constexpr int TILE = kSortThreads * ITEMS;
   union HistOrVals {
@@ -617,11 +621,15 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_batch_sort_pass(
     s_keys[rnk[i]] = key[i];
   }
   __syncthreads();
+  bool bad = false;  // a rowID equal to the reserved miss value (passes that read the input)
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint32_t e = wofs + i * 32;
-    hv.vals[rnk[i]] = e < valid ? src_v[tile_base + e] : 0u;
+    const uint32_t v = e < valid ? src_v[tile_base + e] : 0u;
+    bad |= check_rows && e < valid && v == GI_MISS;
+    hv.vals[rnk[i]] = v;
   }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, kFlagReservedRowid);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
@@ -677,41 +685,58 @@ __global__ void __launch_bounds__(256) k_batch_gather(const K* __restrict__ sk,
 }
 
 // ---------------------------------------------------------------- hybrid batch build
-// One CTA per index: from its digit histograms, the bytes in which its keys differ,
-// the highest such bit hb, and the plan: at most `cap` pairs -> one CTA sorts the
-// whole index (top window = its 8 highest significant bits); more -> one stable
-// scatter on bits [hb-7, hb] (the MSD window), then buckets with the next 8 bits as
-// their top window.  The k-ary slot map of the index goes to maps[i].
-__global__ void __launch_bounds__(256) k_batch_plan(const unsigned long long* __restrict__ hist,
+// OR over every index of key ^ (the index's first key): its set bits are the bits
+// in which two keys of the index differ.  One 64-bit atomic per CTA and chunk.
+template <class K>
+__global__ void __launch_bounds__(256) k_batch_xor(const K* __restrict__ keys,
+                                                   const BatchTile* __restrict__ chunks,
+                                                   uint64_t nchunks,
+                                                   const uint64_t* __restrict__ seg_start,
+                                                   unsigned long long* __restrict__ xor_or) {
+  __shared__ unsigned long long s_or[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const BatchTile t = chunks[c];
+    const K k0 = keys[seg_start[t.seg]];
+    const K* kp = keys + t.start;
+    K acc = 0;
+    uint32_t i = threadIdx.x;
+    for (; i + 3 * blockDim.x < t.count; i += 4 * blockDim.x)  // four loads in flight
+      acc |= (kp[i] ^ k0) | (kp[i + blockDim.x] ^ k0) | (kp[i + 2 * blockDim.x] ^ k0) |
+             (kp[i + 3 * blockDim.x] ^ k0);
+    for (; i < t.count; i += blockDim.x) acc |= kp[i] ^ k0;
+    unsigned long long x = (unsigned long long)acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s_or[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long y = 0;
+      for (int j = 0; j < (int)(blockDim.x >> 5); ++j) y |= s_or[j];
+      if (y) atomicOr(&xor_or[t.seg], y);
+    }
+    __syncthreads();
+  }
+}
+
+// One thread per index: from the bits in which its keys differ (highest: hb), the
+// plan: at most `cap` pairs -> one CTA sorts the whole index (top window = its 8
+// highest significant bits); more -> one stable scatter on a window of w bits
+// ending at hb (the MSD window), then buckets with the next 8 bits as their top
+// window.  The k-ary slot map of the index goes to maps[i].
+__global__ void __launch_bounds__(256) k_batch_plan(const unsigned long long* __restrict__ xor_or,
                                                     const uint64_t* __restrict__ seg_start,
-                                                    int key_bytes, uint32_t k, uint32_t cap,
-                                                    BatchPlan* __restrict__ plan,
+                                                    uint32_t nseg, int key_bytes, uint32_t k,
+                                                    uint32_t cap, BatchPlan* __restrict__ plan,
                                                     SlotMap* __restrict__ maps) {
-  __shared__ int s_lo[8], s_hi[8];
-  const uint32_t i = blockIdx.x;
-  const int d = threadIdx.x;
-  if (d < 8) {
-    s_lo[d] = kRadix;
-    s_hi[d] = -1;
-  }
-  __syncthreads();
-  for (int p = 0; p < key_bytes; ++p) {
-    if (hist[((uint64_t)i * key_bytes + p) * kRadix + d]) {
-      atomicMin(&s_lo[p], d);
-      atomicMax(&s_hi[p], d);
-    }
-  }
-  __syncthreads();
-  if (d != 0) return;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nseg) return;
   const uint64_t n = seg_start[i + 1] - seg_start[i];
+  const unsigned long long x = n ? xor_or[i] : 0ull;
   BatchPlan pl{};
-  int hb = -1;  // highest bit in which two keys differ
-  for (int p = key_bytes - 1; p >= 0; --p) {
-    if (s_hi[p] > s_lo[p]) {
-      pl.lsd_mask |= 1u << p;
-      if (hb < 0) hb = 8 * p + (31 - __clz((uint32_t)(s_lo[p] ^ s_hi[p])));
-    }
-  }
+  for (int p = 0; p < key_bytes; ++p)
+    if ((x >> (8 * p)) & 0xFF) pl.lsd_mask |= 1u << p;
+  const int hb = x ? 63 - __clzll((long long)x) : -1;  // highest bit in which two keys differ
   if (n == 0) {
     pl.mode = kPlanEmpty;
   } else if (n <= cap) {
@@ -1037,7 +1062,8 @@ size_t batch_hybrid_bytes(uint32_t nseg, uint64_t ntiles) {
   return align256(sizeof(BatchPlan) * nseg) + align256(sizeof(SlotMap) * nseg) +
          2 * align256(sizeof(uint64_t) * (uint64_t)nseg * kRadix) + 256 +
          3 * align256(sizeof(uint32_t) * (nseg + 1)) + 2 * align256(sizeof(uint32_t) * (ntiles + 1)) +
-         align256(sizeof(uint32_t) * 3 * (uint64_t)nseg * (kRadix + 1)) + 256;
+         align256(sizeof(uint32_t) * 3 * (uint64_t)nseg * (kRadix + 1)) + 256 +
+         align256(sizeof(uint64_t) * nseg);
 }
 
 cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], uint32_t* tmp_v[2],
@@ -1063,43 +1089,60 @@ cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], u
   const int hgrid = (int)std::min<uint64_t>(nchunks, (uint64_t)sm_count() * 8);
   // persistent radix grids: the 4 CTAs per SM the pass fits
   const unsigned pgrid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count() * 4);
-  if (key_bytes == 4)
-    k_batch_histogram<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)keys, vals, chunks, nchunks, hist, dflags);
-  else
-    k_batch_histogram<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)keys, vals, chunks, nchunks, hist, dflags);
-  k_batch_scan_hist<<<nseg, 256, 0, s>>>(hist, offs, seg_start, passes);
-  count_launch(2);
   const BatchPlan* plan = nullptr;
-  if (hy) {
-    // per-index plans, the MSD window counts, the MSD scatter into tmp[1] and the
-    // bucket sort, which writes the layouts of those indexes
+  if (!hy) {  // the plain segmented LSD sort: digit histograms of every index
+    if (key_bytes == 4)
+      k_batch_histogram<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)keys, vals, chunks, nchunks, hist, dflags, nullptr);
+    else
+      k_batch_histogram<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)keys, vals, chunks, nchunks, hist, dflags, nullptr);
+    k_batch_scan_hist<<<nseg, 256, 0, s>>>(hist, offs, seg_start, passes);
+    count_launch(2);
+  } else {
+    // per-index plans from the bits in which each index's keys differ, the MSD
+    // window counts, then the digit histograms of the indexes that fall back to the
+    // LSD passes only; then the MSD scatter into tmp[1] and the bucket sort, which
+    // writes the layouts of those indexes.  The rowIDs are checked by the kernels
+    // that read the input: the MSD pass, the bucket sort of whole indexes, the
+    // first LSD pass.
     plan = hy->plan;
     const uint32_t cap = local_sort_capacity();
     e = cudaMemsetAsync(hy->hist_w, 0, sizeof(uint64_t) * (uint64_t)nseg * kRadix, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(hy->counter, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(hy->bucket_count, 0, 3 * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hy->xor_or, 0, sizeof(uint64_t) * nseg, s);
     if (e != cudaSuccess) return e;
-    k_batch_plan<<<nseg, 256, 0, s>>>(hist, seg_start, key_bytes, hy->k, cap, hy->plan, hy->slot_maps);
+    if (key_bytes == 4)
+      k_batch_xor<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)keys, chunks, nchunks, seg_start, hy->xor_or);
+    else
+      k_batch_xor<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)keys, chunks, nchunks, seg_start, hy->xor_or);
+    k_batch_plan<<<(nseg + 255) / 256, 256, 0, s>>>(hy->xor_or, seg_start, nseg, key_bytes, hy->k, cap,
+                                                   hy->plan, hy->slot_maps);
     if (key_bytes == 4)
       k_batch_window_hist<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)keys, chunks, nchunks, hy->plan, hy->hist_w);
     else
       k_batch_window_hist<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)keys, chunks, nchunks, hy->plan, hy->hist_w);
     k_batch_window_scan<<<nseg, 256, 0, s>>>(hy->hist_w, hy->offs_w, seg_start, cap, hy->plan);
+    if (key_bytes == 4)
+      k_batch_histogram<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)keys, vals, chunks, nchunks, hist, dflags, hy->plan);
+    else
+      k_batch_histogram<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)keys, vals, chunks, nchunks, hist, dflags, hy->plan);
+    k_batch_scan_hist<<<nseg, 256, 0, s>>>(hist, offs, seg_start, passes);
+    count_launch(6);
     k_batch_mode_prefix<<<1, 1024, 0, s>>>(hy->plan, hy->tile0, nseg, hy->prefix_msd, hy->prefix_lsd);
     k_batch_mode_lists<<<nseg, 256, 0, s>>>(hy->plan, hy->tile0, hy->prefix_msd, hy->prefix_lsd,
                                             hy->list_msd, hy->list_lsd);
-    count_launch(5);
+    count_launch(2);
     // persistent grid over the tiles of the kPlanMsd indexes only; the status
     // array is shared with the LSD passes: a distinct epoch (9)
     const TileMap msd_map{hy->list_msd, hy->prefix_msd + nseg};
     if (key_bytes == 4)
       k_batch_sort_pass<uint32_t><<<pgrid, kSortThreads, 0, s>>>(
           (const uint32_t*)keys, vals, (uint32_t*)tmp_k[1], tmp_v[1], n, 0u, tiles, hy->offs_w, 0,
-          1, status, hy->counter, 9u, dflags, hy->plan, kPlanMsd, 1u, msd_map);
+          1, status, hy->counter, 9u, dflags, hy->plan, kPlanMsd, 1u, msd_map, 1u);
     else
       k_batch_sort_pass<uint64_t><<<pgrid, kSortThreads, 0, s>>>(
           (const uint64_t*)keys, vals, (uint64_t*)tmp_k[1], tmp_v[1], n, 0u, tiles, hy->offs_w, 0,
-          1, status, hy->counter, 9u, dflags, hy->plan, kPlanMsd, 1u, msd_map);
+          1, status, hy->counter, 9u, dflags, hy->plan, kPlanMsd, 1u, msd_map, 1u);
     count_launch();
     e = batch_local_sort(keys, vals, tmp_k[1], tmp_v[1], seg_start, nseg, key_bytes, *hy, dflags, s);
     if (e != cudaSuccess) return e;
@@ -1117,11 +1160,13 @@ cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], u
     if (key_bytes == 4)
       k_batch_sort_pass<uint32_t><<<grid, kSortThreads, 0, s>>>(
           (const uint32_t*)ck, cv, (uint32_t*)tmp_k[dst], tmp_v[dst], n, 8u * ps, tiles, offs, ps,
-          passes, status, counter + ps, (uint32_t)ps + 1, dflags, plan, kPlanLsd, 0u, lsd_map);
+          passes, status, counter + ps, (uint32_t)ps + 1, dflags, plan, kPlanLsd, 0u, lsd_map,
+          (hy && ps == 0) ? 1u : 0u);
     else
       k_batch_sort_pass<uint64_t><<<grid, kSortThreads, 0, s>>>(
           (const uint64_t*)ck, cv, (uint64_t*)tmp_k[dst], tmp_v[dst], n, 8u * ps, tiles, offs, ps,
-          passes, status, counter + ps, (uint32_t)ps + 1, dflags, plan, kPlanLsd, 0u, lsd_map);
+          passes, status, counter + ps, (uint32_t)ps + 1, dflags, plan, kPlanLsd, 0u, lsd_map,
+          (hy && ps == 0) ? 1u : 0u);
     count_launch();
     ck = tmp_k[dst];
     cv = tmp_v[dst];
@@ -1285,11 +1330,11 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
     if (key_bytes == 4)
       k_batch_sort_pass<uint32_t><<<(unsigned)tiles.size(), kSortThreads, 0, s>>>(
           (const uint32_t*)bk[cur], bv[cur], (uint32_t*)bk[dst2], bv[dst2], n, 8u * d2, d_tiles,
-          d_offs, 0, 1, v.status, d_counter, 40u, dflags, nullptr, 0u, 0u, TileMap{});
+          d_offs, 0, 1, v.status, d_counter, 40u, dflags, nullptr, 0u, 0u, TileMap{}, 0u);
     else
       k_batch_sort_pass<uint64_t><<<(unsigned)tiles.size(), kSortThreads, 0, s>>>(
           (const uint64_t*)bk[cur], bv[cur], (uint64_t*)bk[dst2], bv[dst2], n, 8u * d2, d_tiles,
-          d_offs, 0, 1, v.status, d_counter, 40u, dflags, nullptr, 0u, 0u, TileMap{});
+          d_offs, 0, 1, v.status, d_counter, 40u, dflags, nullptr, 0u, 0u, TileMap{}, 0u);
     count_launch();
     cur = dst2;
     cudaFreeAsync(blob, s);

@@ -234,3 +234,35 @@ def test_batch_degenerate_shapes(sizes):
     gi.gi_batch_sync(batch)
     _check(batch, keys, rows, qs, qoff, out, gi.GI_EYTZINGER_KARY, 9)
     gi.gi_batch_destroy(batch)
+
+
+@pytest.mark.parametrize("bits", [64, 32])
+def test_batch_reserved_rowid_reported_by_sync(bits):
+    # the reserved rowID is found in whichever pass first reads the caller's rowIDs:
+    # the bucket sort of a whole index, the MSD scatter, or the first LSD pass
+    dt = np.uint64 if bits == 64 else np.uint32
+    keys = [W.unique_keys(3000, bits, 1),                                  # whole
+            W.unique_keys(60000, bits, 2),                                 # MSD
+            np.concatenate([np.arange(9000, dtype=dt), np.array([np.iinfo(dt).max], dt)]),  # LSD
+            np.full(6000, 12345, dt)]                                      # all equal: LSD
+    off = np.zeros(len(keys) + 1, dtype=np.uint64)
+    np.cumsum(np.array([len(x) for x in keys], dtype=np.uint64), out=off[1:])
+    flag = gi.GI_KEY_U64 if bits == 64 else gi.GI_KEY_U32
+    batch = gi.gi_batch_create(off, gi.GI_EYTZINGER_KARY | flag, 5)
+    kd = to_dev(np.concatenate(keys))
+    for bad in range(len(keys)):
+        rows = [np.arange(len(x), dtype=np.uint32) for x in keys]
+        rows[bad][len(keys[bad]) // 2] = gi.GI_MISS
+        gi.gi_batch_build(batch, kd, to_dev(np.concatenate(rows)))
+        with pytest.raises(gi.GIError) as e:
+            gi.gi_batch_sync(batch)
+        assert e.value.code == gi.GI_ERR_INVALID, bad
+    # reported once; a clean build afterwards syncs without error and is correct
+    rows = [np.random.default_rng(i).permutation(len(x)).astype(np.uint32) for i, x in enumerate(keys)]
+    gi.gi_batch_build(batch, kd, to_dev(np.concatenate(rows)))
+    qs, qoff = _probes(keys, bits, [2000] * len(keys), 23)
+    out = torch.full((int(qoff[-1]),), -5, dtype=torch.int32, device=DEV)
+    gi.gi_batch_point_lookup(batch, to_dev(np.concatenate(qs)), to_dev(qoff), out)
+    gi.gi_batch_sync(batch)
+    _check(batch, keys, rows, qs, qoff, out, gi.GI_EYTZINGER_KARY, 5)
+    gi.gi_batch_destroy(batch)

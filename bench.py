@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="timed steps only (for profiler launch lists)")
     ap.add_argument("--workload", default="point",
-                    choices=["point", "batched", "ranges", "dups", "skew", "serve", "sizes"],
+                    choices=["point", "batched", "ranges", "dups", "skew", "serve", "sizes", "tune"],
                     help="point: the 2^26-key step (default); batched: 4096 indexes in one graph; "
                          "ranges: 2^24 ranges on 2^26 u32 keys; dups: replicated keys, point = range [x, x]")
     ap.add_argument("--batch-k", type=int, default=5)
@@ -388,7 +388,7 @@ def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, 
     bpl, reqs = eks_bytes_per_lookup(n, a.k, 8, 0.5, l2)
     achieved = bpl * m / (pt_ms / 1e3) / 1e9
     res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                       "frac": achieved / hbm, "traffic": recorded_traffic(a, m, opts["hot_levels"]),
+                       "frac": achieved / hbm, "traffic": recorded_traffic(a, m, opts["hot_levels"], opts["block"]),
                        "peak_source": "measured" if peaks else "fallback",
                        "kernel": "k_eks_point", "algorithmic_bytes_per_lookup": bpl,
                        "random_requests_per_lookup": reqs, "l2_bytes": l2}
@@ -446,11 +446,11 @@ def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, 
     return res
 
 
-def recorded_traffic(a, m, hot_levels):
+def recorded_traffic(a, m, hot_levels, block):
     """DRAM bytes of one k_eks_point launch from the committed ncu summary, or None.
 
     Valid only for the configuration it was captured on (2^26 u64 keys, k = 5,
-    2^27 probes, default knobs, the same number of evict-last levels) and while
+    2^27 probes, default knobs, the same number of evict-last levels and block size) and while
     the kernel source is unchanged.
     """
     import hashlib
@@ -461,13 +461,13 @@ def recorded_traffic(a, m, hot_levels):
         txt = open(os.path.join(ROOT, "profiles", "k_eks_point_u64_k5_2e26.md")).read()
         rec = dict(l.split(": ", 1) for l in txt.splitlines()
                    if l.startswith(("traffic_full_launch_bytes:", "kernel_source_sha256:",
-                                    "hot_levels:")))
+                                    "hot_levels:", "block:")))
         h = hashlib.sha256()
         for f in ("gi_point_impl.cuh", "gi_eks_inst.cuh"):
             h.update(open(os.path.join(ROOT, "paper_2506_01576_gb300", "csrc", f), "rb").read())
         if h.hexdigest() != rec["kernel_source_sha256"].strip():
             return None
-        if int(rec["hot_levels"]) != int(hot_levels):
+        if int(rec["hot_levels"]) != int(hot_levels) or int(rec["block"]) != int(block):
             return None
         return int(rec["traffic_full_launch_bytes"])
     except Exception:
@@ -659,6 +659,14 @@ def run_batched(a):
     got = out.cpu().numpy().view(np.uint32)
     lookup_ms = ev(lambda: gi.gi_batch_point_lookup(batch, qd, qod, out), a.steps)
     build_ms = ev(lambda: gi.gi_batch_build(batch, kd, rd), max(2, a.steps // 2))
+    tuned = None
+    if not a.no_extras:  # the autotuner on the same probes (the graph keeps the defaults)
+        r = gi.gi_batch_tune(batch, qd, qod)
+        names = {gi.GI_BATCH_OPT_CHUNK: "chunk", gi.GI_BATCH_OPT_BLOCKS_PER_SM: "blocks_per_sm",
+                 gi.GI_BATCH_OPT_SMEM_BUDGET: "smem_budget"}
+        tuned = {"lookup_ms": ev(lambda: gi.gi_batch_point_lookup(batch, qd, qod, out), a.steps),
+                 "start": {v: int(r.start_options[o]) for o, v in names.items()},
+                 "chosen": {v: int(r.options[o]) for o, v in names.items()}, "trials": int(r.trials)}
     # one index at a time through the single-index API
     gi.gi_set_stream(None, s)
     out2 = torch.empty(m, dtype=torch.int32, device=dev)
@@ -671,12 +679,14 @@ def run_batched(a):
             gi.gi_point_lookup(idx, qd[q0:q1], out2[q0:q1])
             gi.gi_destroy(idx)
 
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    per_index()
-    torch.cuda.synchronize()
-    per_ms = (time.perf_counter() - t0) * 1e3
-    same = bool(np.array_equal(got, out2.cpu().numpy().view(np.uint32)))
+    per_ms, same = None, None
+    if not a.no_extras:  # thousands of launches: left out of profiler launch lists
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        per_index()
+        torch.cuda.synchronize()
+        per_ms = (time.perf_counter() - t0) * 1e3
+        same = bool(np.array_equal(got, out2.cpu().numpy().view(np.uint32)))
     gi.gi_set_stream(None, None)
     print(json.dumps({
         "metric": "batched lookups/s (%d indexes, 2^8..2^20 u64 keys, 2^10..2^18 probes each, hit 0.75)" % B,
@@ -685,8 +695,8 @@ def run_batched(a):
         "config": {"workload": "batched build + lookup, one CUDA graph", "indexes": B,
                    "keys_total": int(off[-1]), "probes_total": m, "k": a.batch_k},
         "graph_step_ms": graph_ms, "build_ms": build_ms, "lookup_ms": lookup_ms,
-        "lookup_only_per_s": m / (lookup_ms / 1e3),
-        "per_index_launches_ms": per_ms, "speedup_vs_per_index": per_ms / graph_ms,
+        "lookup_only_per_s": m / (lookup_ms / 1e3), "lookup_tuned": tuned,
+        "per_index_launches_ms": per_ms, "speedup_vs_per_index": per_ms and per_ms / graph_ms,
         "per_index_results_identical": same, "gpu_launches": int(launches),
         "clocks": clk.summary()}), flush=True)
     gi.gi_batch_destroy(batch)
@@ -784,6 +794,56 @@ def run_sizes(a):
                 torch, lambda: gi.gi_destroy(gi.gi_build(kd, rd, lay | U, k)), max(3, a.steps // 3))
         print(json.dumps(line), flush=True)
         del kd, rd, qd
+
+
+_OPT_NAMES = {1: "group", 2: "per_thread", 3: "smem_levels", 4: "block", 5: "blocks_per_sm",
+              6: "prefetch", 7: "early_exit", 8: "hot_levels", 9: "range_fill", 10: "reorder"}
+
+
+def run_tune(a):
+    """The autotuner (gi_tune) over the index size: n = 2^10 .. 2^28 unique u64 keys
+    (even powers), 2^27 probes (hit rate 0.5, uniform); BS, EBS and EKS k = 5, 9, 17,
+    each timed with the default knobs and with the knobs gi_tune picks on a 2^22-probe
+    sample, and the fastest layout per size either way (the paper's composite
+    strategy, Section 9).  One JSON line per size."""
+    import torch
+
+    import paper_2506_01576_gb300 as gi
+    gi.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    m = 1 << a.m_log
+    out = torch.empty(m, dtype=torch.int32, device=dev)
+    for nl in range(10, 29, 2):
+        n = 1 << nl
+        seed = W.seed_for(5, nl)
+        keys = W.unique_keys(n, 64, seed)
+        q = W.point_probes(keys, m, 0.5, 64, seed, seed + 1)
+        kd = torch.from_numpy(keys.view(np.int64)).to(dev)
+        rd = torch.arange(n, dtype=torch.int32, device=dev)
+        qd = torch.from_numpy(q.view(np.int64)).to(dev)
+        sample = qd[: min(m, 1 << 22)]
+        line = {"workload": "tune", "n_log": nl, "probes": m, "tune_sample": int(sample.numel()),
+                "default": {}, "tuned": {}, "knobs": {}, "trials": {}, "tune_s": {}}
+        for name, lay, k in (("BS", gi.GI_SORTED, 0), ("EBS", gi.GI_EYTZINGER, 0),
+                             ("EKS5", gi.GI_EYTZINGER_KARY, 5), ("EKS9", gi.GI_EYTZINGER_KARY, 9),
+                             ("EKS17", gi.GI_EYTZINGER_KARY, 17)):
+            idx = gi.gi_build(kd, rd, lay | gi.GI_KEY_U64, k)
+            ms = _ev_ms(torch, lambda: gi.gi_point_lookup(idx, qd, out), a.steps)
+            line["default"][name] = m / ms * 1e3
+            t0 = time.perf_counter()
+            r = gi.gi_tune(idx, sample, 0, gi.GI_TUNE_APPLY)
+            line["tune_s"][name] = time.perf_counter() - t0
+            ms = _ev_ms(torch, lambda: gi.gi_point_lookup(idx, qd, out), a.steps)
+            line["tuned"][name] = m / ms * 1e3
+            line["knobs"][name] = {_OPT_NAMES[o]: int(r.options[o]) for o in range(1, 11)
+                                   if r.options[o] != r.start_options[o]}
+            line["trials"][name] = int(r.trials)
+            gi.gi_destroy(idx)
+        line["fastest_default"] = max(line["default"], key=line["default"].get)
+        line["fastest_tuned"] = max(line["tuned"], key=line["tuned"].get)
+        print(json.dumps(line), flush=True)
+        del kd, rd, qd, sample
 
 
 def run_dups(a):
@@ -987,6 +1047,8 @@ if __name__ == "__main__":
         run_batched(args)
     elif args.workload == "sizes":
         run_sizes(args)
+    elif args.workload == "tune":
+        run_tune(args)
     elif args.probe_sweep:
         probe_sweep()
     elif args.impl == "reference":

@@ -62,11 +62,11 @@ typedef struct gi_index gi_index;
  *                    sort: stable scatters on the top two non-trivial digits, then
  *                    every resulting bucket sorted in one CTA's shared memory and
  *                    written straight into the layout.  Smaller or narrower inputs,
- *                    and inputs whose buckets come out larger than 4096 pairs,
+ *                    and inputs whose buckets come out larger than 5120 pairs,
  *                    take the plain LSD sort.
  *   GI_BUILD_LSD     always the plain 8-bit LSD radix passes (then the permutation).
  *   GI_BUILD_HYBRID  the hybrid sort whenever it can run (at least two non-trivial
- *                    digits, n < 2^32, buckets of at most 4096 pairs), whatever n
+ *                    digits, n < 2^32, buckets of at most 5120 pairs), whatever n
  *                    and the key width; else the LSD sort. */
 #define GI_BUILD_LSD 0x10000
 #define GI_BUILD_HYBRID 0x20000
@@ -184,7 +184,7 @@ int gi_copy_layout(const gi_index* index, void* keys_out, uint32_t* rowids_out);
  *                       lookup, "EKS (single)"; up to 32; must be supported for k).
  *   GI_OPT_PER_THREAD   independent lookups interleaved per thread/group: 1, 2, 4.
  *   GI_OPT_SMEM_LEVELS  top tree levels pinned in shared memory (0 = none).
- *   GI_OPT_BLOCK        threads per block: 128, 256, 512, 1024.
+ *   GI_OPT_BLOCK        threads per block: 64, 128, 256, 512.
  *   GI_OPT_BLOCKS_PER_SM  0 = one thread (group) per work item; >0 = persistent grid
  *                       of that many blocks per SM with a static schedule.
  *   GI_OPT_PREFETCH     EYTZINGER prefetch distance in levels: 0, 2, 3, 4.
@@ -194,7 +194,7 @@ int gi_copy_layout(const gi_index* index, void* keys_out, uint32_t* rowids_out);
  *   GI_OPT_HOT_LEVELS   EYTZINGER_KARY: top levels read with an L2 evict-last hint;
  *                       deeper levels, rowIDs, probes and results use evict-first
  *                       (0 = every level streamed).  Default: the levels whose keys
- *                       fit in two thirds of L2.
+ *                       fit in a quarter of L2.
  *   GI_OPT_RANGE_FILL   Eytzinger layouts: 1 writes a range's rows level by level,
  *                       one contiguous slot run per level, a warp taking runs of
  *                       >= 32 slots (Sections 5, 5.1); 0 (default) maps every rank
@@ -216,6 +216,50 @@ int gi_copy_layout(const gi_index* index, void* keys_out, uint32_t* rowids_out);
 #define GI_OPT_REORDER       10
 int gi_set_option(gi_index* index, int option, int64_t value);
 int gi_get_option(const gi_index* index, int option, int64_t* value);
+
+/*
+ * Autotuner.  The paper picks block size, lookups per thread, limited concurrency,
+ * pinned levels, prefetch distance, lane-group size and lookup reordering by sweeps
+ * per figure (Sections 7.2-7.4, 8.2-8.4); this runs such a sweep on the caller's own
+ * index and probes.
+ *
+ * gi_tune -- times point lookups of the DEVICE probes queries[0..m) under candidate
+ *   values of the knobs that apply to the index's layout (GI_OPT_GROUP, PER_THREAD,
+ *   BLOCK, BLOCKS_PER_SM, SMEM_LEVELS alone and paired with a persistent grid,
+ *   PREFETCH, HOT_LEVELS, EARLY_EXIT, REORDER) by coordinate descent: from the
+ *   index's current settings, each knob in turn takes its fastest candidate with the
+ *   others held; the sweep repeats until a pass changes nothing (at most 3 passes).
+ *   A change is kept only if it is at least 1% faster.  Each timing is one untimed
+ *   run and `reps` runs timed with CUDA events on the index's stream, the best kept
+ *   (reps = 0: 5).  The knobs change the schedule only, never a lookup's result.
+ *   flags: GI_TUNE_APPLY sets the chosen values on the index (otherwise its settings
+ *   are restored); GI_TUNE_RECORD stores them in a process-wide table keyed by (key
+ *   width, layout, k, floor(log2 n)), from which every index of that class takes
+ *   the knobs it leaves automatic (-1).
+ *   out (may be NULL): the values on entry and the chosen values, indexed by
+ *   GI_OPT_* (-1 where the knob does not apply), and their times.
+ *   Allocates m uint32 of device scratch for the call.  Synchronous.
+ *   Errors: GI_ERR_INVALID (NULL index, m == 0, host probes, unknown flags),
+ *   GI_ERR_NOMEM, GI_ERR_CUDA, GI_ERR_TIMEOUT.  On error the settings are restored.
+ * gi_tune_table_get -- the table's entry for (layout | key width, k, n):
+ *   options[o], o = 1..10, or -1 where nothing is recorded; *found = 1 if the class
+ *   has an entry.  options: 11 int64.
+ * gi_tune_table_clear -- empties the table.
+ */
+#define GI_TUNE_APPLY  1
+#define GI_TUNE_RECORD 2
+typedef struct gi_tune_result {
+  int64_t start_options[11]; /* [GI_OPT_*] on entry; [0] unused (-1)          */
+  int64_t options[11];       /* [GI_OPT_*] chosen                             */
+  double start_ms;           /* best time of the settings on entry            */
+  double best_ms;            /* best time of the chosen settings              */
+  uint32_t trials;           /* settings timed                                */
+  uint32_t passes;           /* coordinate-descent passes                     */
+} gi_tune_result;
+int gi_tune(gi_index* index, const void* queries, uint64_t m, uint32_t reps, int flags,
+            gi_tune_result* out);
+int gi_tune_table_get(int layout, uint32_t k, uint64_t n, int64_t* options, int* found);
+void gi_tune_table_clear(void);
 
 /*
  * gi_probe_random_sectors -- roofline probe: `loads` loads of `chunk_bytes`
@@ -264,9 +308,10 @@ int gi_coalescing_probe(const uint32_t* buf, uint64_t entries, uint32_t threads,
  *   (a bulk asynchronous copy; whole small indexes), up to a per-CTA budget.
  *   Asynchronous, no allocation, capturable.
  * gi_batch_copy_index -- copy index b's arrays in layout order (device or host).
- * gi_batch_set_option -- GI_BATCH_OPT_CHUNK (probes per work item, default 1024),
- *   GI_BATCH_OPT_BLOCKS_PER_SM (default 4), GI_BATCH_OPT_SMEM_BUDGET (bytes of
- *   pinned levels per CTA, 0..40960, default 16384).
+ * gi_batch_set_option -- GI_BATCH_OPT_CHUNK (probes per work item, default 2048),
+ *   GI_BATCH_OPT_BLOCKS_PER_SM (default 8), GI_BATCH_OPT_SMEM_BUDGET (bytes of
+ *   pinned levels per CTA, 0..40960, default 0: no pinning).  The defaults are
+ *   gi_batch_tune's choice on 4096 indexes of 2^8..2^20 u64 keys.
  */
 typedef struct gi_batch gi_batch;
 #define GI_BATCH_OPT_CHUNK         1
@@ -282,6 +327,18 @@ int gi_batch_sync(gi_batch* batch);
 int gi_batch_copy_index(const gi_batch* batch, uint32_t i, void* keys_out, uint32_t* rowids_out);
 int gi_batch_set_option(gi_batch* batch, int option, int64_t value);
 uint64_t gi_batch_footprint_bytes(const gi_batch* batch);
+/*
+ * gi_batch_tune -- the autotuner for the batched lookup: times
+ *   gi_batch_point_lookup(batch, queries, query_offsets, m, .) (arguments as there,
+ *   DEVICE memory) under GI_BATCH_OPT_CHUNK, GI_BATCH_OPT_BLOCKS_PER_SM and
+ *   GI_BATCH_OPT_SMEM_BUDGET candidates by the coordinate descent of gi_tune, and
+ *   leaves the fastest values set on the batch.  out (may be NULL): values on entry
+ *   and chosen, indexed by GI_BATCH_OPT_*.  Allocates m uint32 of device scratch.
+ *   Synchronous; the batch must be built.  Errors: as gi_batch_point_lookup and
+ *   gi_batch_sync; on error the values on entry are restored.
+ */
+int gi_batch_tune(gi_batch* batch, const void* queries, const uint64_t* query_offsets, uint64_t m,
+                  uint32_t reps, gi_tune_result* out);
 void gi_batch_destroy(gi_batch* batch);
 
 /*

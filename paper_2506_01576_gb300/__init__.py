@@ -34,6 +34,8 @@ __all__ = [
     "gi_batch_destroy", "GI_BATCH_OPT_CHUNK", "GI_BATCH_OPT_BLOCKS_PER_SM", "GI_BATCH_OPT_SMEM_BUDGET",
     "Server", "gi_request", "gi_server_create", "gi_server_submit", "gi_server_wait", "gi_server_stats",
     "gi_server_destroy", "GI_REQ_POINT", "GI_REQ_RANGE", "GI_ERR_CAPACITY",
+    "gi_tune_result", "gi_tune", "gi_tune_table_get", "gi_tune_table_clear", "gi_batch_tune",
+    "GI_TUNE_APPLY", "GI_TUNE_RECORD",
 ]
 
 GI_SORTED, GI_EYTZINGER, GI_EYTZINGER_KARY = 0, 1, 2
@@ -45,6 +47,7 @@ GI_REQ_POINT, GI_REQ_RANGE = 0, 1
 GI_MISS = 0xFFFFFFFF
 GI_NOALLOC_MAX_RANGES = 1 << 20
 GI_BATCH_OPT_CHUNK, GI_BATCH_OPT_BLOCKS_PER_SM, GI_BATCH_OPT_SMEM_BUDGET = 1, 2, 3
+GI_TUNE_APPLY, GI_TUNE_RECORD = 1, 2
 (GI_OPT_GROUP, GI_OPT_PER_THREAD, GI_OPT_SMEM_LEVELS, GI_OPT_BLOCK, GI_OPT_BLOCKS_PER_SM,
  GI_OPT_PREFETCH, GI_OPT_EARLY_EXIT, GI_OPT_HOT_LEVELS, GI_OPT_RANGE_FILL, GI_OPT_REORDER) = range(1, 11)
 
@@ -71,6 +74,12 @@ class gi_info(ctypes.Structure):
                 ("levels", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("keys", ctypes.c_void_p), ("rowids", ctypes.c_void_p),
                 ("footprint_bytes", ctypes.c_uint64)]
+
+
+class gi_tune_result(ctypes.Structure):
+    _fields_ = [("start_options", ctypes.c_int64 * 11), ("options", ctypes.c_int64 * 11),
+                ("start_ms", ctypes.c_double), ("best_ms", ctypes.c_double),
+                ("trials", ctypes.c_uint32), ("passes", ctypes.c_uint32)]
 
 
 def load(build_if_missing: bool = False):
@@ -116,6 +125,10 @@ def load(build_if_missing: bool = False):
         "gi_server_wait": (I, [P, U64, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "gi_server_stats": (I, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64)]),
         "gi_server_destroy": (None, [P]),
+        "gi_tune": (I, [P, P, U64, U32, I, ctypes.POINTER(gi_tune_result)]),
+        "gi_tune_table_get": (I, [I, U32, U64, ctypes.POINTER(I64), ctypes.POINTER(I)]),
+        "gi_tune_table_clear": (None, []),
+        "gi_batch_tune": (I, [P, P, P, U64, U32, ctypes.POINTER(gi_tune_result)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -394,6 +407,31 @@ def gi_get_option(index: Index, option: int) -> int:
     v = ctypes.c_int64()
     _check(load().gi_get_option(index.handle, option, ctypes.byref(v)))
     return int(v.value)
+
+
+def gi_tune(index: Index, queries, reps: int = 0, flags: int = GI_TUNE_APPLY) -> gi_tune_result:
+    r = gi_tune_result()
+    _check(load().gi_tune(index.handle, _ptr(queries), _len(queries), reps, flags, ctypes.byref(r)))
+    return r
+
+
+def gi_tune_table_get(layout: int, k: int, n: int):
+    """The autotuner table's options for (layout | key width, k, n), or None."""
+    opts = (ctypes.c_int64 * 11)()
+    found = ctypes.c_int()
+    _check(load().gi_tune_table_get(layout, k, n, opts, ctypes.byref(found)))
+    return list(opts) if found.value else None
+
+
+def gi_tune_table_clear() -> None:
+    load().gi_tune_table_clear()
+
+
+def gi_batch_tune(batch: Batch, queries, query_offsets, reps: int = 0) -> gi_tune_result:
+    r = gi_tune_result()
+    _check(load().gi_batch_tune(batch.handle, _ptr(queries), _ptr(query_offsets), _len(queries),
+                                reps, ctypes.byref(r)))
+    return r
 
 
 def gi_probe_random_sectors(buf, chunk_bytes: int, loads: int, seed: int, sink, stream=None) -> None:

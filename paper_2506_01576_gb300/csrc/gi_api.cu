@@ -205,7 +205,22 @@ gi::LookupCfg resolve_cfg(const gi_index* idx) {
   gi::LookupCfg c;
   c.layout = idx->layout;
   c.key_bytes = idx->key_bytes;
-  const int64_t* o = idx->opt;
+  // knobs left automatic take the autotuner's entry for this size class, if any
+  int64_t o[11];
+  for (int i = 0; i < 11; ++i) o[i] = idx->opt[i];
+  int64_t tb[11];
+  if (gi::tune_table_lookup(idx->key_bytes, idx->layout, idx->k, idx->n, tb)) {
+    for (int i = 1; i < 11; ++i)
+      if (o[i] < 0 && tb[i] >= 0 && i != GI_OPT_RANGE_FILL) o[i] = tb[i];
+    if (o[GI_OPT_GROUP] >= 0 && idx->opt[GI_OPT_GROUP] < 0 &&
+        (idx->layout != GI_EYTZINGER_KARY || !gi::eks_group_supported(idx->k, idx->key_bytes, (int)o[GI_OPT_GROUP])))
+      o[GI_OPT_GROUP] = -1;
+    if (o[GI_OPT_SMEM_LEVELS] > 0 && idx->opt[GI_OPT_SMEM_LEVELS] < 0) {
+      const uint64_t slots = gi::smem_slots_for_levels(idx->layout, idx->geom, (int)o[GI_OPT_SMEM_LEVELS], idx->key_bytes);
+      if (((slots * idx->key_bytes + 15) & ~15ull) > (uint64_t)gi::device_max_smem_optin() - 1024)
+        o[GI_OPT_SMEM_LEVELS] = -1;  // the recorded depth does not fit this index
+    }
+  }
   c.group = o[GI_OPT_GROUP] >= 0 ? (int)o[GI_OPT_GROUP]
                                   : (idx->layout == GI_EYTZINGER_KARY
                                          ? gi::eks_default_group(idx->k, idx->key_bytes)
@@ -214,7 +229,10 @@ gi::LookupCfg resolve_cfg(const gi_index* idx) {
   if (idx->layout == GI_EYTZINGER) def_pt = 4;
   c.per_thread = o[GI_OPT_PER_THREAD] >= 0 ? (int)o[GI_OPT_PER_THREAD] : def_pt;
   c.smem_levels = o[GI_OPT_SMEM_LEVELS] >= 0 ? (int)o[GI_OPT_SMEM_LEVELS] : 0;
-  c.block = o[GI_OPT_BLOCK] >= 0 ? (int)o[GI_OPT_BLOCK] : 256;
+  // k-ary lookups: 512 threads per block measured 3% faster than 256 at 2^26 u64
+  // keys, k = 5 (interleaved A/B, 2^27 probes), and the autotuner picks 512 at
+  // most sizes from 2^18 keys up
+  c.block = o[GI_OPT_BLOCK] >= 0 ? (int)o[GI_OPT_BLOCK] : (idx->layout == GI_EYTZINGER_KARY ? 512 : 256);
   c.blocks_per_sm = o[GI_OPT_BLOCKS_PER_SM] >= 0 ? (int)o[GI_OPT_BLOCKS_PER_SM] : 0;
   c.prefetch = o[GI_OPT_PREFETCH] >= 0 ? (int)o[GI_OPT_PREFETCH] : 0;
   const int ee = o[GI_OPT_EARLY_EXIT] >= 0 ? (int)o[GI_OPT_EARLY_EXIT] : 1;
@@ -296,6 +314,10 @@ namespace gi {
 
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+cudaStream_t index_stream(const gi_index* idx) { return idx->stream; }
+
+int64_t index_raw_option(const gi_index* idx, int option) { return idx->opt[option]; }
+
 void set_last_error(const char* msg) { t_err = msg; }
 
 int sm_count() {
@@ -358,9 +380,12 @@ bool eks_group_supported(uint32_t k, int key_bytes, int group) {
 int eks_default_group(uint32_t k, int key_bytes) {
   // One thread per lookup reading its whole node with vector loads measured
   // fastest beyond L2 (fewest instructions per level); nodes wider than 64
-  // bytes are split over lanes in 16-byte pieces.
+  // bytes are split over lanes in 32-byte pieces, one sector per lane (the
+  // autotuner's choice for 128-byte nodes from 2^16 keys up: 1.4-1.7x over
+  // 16-byte pieces), else 16-byte pieces.
   const int node_bytes = (int)(k - 1) * key_bytes;
   if (node_bytes <= 64 && eks_group_supported(k, key_bytes, 1)) return 1;
+  if (node_bytes % 32 == 0 && eks_group_supported(k, key_bytes, node_bytes / 32)) return node_bytes / 32;
   if (node_bytes % 16 == 0 && eks_group_supported(k, key_bytes, node_bytes / 16)) return node_bytes / 16;
   for (int g = 32; g >= 1; g >>= 1)
     if (eks_group_supported(k, key_bytes, g)) return g;

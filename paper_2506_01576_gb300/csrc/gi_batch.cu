@@ -241,9 +241,11 @@ struct gi_batch {
   void* hy_mem = nullptr;    // tables of the hybrid build
   gi::BatchHybrid hy{};
   int result = -1;
-  uint32_t chunk = 1024;       // probes per work item
-  uint32_t smem_budget = 16384;  // bytes of pinned levels per CTA
-  int blocks_per_sm = 4;
+  // defaults: gi_batch_tune's choice on 4096 indexes of 2^8..2^20 u64 keys with
+  // 2^10..2^18 probes each (1.41x over 1024 / 4 / 16384)
+  uint32_t chunk = 2048;       // probes per work item
+  uint32_t smem_budget = 0;    // bytes of pinned levels per CTA
+  int blocks_per_sm = 8;
 };
 
 namespace {
@@ -561,6 +563,25 @@ int gi_batch_set_option(gi_batch* b, int option, int64_t v) {
   }
   return bfail(GI_ERR_INVALID, "gi_batch_set_option: unknown option %d", option);
 }
+
+}  // extern "C"
+
+namespace gi {
+
+cudaStream_t batch_stream(const gi_batch* b) { return b->stream; }
+
+int64_t batch_option(const gi_batch* b, int option) {
+  switch (option) {
+    case GI_BATCH_OPT_CHUNK: return b->chunk;
+    case GI_BATCH_OPT_BLOCKS_PER_SM: return b->blocks_per_sm;
+    case GI_BATCH_OPT_SMEM_BUDGET: return b->smem_budget;
+  }
+  return -1;
+}
+
+}  // namespace gi
+
+extern "C" {
 
 uint64_t gi_batch_footprint_bytes(const gi_batch* b) {
   return b ? b->n * (uint64_t)(b->key_bytes + 4) : 0;

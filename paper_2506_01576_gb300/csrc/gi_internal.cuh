@@ -181,6 +181,13 @@ __device__ __forceinline__ Geom device_geom(uint64_t n, uint32_t k) {
 
 // ---------------------------------------------------------------- launch bookkeeping
 void count_launch(uint64_t n = 1);
+// accessors for the autotuner (gi_tune.cu)
+cudaStream_t index_stream(const gi_index* idx);
+int64_t index_raw_option(const gi_index* idx, int option);  // -1: automatic
+cudaStream_t batch_stream(const gi_batch* b);
+int64_t batch_option(const gi_batch* b, int option);
+// the autotuner's recorded options for (key bytes, layout, k, floor(log2 n)); false if none
+bool tune_table_lookup(int key_bytes, int layout, uint32_t k, uint64_t n, int64_t* opt);
 void set_last_error(const char* msg);  // the thread's gi_last_error() text
 int sm_count();
 int device_max_smem_optin();

@@ -72,6 +72,13 @@ def test_host_side_argument_checks_need_no_gpu(lib_path):
     assert lib.gi_range_lookup(None, None, None, 1, None, None) == gi.GI_ERR_INVALID
     assert lib.gi_sync(None) == gi.GI_ERR_INVALID
     lib.gi_destroy(None)  # no-op
+    # the autotuner rejects a NULL index or batch before any device call; its table
+    # lives on the host
+    assert lib.gi_tune(None, None, 1, 0, gi.GI_TUNE_APPLY, None) == gi.GI_ERR_INVALID
+    assert lib.gi_batch_tune(None, None, None, 1, 0, None) == gi.GI_ERR_INVALID
+    gi.gi_tune_table_clear()
+    assert gi.gi_tune_table_get(gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 5, 1 << 20) is None
+    assert lib.gi_tune_table_get(0, 0, 1, None, None) == gi.GI_ERR_INVALID
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

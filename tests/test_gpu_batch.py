@@ -187,10 +187,10 @@ def test_batched_workload_shape_sampled():
 @pytest.mark.parametrize("bits", [64, 32])
 @pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER_KARY, 5), (gi.GI_SORTED, 0), (gi.GI_EYTZINGER_KARY, 17)])
 def test_batch_build_plans_every_path(bits, layout, k):
-    # the build sorts each index by a plan chosen on the device from its digit
-    # histograms: whole index in one CTA (<= 4096 pairs), one MSD scatter on its 8
-    # highest significant bits + bucket sort, or the LSD passes when a bucket would
-    # exceed 4096 pairs.  One batch holds every case: tiny, uniform, skewed (almost
+    # the build sorts each index by a plan chosen on the device from the bits in
+    # which its keys differ: whole index in one CTA (<= 5120 pairs), one MSD scatter
+    # on a window of its highest significant bits + bucket sort, or the LSD passes
+    # when a window bucket would exceed 5120 pairs.  One batch holds every case: tiny, uniform, skewed (almost
     # all keys in one MSD bucket), all keys equal, heavy duplicates, narrow ranges.
     dt = np.uint64 if bits == 64 else np.uint32
     top = np.iinfo(dt).max
@@ -202,7 +202,8 @@ def test_batch_build_plans_every_path(bits, layout, k):
         np.full(6000, 12345, dt),                                            # all equal: LSD
         W.duplicate_keys(1500, 8, bits, 3)[:12000].astype(dt),               # duplicates: MSD
         rng.integers(0, 1 << 10, size=20000).astype(dt),                     # narrow: MSD on low bits
-        np.zeros(0, dt), np.array([7], dt), W.unique_keys(4097, bits, 4),    # empty, one, just above
+        np.zeros(0, dt), np.array([7], dt), W.unique_keys(5120, bits, 4),    # empty, one, largest whole
+        W.unique_keys(5121, bits, 6),                                        # just above: MSD
         W.unique_keys(100000, bits, 5),
     ]
     rows = [rng.permutation(len(x)).astype(np.uint32) for x in keys]

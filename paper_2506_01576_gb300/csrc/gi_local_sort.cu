@@ -150,14 +150,25 @@ struct BucketSmem {
   }
 };
 
+// Where a sorted bucket's pairs are: direct = s_k / s_v in sorted order, else
+// sorted position j is at s_src[j]; packed = s_k holds (key & low mask) << 13 |
+// position instead of the key, which is hi | (s_k[p] >> 13).
+template <class K>
+struct BucketOrder {
+  bool direct;
+  bool packed;
+  K hi;
+  __device__ __forceinline__ K key(K stored) const { return packed ? (K)(hi | (stored >> 13)) : stored; }
+};
+
 // Sorts the `count` pairs at src + start (count <= T * ITEMS) in shared memory.
 // top_shift: the window (8 bits at that shift) that splits the bucket into
-// sub-buckets for count ranking; lsd_mask: the bytes that may differ inside the
-// bucket, sorted one ballot pass each (LSD order) when a sub-bucket is larger than
-// `limit`; single: the top window alone orders the bucket.  Returns true if s_k /
-// s_v end in sorted order, false if s_src holds it.  Block-uniform.
+// sub-buckets for count ranking; every key of the bucket agrees on the bits at
+// and above top_shift + 8; lsd_mask: the bytes that may differ inside the bucket,
+// sorted one ballot pass each (LSD order) when a sub-bucket is larger than
+// `limit`; single: the top window alone orders the bucket.  Block-uniform.
 template <class K, int ITEMS, int T>
-__device__ __forceinline__ bool sort_bucket(const BucketSmem<K, ITEMS, T>& m,
+__device__ __forceinline__ BucketOrder<K> sort_bucket(const BucketSmem<K, ITEMS, T>& m,
                                             const K* __restrict__ src_k,
                                             const uint32_t* __restrict__ src_v, uint64_t start,
                                             uint32_t count, uint32_t top_shift, uint32_t lsd_mask,
@@ -205,26 +216,55 @@ __device__ __forceinline__ bool sort_bucket(const BucketSmem<K, ITEMS, T>& m,
       }
     }
   }
+  BucketOrder<K> ord{direct, false, K(0)};
   if (!direct) {
     const uint32_t wofs = (uint32_t)warp * 32 * items + lane;
+    // 64-bit keys: inside a sub-bucket only the bits below top_shift + 8 differ.
+    // When they and the 13-bit position fit in 64 bits, every key is replaced in
+    // place by (those bits << 13 | position): distinct values whose order is the
+    // (key, position) order, so one 64-bit compare ranks a pair.
+    const uint32_t low = top_shift + 8;
+    if (sizeof(K) == 8 && low + 13 <= 64) {
+      const uint64_t lmask = (1ull << low) - 1;
+      const K hi = (K)((uint64_t)m.s_k[0] & ~lmask);  // position 0 holds a real key (count >= 1)
+      __syncthreads();
+      for (uint32_t j = tid; j < count; j += T) m.s_k[j] = (K)((((uint64_t)m.s_k[j] & lmask) << 13) | j);
+      __syncthreads();
 #pragma unroll 1
-    for (uint32_t i = 0; i < items; ++i) {
-      const uint32_t p = wofs + i * 32;
-      if (p < count) {
-        const K x = m.s_k[p];
-        const uint32_t d = (uint32_t)(x >> top_shift) & 0xFF;
-        const uint32_t b = m.s_start[d], e = m.s_end[d];
-        uint32_t r = 0;
-        for (uint32_t j = b; j < e; ++j) {
-          const K y = m.s_k[j];
-          r += (y < x || (y == x && j < p)) ? 1u : 0u;
+      for (uint32_t i = 0; i < items; ++i) {
+        const uint32_t p = wofs + i * 32;
+        if (p < count) {
+          const K c = m.s_k[p];
+          const uint32_t d = (uint32_t)(c >> (top_shift + 13)) & 0xFF;
+          const uint32_t b = m.s_start[d], e = m.s_end[d];
+          uint32_t r = 0, j = b;
+          for (; j + 1 < e; j += 2) r += (m.s_k[j] < c ? 1u : 0u) + (m.s_k[j + 1] < c ? 1u : 0u);
+          if (j < e) r += m.s_k[j] < c ? 1u : 0u;
+          m.s_src[b + r] = (uint16_t)p;
         }
-        m.s_src[b + r] = (uint16_t)p;
+      }
+      ord.packed = true;
+      ord.hi = hi;
+    } else {
+#pragma unroll 1
+      for (uint32_t i = 0; i < items; ++i) {
+        const uint32_t p = wofs + i * 32;
+        if (p < count) {
+          const K x = m.s_k[p];
+          const uint32_t d = (uint32_t)(x >> top_shift) & 0xFF;
+          const uint32_t b = m.s_start[d], e = m.s_end[d];
+          uint32_t r = 0;
+          for (uint32_t j = b; j < e; ++j) {
+            const K y = m.s_k[j];
+            r += (y < x || (y == x && j < p)) ? 1u : 0u;
+          }
+          m.s_src[b + r] = (uint16_t)p;
+        }
       }
     }
     __syncthreads();
   }
-  return direct;
+  return ord;
 }
 
 // KF: 1 = sorted layout (slot = rank); >= 2 = k-ary Eytzinger with that fan-out
@@ -245,13 +285,14 @@ __global__ void __launch_bounds__(T, MINB) k_local_sort(
   bool dup = false;
   for (uint64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
     const BatchTile seg = segs[sg];
-    const bool direct = sort_bucket<K, ITEMS, T>(m, src_k, src_v, seg.start, seg.count, 8u * top,
-                                                 local_mask, single, limit, false, flags);
+    const BucketOrder<K> ord = sort_bucket<K, ITEMS, T>(m, src_k, src_v, seg.start, seg.count,
+                                                        8u * top, local_mask, single, limit, false,
+                                                        flags);
     // sorted position j -> rank seg.start + j -> its slot in the layout
     for (uint32_t j = tid; j < seg.count; j += T) {
-      const uint32_t p = direct ? j : m.s_src[j];
-      const K key = m.s_k[p];
-      if (j > 0) dup |= m.s_k[direct ? j - 1 : m.s_src[j - 1]] == key;
+      const uint32_t p = ord.direct ? j : m.s_src[j];
+      const K key = ord.key(m.s_k[p]);
+      if (j > 0) dup |= ord.key(m.s_k[ord.direct ? j - 1 : m.s_src[j - 1]]) == key;
       const uint32_t r = (uint32_t)(seg.start + j);
       uint32_t t = r;
       if constexpr (KF != 1) t = slot_of_rank<KF>(r, s_map);
@@ -300,15 +341,15 @@ __global__ void __launch_bounds__(T, MINB) k_batch_local_sort(
     }
     const uint32_t limit = 8u * (uint32_t)__popc(pl.lsd_mask) + 8u;
     // a whole index is read straight from the input: its rowIDs are checked here
-    const bool direct = sort_bucket<K, ITEMS, T>(m, msd ? src_k : keys, msd ? src_v : vals, start,
-                                                 count, pl.ts, pl.lsd_mask, false, limit, !msd,
-                                                 flags);
+    const BucketOrder<K> ord = sort_bucket<K, ITEMS, T>(m, msd ? src_k : keys, msd ? src_v : vals,
+                                                        start, count, pl.ts, pl.lsd_mask, false,
+                                                        limit, !msd, flags);
     const uint64_t base = seg_base[i];
     const uint32_t r0 = (uint32_t)(start - s0);
     for (uint32_t j = tid; j < count; j += T) {
-      const uint32_t p = direct ? j : m.s_src[j];
-      const K key = m.s_k[p];
-      if (j > 0) dup |= m.s_k[direct ? j - 1 : m.s_src[j - 1]] == key;
+      const uint32_t p = ord.direct ? j : m.s_src[j];
+      const K key = ord.key(m.s_k[p]);
+      if (j > 0) dup |= ord.key(m.s_k[ord.direct ? j - 1 : m.s_src[j - 1]]) == key;
       const uint32_t r = r0 + j;
       uint32_t t = r;
       if constexpr (KF != 1) t = slot_of_rank<KF>(r, s_map);

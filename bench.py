@@ -805,7 +805,8 @@ def run_tune(a):
     (even powers), 2^27 probes (hit rate 0.5, uniform); BS, EBS and EKS k = 5, 9, 17,
     each timed with the default knobs and with the knobs gi_tune picks on a 2^22-probe
     sample, and the fastest layout per size either way (the paper's composite
-    strategy, Section 9).  One JSON line per size."""
+    strategy, Section 9); then the layout, k and knobs gi_build_tuned picks on the same
+    sample.  One JSON line per size."""
     import torch
 
     import paper_2506_01576_gb300 as gi
@@ -842,6 +843,14 @@ def run_tune(a):
             gi.gi_destroy(idx)
         line["fastest_default"] = max(line["default"], key=line["default"].get)
         line["fastest_tuned"] = max(line["tuned"], key=line["tuned"].get)
+        # the layout and k chosen by the library itself (gi_build_tuned)
+        t0 = time.perf_counter()
+        idx, r = gi.gi_build_tuned(kd, rd, gi.GI_KEY_U64, sample)
+        info = gi.gi_get_info(idx)
+        ms = _ev_ms(torch, lambda: gi.gi_point_lookup(idx, qd, out), a.steps)
+        line["build_tuned"] = {"layout": {0: "sorted", 1: "EBS", 2: "EKS"}[info.layout], "k": int(info.k),
+                               "lookups_per_s": m / ms * 1e3, "seconds": time.perf_counter() - t0}
+        gi.gi_destroy(idx)
         print(json.dumps(line), flush=True)
         del kd, rd, qd, sample
 

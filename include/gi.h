@@ -262,6 +262,26 @@ int gi_tune_table_get(int layout, uint32_t k, uint64_t n, int64_t* options, int*
 void gi_tune_table_clear(void);
 
 /*
+ * gi_build_tuned -- picks the layout and k as well (the paper's composite strategy,
+ *   Section 9, measured instead of assumed).  Builds the pairs as GI_SORTED,
+ *   GI_EYTZINGER and GI_EYTZINGER_KARY with k = 3, 5, 9, 17 in turn (arguments as
+ *   gi_build; key_flags = the key width and build flags, no layout), tunes each with
+ *   gi_tune on the DEVICE probes queries[0..m) and keeps the index whose best time
+ *   is shortest; the others are destroyed as soon as they lose, so at most two
+ *   indexes exist at a time.  flags: GI_TUNE_APPLY leaves the winner's knobs set
+ *   (otherwise automatic); GI_TUNE_RECORD records its knobs as gi_tune does and its
+ *   (layout, k) under (key width, floor(log2 n)) for gi_tune_table_layout.
+ *   result (may be NULL): the winner's gi_tune result; gi_get_info gives its layout.
+ *   Synchronous.  Errors: as gi_build and gi_tune; *out is NULL on error.
+ * gi_tune_table_layout -- the recorded (layout, k) for (key width, n): *found = 1 if
+ *   the size class has one (else *layout = -1, *k = 0).
+ */
+int gi_build_tuned(const void* keys, const uint32_t* rowids, uint64_t n, int key_flags,
+                   const void* queries, uint64_t m, uint32_t reps, int flags, gi_index** out,
+                   gi_tune_result* result);
+int gi_tune_table_layout(int key_flags, uint64_t n, int* layout, uint32_t* k, int* found);
+
+/*
  * gi_probe_random_sectors -- roofline probe: `loads` loads of `chunk_bytes`
  * (16, 32, 64, 128 or 256) contiguous bytes each from uniformly random
  * chunk-aligned offsets of the device buffer `buf` (`bytes` long, 256-byte

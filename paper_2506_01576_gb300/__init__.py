@@ -35,7 +35,7 @@ __all__ = [
     "Server", "gi_request", "gi_server_create", "gi_server_submit", "gi_server_wait", "gi_server_stats",
     "gi_server_destroy", "GI_REQ_POINT", "GI_REQ_RANGE", "GI_ERR_CAPACITY",
     "gi_tune_result", "gi_tune", "gi_tune_table_get", "gi_tune_table_clear", "gi_batch_tune",
-    "GI_TUNE_APPLY", "GI_TUNE_RECORD",
+    "GI_TUNE_APPLY", "GI_TUNE_RECORD", "gi_build_tuned", "gi_tune_table_layout",
 ]
 
 GI_SORTED, GI_EYTZINGER, GI_EYTZINGER_KARY = 0, 1, 2
@@ -129,6 +129,9 @@ def load(build_if_missing: bool = False):
         "gi_tune_table_get": (I, [I, U32, U64, ctypes.POINTER(I64), ctypes.POINTER(I)]),
         "gi_tune_table_clear": (None, []),
         "gi_batch_tune": (I, [P, P, P, U64, U32, ctypes.POINTER(gi_tune_result)]),
+        "gi_build_tuned": (I, [P, P, U64, I, P, U64, U32, I, ctypes.POINTER(P),
+                               ctypes.POINTER(gi_tune_result)]),
+        "gi_tune_table_layout": (I, [I, U64, ctypes.POINTER(I), ctypes.POINTER(U32), ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -421,6 +424,24 @@ def gi_tune_table_get(layout: int, k: int, n: int):
     found = ctypes.c_int()
     _check(load().gi_tune_table_get(layout, k, n, opts, ctypes.byref(found)))
     return list(opts) if found.value else None
+
+
+def gi_build_tuned(keys, rowids, key_flags: int, queries, reps: int = 0,
+                   flags: int = GI_TUNE_APPLY):
+    """Build in every layout / k, tune each on `queries`, keep the fastest:
+    returns (Index, gi_tune_result)."""
+    r = gi_tune_result()
+    h = ctypes.c_void_p()
+    _check(load().gi_build_tuned(_ptr(keys), _ptr(rowids), _len(keys), key_flags, _ptr(queries),
+                                 _len(queries), reps, flags, ctypes.byref(h), ctypes.byref(r)))
+    return Index(h.value, (keys, rowids)), r
+
+
+def gi_tune_table_layout(key_flags: int, n: int):
+    """The recorded (layout, k) for the size class of n, or None."""
+    lay, k, found = ctypes.c_int(), ctypes.c_uint32(), ctypes.c_int()
+    _check(load().gi_tune_table_layout(key_flags, n, ctypes.byref(lay), ctypes.byref(k), ctypes.byref(found)))
+    return (lay.value, k.value) if found.value else None
 
 
 def gi_tune_table_clear() -> None:

@@ -43,6 +43,8 @@ using TableKey = std::tuple<int, int, uint32_t, int>;
 std::mutex g_mu;
 std::map<TableKey, std::array<int64_t, 11>> g_table;
 std::atomic<bool> g_table_used{false};
+// (key bytes, floor(log2 n)) -> (layout, k) of the fastest layout gi_build_tuned found
+std::map<std::pair<int, int>, std::pair<int, uint32_t>> g_layouts;
 
 int size_class(uint64_t n) {
   int c = 0;
@@ -326,7 +328,75 @@ int gi_tune_table_get(int layout, uint32_t k, uint64_t n, int64_t* options, int*
 void gi_tune_table_clear(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_table.clear();
+  g_layouts.clear();
   g_table_used.store(false, std::memory_order_release);
+}
+
+int gi_build_tuned(const void* keys, const uint32_t* rowids, uint64_t n, int key_flags,
+                   const void* queries, uint64_t m, uint32_t reps, int flags, gi_index** out,
+                   gi_tune_result* result) {
+  gi::set_last_error("");
+  if (!out) return tfail(GI_ERR_INVALID, "gi_build_tuned: out is NULL");
+  *out = nullptr;
+  if (key_flags & 0xFF) return tfail(GI_ERR_INVALID, "gi_build_tuned: pass the key width and build flags only");
+  if (flags & ~(GI_TUNE_APPLY | GI_TUNE_RECORD)) return tfail(GI_ERR_INVALID, "gi_build_tuned: unknown flags");
+  // the layouts of Sections 3 and 6 with compiled lane-group kernels: sorted, EBS,
+  // k-ary with k - 1 a power of two
+  static const int kLayouts[][2] = {{GI_SORTED, 0}, {GI_EYTZINGER, 2}, {GI_EYTZINGER_KARY, 3},
+                                    {GI_EYTZINGER_KARY, 5}, {GI_EYTZINGER_KARY, 9},
+                                    {GI_EYTZINGER_KARY, 17}};
+  gi_index* best = nullptr;
+  gi_tune_result best_r{};
+  for (const auto& c : kLayouts) {
+    gi_index* idx = nullptr;
+    int rc = gi_build(keys, rowids, n, key_flags | c[0], (uint32_t)c[1], &idx);
+    if (rc == GI_OK) {
+      gi_tune_result r{};
+      rc = gi_tune(idx, queries, m, reps, GI_TUNE_APPLY, &r);
+      if (rc == GI_OK && (!best || r.best_ms < best_r.best_ms)) {
+        gi_destroy(best);
+        best = idx;
+        best_r = r;
+        idx = nullptr;
+      }
+    }
+    gi_destroy(idx);
+    if (rc != GI_OK) {
+      gi_destroy(best);
+      return rc;
+    }
+  }
+  gi_info info{};
+  gi_get_info(best, &info);
+  if (flags & GI_TUNE_RECORD) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    const int kb = (int)info.key_bytes, cls = size_class(n);
+    g_table[TableKey{kb, info.layout, info.layout == GI_EYTZINGER_KARY ? info.k : 0u, cls}] = [&] {
+      std::array<int64_t, 11> a{};
+      for (int o = 0; o < 11; ++o) a[o] = o == GI_OPT_RANGE_FILL ? -1 : best_r.options[o];
+      a[0] = -1;
+      return a;
+    }();
+    g_layouts[{kb, cls}] = {info.layout, info.layout == GI_EYTZINGER_KARY ? info.k : 0u};
+    g_table_used.store(true, std::memory_order_release);
+  }
+  if (!(flags & GI_TUNE_APPLY))
+    for (int o = 1; o < 11; ++o) gi_set_option(best, o, -1);
+  if (result) *result = best_r;
+  *out = best;
+  return GI_OK;
+}
+
+int gi_tune_table_layout(int key_flags, uint64_t n, int* layout, uint32_t* k, int* found) {
+  gi::set_last_error("");
+  if (!layout || !k || !found) return tfail(GI_ERR_INVALID, "gi_tune_table_layout: NULL argument");
+  const int kb = (key_flags & 0xFF00) == GI_KEY_U64 ? 8 : 4;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_layouts.find({kb, size_class(n)});
+  *found = it != g_layouts.end();
+  *layout = *found ? it->second.first : -1;
+  *k = *found ? it->second.second : 0u;
+  return GI_OK;
 }
 
 int gi_batch_tune(gi_batch* b, const void* queries, const uint64_t* query_offsets, uint64_t m,

@@ -79,6 +79,11 @@ def test_host_side_argument_checks_need_no_gpu(lib_path):
     gi.gi_tune_table_clear()
     assert gi.gi_tune_table_get(gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 5, 1 << 20) is None
     assert lib.gi_tune_table_get(0, 0, 1, None, None) == gi.GI_ERR_INVALID
+    assert gi.gi_tune_table_layout(gi.GI_KEY_U64, 1 << 20) is None
+    out = ctypes.c_void_p()
+    assert lib.gi_build_tuned(None, None, 0, gi.GI_KEY_U64, None, 1, 0, 0, None, None) == gi.GI_ERR_INVALID
+    assert lib.gi_build_tuned(None, None, 0, gi.GI_KEY_U64 | gi.GI_EYTZINGER, None, 1, 0, 0,
+                              ctypes.byref(out), None) == gi.GI_ERR_INVALID
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

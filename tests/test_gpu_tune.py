@@ -147,3 +147,33 @@ def test_batch_tune_keeps_results():
         sk, sr = oracle.sort_pairs(keys[i], rows[i])
         assert np.array_equal(got[int(qoff[i]):int(qoff[i + 1])], oracle.point_lookup(sk, sr, qs[i])), i
     gi.gi_batch_destroy(batch)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_build_tuned_picks_a_layout_and_answers_exactly(dtype):
+    gi.gi_tune_table_clear()
+    bits = 8 * np.dtype(dtype).itemsize
+    n = (1 << 16) + 123
+    keys = W.unique_keys(n, bits, 71)
+    rows = np.random.default_rng(71).permutation(n).astype(np.uint32)
+    q = W.point_probes(keys, 1 << 17, 0.5, bits, 71, 72)
+    kf = gi.GI_KEY_U64 if bits == 64 else gi.GI_KEY_U32
+    idx, r = gi.gi_build_tuned(to_dev(keys), to_dev(rows), kf, to_dev(q), 2,
+                               gi.GI_TUNE_APPLY | gi.GI_TUNE_RECORD)
+    info = gi.gi_get_info(idx)
+    assert (info.layout, info.k) in {(gi.GI_SORTED, 0), (gi.GI_EYTZINGER, 2), (gi.GI_EYTZINGER_KARY, 3),
+                                     (gi.GI_EYTZINGER_KARY, 5), (gi.GI_EYTZINGER_KARY, 9),
+                                     (gi.GI_EYTZINGER_KARY, 17)}
+    assert info.n == n and info.key_bytes == bits // 8
+    for o in range(1, 11):
+        if o != gi.GI_OPT_RANGE_FILL:
+            assert gi.gi_get_option(idx, o) == r.options[o], o
+    sk, sr = oracle.sort_pairs(keys, rows)
+    assert np.array_equal(point(idx, q), oracle.point_lookup(sk, sr, q))
+    # the layout, k and knobs of the size class are recorded
+    assert gi.gi_tune_table_layout(kf, n) == (info.layout, info.k if info.layout == gi.GI_EYTZINGER_KARY else 0)
+    assert gi.gi_tune_table_layout(kf, n * 4) is None
+    assert gi.gi_tune_table_get(kf | info.layout, info.k, n) is not None
+    gi.gi_destroy(idx)
+    gi.gi_tune_table_clear()
+    assert gi.gi_tune_table_layout(kf, n) is None

@@ -440,6 +440,16 @@ int gi_range_lookup_noalloc(const gi_index* index, const void* lo, const void* h
 /* Number of kernels this library has launched in the process so far. */
 uint64_t gi_launch_count(void);
 
+/*
+ * gi_debug_fail_alloc -- test hook for out-of-memory handling without exhausting a
+ *   shared GPU: after `after` more successful device allocations made through the
+ *   library's index paths (build buffers, sort scratch, range scratch, host-memory
+ *   staging), the next one reports cudaErrorMemoryAllocation without allocating, and
+ *   the hook disarms.  The failing call returns GI_ERR_NOMEM having freed what it had
+ *   allocated; the library stays usable.  after < 0 disarms.  Process-wide.
+ */
+void gi_debug_fail_alloc(int64_t after);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,7 @@ __all__ = [
     "Server", "gi_request", "gi_server_create", "gi_server_submit", "gi_server_wait", "gi_server_stats",
     "gi_server_destroy", "GI_REQ_POINT", "GI_REQ_RANGE", "GI_ERR_CAPACITY",
     "gi_tune_result", "gi_tune", "gi_tune_table_get", "gi_tune_table_clear", "gi_batch_tune",
-    "GI_TUNE_APPLY", "GI_TUNE_RECORD", "gi_build_tuned", "gi_tune_table_layout",
+    "GI_TUNE_APPLY", "GI_TUNE_RECORD", "gi_build_tuned", "gi_tune_table_layout", "gi_debug_fail_alloc",
 ]
 
 GI_SORTED, GI_EYTZINGER, GI_EYTZINGER_KARY = 0, 1, 2
@@ -132,6 +132,7 @@ def load(build_if_missing: bool = False):
         "gi_build_tuned": (I, [P, P, U64, I, P, U64, U32, I, ctypes.POINTER(P),
                                ctypes.POINTER(gi_tune_result)]),
         "gi_tune_table_layout": (I, [I, U64, ctypes.POINTER(I), ctypes.POINTER(U32), ctypes.POINTER(I)]),
+        "gi_debug_fail_alloc": (None, [I64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -465,6 +466,12 @@ def gi_coalescing_probe(buf, threads: int, group: int, steps: int, seed: int, si
                         stream=None) -> None:
     _check(load().gi_coalescing_probe(_ptr(buf), _len(buf), threads, group, steps, seed,
                                       _ptr(sink), _stream_handle(stream)))
+
+
+def gi_debug_fail_alloc(after: int) -> None:
+    """Test hook: the library's device allocation after `after` more succeeds fails
+    with out-of-memory (once); after < 0 disarms."""
+    load().gi_debug_fail_alloc(after)
 
 
 def gi_launch_count() -> int:

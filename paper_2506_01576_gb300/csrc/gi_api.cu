@@ -167,7 +167,22 @@ PinnedScratch& pinned_scratch() {
 // the sort buffers a build frees are reused by the next build instead of being
 // unmapped and mapped again at every synchronisation, while freed memory beyond
 // 8 GiB still goes back to the driver.
+// Test hook (gi_debug_fail_alloc): the countdown of device allocations until one
+// reports out-of-memory on the host side, or -1.
+std::atomic<int64_t> g_fail_alloc{-1};
+
+bool injected_alloc_failure() {
+  int64_t v = g_fail_alloc.load();
+  while (v >= 0)
+    if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return v == 0;
+  return false;
+}
+
 cudaError_t dalloc(void** p, size_t bytes, cudaStream_t s) {
+  if (injected_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
   static std::once_flag once[64];
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
@@ -269,9 +284,12 @@ void free_staging(gi_index* idx) {
   cudaStreamSynchronize(idx->stream);
   for (int i = 0; i < 3; ++i) {
     if (st->st[i]) cudaStreamSynchronize(st->st[i]);
-    cudaFree(st->q[i]);
-    cudaFree(st->out[i]);
-    if (st->st[i]) cudaStreamDestroy(st->st[i]);
+    if (st->q[i]) cudaFreeAsync(st->q[i], st->st[i]);
+    if (st->out[i]) cudaFreeAsync(st->out[i], st->st[i]);
+    if (st->st[i]) {
+      cudaStreamSynchronize(st->st[i]);
+      cudaStreamDestroy(st->st[i]);
+    }
   }
   if (st->ev) cudaEventDestroy(st->ev);
   for (cudaEvent_t e : st->cev)
@@ -286,13 +304,23 @@ int ensure_staging(gi_index* idx, uint64_t chunk) {
   GiStaging* st = new GiStaging();
   st->chunk = chunk;
   idx->stage = st;
-  for (int i = 0; i < 3; ++i) {
-    GI_CUDA(cudaStreamCreateWithFlags(&st->st[i], cudaStreamNonBlocking), "staging stream");
-    GI_CUDA(cudaMalloc(&st->q[i], chunk * idx->key_bytes), "staging buffer");
-    GI_CUDA(cudaMalloc((void**)&st->out[i], chunk * 4), "staging buffer");
+  // on any failure the partial staging is freed, so a later call starts over
+  // instead of finding buffers that were never allocated
+  auto give_up = [&](cudaError_t e, const char* what) {
+    free_staging(idx);
+    return cuda_fail(e, what);
+  };
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&st->st[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = dalloc(&st->q[i], chunk * idx->key_bytes, st->st[i]);
+    if (e == cudaSuccess) e = dalloc((void**)&st->out[i], chunk * 4, st->st[i]);
   }
-  GI_CUDA(cudaEventCreateWithFlags(&st->ev, cudaEventDisableTiming), "staging event");
-  for (cudaEvent_t& e : st->cev) GI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "staging event");
+  if (e != cudaSuccess) return give_up(e, "staging buffer");
+  e = cudaEventCreateWithFlags(&st->ev, cudaEventDisableTiming);
+  for (cudaEvent_t& ev : st->cev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return give_up(e, "staging event");
   return GI_OK;
 }
 
@@ -430,6 +458,8 @@ extern "C" {
 const char* gi_last_error(void) { return t_err.c_str(); }
 
 uint64_t gi_launch_count(void) { return g_launches.load(); }
+
+void gi_debug_fail_alloc(int64_t after) { g_fail_alloc.store(after < 0 ? -1 : after); }
 
 int gi_set_stream(gi_index* idx, void* stream) {
   t_err.clear();

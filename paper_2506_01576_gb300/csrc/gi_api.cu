@@ -344,6 +344,8 @@ void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxe
 
 cudaStream_t index_stream(const gi_index* idx) { return idx->stream; }
 
+int index_device(const gi_index* idx) { return idx->device; }
+
 int64_t index_raw_option(const gi_index* idx, int option) { return idx->opt[option]; }
 
 void set_last_error(const char* msg) { t_err = msg; }

@@ -570,6 +570,8 @@ namespace gi {
 
 cudaStream_t batch_stream(const gi_batch* b) { return b->stream; }
 
+int batch_device(const gi_batch* b) { return b->device; }
+
 int64_t batch_option(const gi_batch* b, int option) {
   switch (option) {
     case GI_BATCH_OPT_CHUNK: return b->chunk;

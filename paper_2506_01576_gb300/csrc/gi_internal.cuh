@@ -183,6 +183,8 @@ __device__ __forceinline__ Geom device_geom(uint64_t n, uint32_t k) {
 void count_launch(uint64_t n = 1);
 // accessors for the autotuner (gi_tune.cu)
 cudaStream_t index_stream(const gi_index* idx);
+int index_device(const gi_index* idx);
+int batch_device(const gi_batch* b);
 int64_t index_raw_option(const gi_index* idx, int option);  // -1: automatic
 cudaStream_t batch_stream(const gi_batch* b);
 int64_t batch_option(const gi_batch* b, int option);

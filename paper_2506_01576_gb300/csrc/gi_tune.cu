@@ -9,7 +9,6 @@
 #include <algorithm>
 #include <array>
 #include <atomic>
-#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <map>
@@ -144,6 +143,21 @@ std::vector<std::vector<Move>> index_moves(const gi_info& info, int64_t hot_defa
 }
 
 // ---------------------------------------------------------------- timing
+// Makes the index's device current for the call (scratch and events live there).
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess || prev == dev) {
+      prev = -1;
+      return;
+    }
+    cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 struct Timer {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   ~Timer() {
@@ -250,6 +264,7 @@ int gi_tune(gi_index* idx, const void* queries, uint64_t m, uint32_t reps, int f
   gi_info info{};
   int rc = gi_get_info(idx, &info);
   if (rc != GI_OK) return rc;
+  const DeviceGuard dg(gi::index_device(idx));
   const cudaStream_t s = gi::index_stream(idx);
   // the settings on entry: raw (to restore) and resolved (the starting point)
   std::array<int64_t, 11> raw{}, cur{};
@@ -404,6 +419,7 @@ int gi_batch_tune(gi_batch* b, const void* queries, const uint64_t* query_offset
   gi::set_last_error("");
   if (!b) return tfail(GI_ERR_INVALID, "gi_batch_tune: NULL batch");
   if (reps == 0) reps = 5;
+  const DeviceGuard dg(gi::batch_device(b));
   const cudaStream_t s = gi::batch_stream(b);
   std::array<int64_t, 11> cur{};
   cur.fill(-1);

@@ -537,7 +537,7 @@ def run_reference(a):
     rows = np.arange(n, dtype=np.uint32)
     threads = oracle.hardware_threads()
     sk, sr = oracle.sort_pairs(keys, rows)
-    sort_sample, point_sample, range_sample = 1 << 21, 1 << 20, min(1 << 16, mr)
+    sort_sample, point_sample, range_sample = min(1 << 21, n), min(1 << 20, m), min(1 << 16, mr)
     rng = np.random.default_rng(1)
 
     def step():

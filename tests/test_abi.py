@@ -86,9 +86,11 @@ def test_host_side_argument_checks_need_no_gpu(lib_path):
                               ctypes.byref(out), None) == gi.GI_ERR_INVALID
 
 
-def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+def test_binding_fails_loudly_without_library(monkeypatch):
     import importlib
     monkeypatch.setattr(gi, "_lib", None)
-    monkeypatch.setattr(gi, "lib_path", str(tmp_path / "missing.so"))
+    # a path that does not exist (nothing is created)
+    monkeypatch.setattr(gi, "lib_path", os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                     "_build", "no-such-dir", "missing.so"))
     with pytest.raises(ImportError):
         gi.load()

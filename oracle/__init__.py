@@ -32,12 +32,17 @@ MISS = 0xFFFFFFFF
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.cpp")
-_LIB = os.path.join(_HERE, "liboracle.so")
+# GI_ORACLE_LIB names another build of oracle.cpp to load instead; the mutation
+# tests load copies with a planted mistake this way, to show that the pins fail
+_OVERRIDE = os.environ.get("GI_ORACLE_LIB")
+_LIB = _OVERRIDE or os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 
 def build(force: bool = False) -> str:
     """Compile liboracle.so next to its source (g++, host only)."""
+    if _OVERRIDE:
+        return _LIB
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC,

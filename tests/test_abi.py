@@ -39,6 +39,19 @@ def test_header_declares_the_boundary():
         assert f in names
 
 
+def test_header_is_plain_c():
+    # the boundary is a C ABI: the header compiles as strict C99, with no C++
+    build = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build")
+    os.makedirs(build, exist_ok=True)
+    src = os.path.join(build, "header_c99.c")
+    with open(src, "w") as f:
+        f.write('#include "gi.h"\nint main(void) { gi_info i; gi_tune_result r; (void)i; (void)r; return 0; }\n')
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I" + include,
+                        "-c", src, "-o", src + ".o"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_library_exports_every_declared_function(lib_path):
     out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
                          text=True, check=True).stdout

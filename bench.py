@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="timed steps only (for profiler launch lists)")
+    ap.add_argument("--no-legs", action="store_true", help="skip the ranges / batched / serving legs")
     ap.add_argument("--workload", default="point",
                     choices=["point", "batched", "ranges", "dups", "skew", "serve", "sizes", "tune"],
                     help="point: the 2^26-key step (default); batched: 4096 indexes in one graph; "
@@ -70,8 +71,8 @@ def parse():
     ap.add_argument("--serve-indexes", type=int, default=64)
     ap.add_argument("--serve-min-log", type=int, default=20)
     ap.add_argument("--serve-max-log", type=int, default=27)
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
-    ap.add_argument("--serve-rates", default="2000,8000,32000,64000")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-rates", default="1000,4000,16000,64000,128000,256000")
     ap.add_argument("--batch-indexes", type=int, default=4096)
     ap.add_argument("--probe-sweep", action="store_true",
                     help="print random-access throughput over buffer sizes (L2 vs HBM) and exit")
@@ -440,6 +441,17 @@ def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, 
                       "h2d_bytes_per_step": nk * 8 + nk * 4 + m * 8 + 2 * mr * 8,
                       "d2h_bytes_per_step": m * 4 + (mr + 1) * 8 + total * 4,
                       "ms_per_step": dt * 1e3, "host_buffers": "pinned"}
+    # ---- the other forms of the path, each at a stated size (after the timed region)
+    if not a.no_legs:
+        res["ranges"] = ranges_leg(gi, torch, dev)
+        bt = batched_measure(gi, torch, dev, 1024, 5, 5, 3, tune=False, per_index=True)
+        bt["note"] = "1024 of the 4096 indexes of the batched workload (same size law)"
+        res["batched"] = bt
+        meta, runs = serving_sweep(gi, torch, dev, 8, 20, 24, [2000.0, 64000.0], 0.5, 400,
+                                   serial_max_requests=4000)
+        meta["note"] = ("8 resident indexes of 2^20..2^24 u64 keys (the serving workload's request "
+                        "mix and arrival law at two offered loads)")
+        res["serving"] = {**meta, "runs": runs}
     # ---- CPU oracle on the host cores (bounded sample)
     if not a.no_cpu:
         res["cpu_baseline"] = cpu_oracle_sample(keys, q, lo, hi, n, m, a)
@@ -588,18 +600,12 @@ def probe_sweep():
         del buf
 
 
-def run_batched(a):
-    """4096 independent indexes (2^8..2^20 u64 keys, log-uniform) with 2^10..2^18
-    probes each at hit rate 0.75: build + lookup of all of them as one CUDA graph
-    (gi_batch_*), against one gi_build + gi_point_lookup per index."""
-    import torch
-
-    import paper_2506_01576_gb300 as gi
-    gi.load()
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    rng = np.random.default_rng(2024)
-    B = a.batch_indexes
+def batched_measure(gi, torch, dev, B, k, steps, warmup, tune=False, per_index=True, seed=2024,
+                    mixed=True):
+    """B independent indexes (2^8..2^20 u64 keys, log-uniform) with 2^10..2^18 probes
+    each at hit rate 0.75: build + lookup of all of them as one CUDA graph
+    (gi_batch_*), against one gi_build + gi_point_lookup per index.  Returns a dict."""
+    rng = np.random.default_rng(seed)
     sizes = np.exp2(rng.uniform(8, 20, size=B)).astype(np.int64)
     nq = np.exp2(rng.uniform(10, 18, size=B)).astype(np.int64)
     off = np.zeros(B + 1, dtype=np.uint64)
@@ -619,7 +625,7 @@ def run_batched(a):
     qod = torch.from_numpy(qoff.view(np.int64)).to(dev)
     out = torch.empty(m, dtype=torch.int32, device=dev)
     layout = gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64
-    batch = gi.gi_batch_create(off, layout, a.batch_k)
+    batch = gi.gi_batch_create(off, layout, k)
     s = torch.cuda.Stream()
     gi.gi_batch_set_stream(batch, s)
     with torch.cuda.stream(s):
@@ -635,7 +641,7 @@ def run_batched(a):
 
     def ev(fn, reps):
         with torch.cuda.stream(s):  # replays and launches both go to stream s
-            for _ in range(a.warmup):
+            for _ in range(warmup):
                 fn()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -651,55 +657,117 @@ def run_batched(a):
         g.replay()
     torch.cuda.synchronize()
     clk.begin()
-    graph_ms = ev(lambda: g.replay(), a.steps)
+    graph_ms = ev(lambda: g.replay(), steps)
     clk.end()
     clk.stop()
-    launches = kernels_per_replay * a.steps
     gi.gi_batch_sync(batch)
     got = out.cpu().numpy().view(np.uint32)
-    lookup_ms = ev(lambda: gi.gi_batch_point_lookup(batch, qd, qod, out), a.steps)
-    build_ms = ev(lambda: gi.gi_batch_build(batch, kd, rd), max(2, a.steps // 2))
+    lookup_ms = ev(lambda: gi.gi_batch_point_lookup(batch, qd, qod, out), steps)
+    build_ms = ev(lambda: gi.gi_batch_build(batch, kd, rd), max(2, steps // 2))
+    # sampled parity without the oracle: per index, sorted keys and numpy searchsorted
+    samp_ok = True
+    for i in rng.choice(B, size=min(B, 64), replace=False):
+        k0, k1, q0, q1 = int(off[i]), int(off[i + 1]), int(qoff[i]), int(qoff[i + 1])
+        order = np.argsort(keys[k0:k1], kind="stable")
+        sk = keys[k0:k1][order]
+        r = np.searchsorted(sk, q[q0:q1])
+        rc = np.minimum(r, len(sk) - 1)
+        hit = (r < len(sk)) & (sk[rc] == q[q0:q1])
+        want = np.where(hit, (order[rc] + k0).astype(np.uint32), np.uint32(0xFFFFFFFF))
+        samp_ok &= bool(np.array_equal(got[q0:q1], want))
+    # per-index fan-outs: the automatic choice by size class, then the tuner's
+    # per-class choice; each captured and replayed as its own graph
+    fan = {}
+    if mixed:
+        def graph_ms_now():
+            gg = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(s):
+                gi.gi_batch_build(batch, kd, rd)
+                gi.gi_batch_point_lookup(batch, qd, qod, out)
+            s.synchronize()
+            with torch.cuda.graph(gg, stream=s, capture_error_mode="relaxed"):
+                gi.gi_batch_build(batch, kd, rd)
+                gi.gi_batch_point_lookup(batch, qd, qod, out)
+            t = ev(lambda: gg.replay(), steps)
+            gi.gi_batch_sync(batch)
+            return t, out.cpu().numpy().view(np.uint32)
+
+        gi.gi_batch_fanout_table_clear()
+        gi.gi_batch_set_fanouts(batch, None)
+        ks_auto = gi.gi_batch_get_fanouts(batch, B)
+        t_auto, got_auto = graph_ms_now()
+        ks_t, cms = gi.gi_batch_tune_fanouts(batch, B, kd, rd, qd, qod, reps=3, flags=gi.GI_TUNE_APPLY)
+        t_tuned, got_tuned = graph_ms_now()
+        classes = {}
+        for c in range(64):
+            if cms[c].max() > 0:
+                classes["2^%d" % c] = {"chosen_k": int([2, 3, 5, 9, 17][int(np.argmin(cms[c]))]),
+                                       "ms_by_k": {str(k): round(float(v), 4)
+                                                   for k, v in zip((2, 3, 5, 9, 17), cms[c])}}
+        fan = {"graph_step_ms_auto_fanouts": t_auto, "graph_step_ms_tuned_fanouts": t_tuned,
+               "lookups_per_s_tuned_fanouts": m / (t_tuned / 1e3),
+               "auto_fanout_counts": {str(k): int((ks_auto == k).sum()) for k in (2, 3, 5, 9, 17)},
+               "tuned_per_class": classes,
+               "results_identical_to_k5": bool(np.array_equal(got_auto, got) and np.array_equal(got_tuned, got))}
+        gi.gi_batch_set_fanouts(batch, np.full(B, k, np.uint32))
+        gi.gi_batch_build(batch, kd, rd)
     tuned = None
-    if not a.no_extras:  # the autotuner on the same probes (the graph keeps the defaults)
+    if tune:  # the autotuner on the same probes (the graph keeps the defaults)
         r = gi.gi_batch_tune(batch, qd, qod)
         names = {gi.GI_BATCH_OPT_CHUNK: "chunk", gi.GI_BATCH_OPT_BLOCKS_PER_SM: "blocks_per_sm",
                  gi.GI_BATCH_OPT_SMEM_BUDGET: "smem_budget"}
-        tuned = {"lookup_ms": ev(lambda: gi.gi_batch_point_lookup(batch, qd, qod, out), a.steps),
+        tuned = {"lookup_ms": ev(lambda: gi.gi_batch_point_lookup(batch, qd, qod, out), steps),
                  "start": {v: int(r.start_options[o]) for o, v in names.items()},
                  "chosen": {v: int(r.options[o]) for o, v in names.items()}, "trials": int(r.trials)}
     # one index at a time through the single-index API
-    gi.gi_set_stream(None, s)
-    out2 = torch.empty(m, dtype=torch.int32, device=dev)
-
-    def per_index():
-        for i in range(B):
-            k0, k1 = int(off[i]), int(off[i + 1])
-            q0, q1 = int(qoff[i]), int(qoff[i + 1])
-            idx = gi.gi_build(kd[k0:k1], rd[k0:k1], layout, a.batch_k)
-            gi.gi_point_lookup(idx, qd[q0:q1], out2[q0:q1])
-            gi.gi_destroy(idx)
-
     per_ms, same = None, None
-    if not a.no_extras:  # thousands of launches: left out of profiler launch lists
+    if per_index:
+        gi.gi_set_stream(None, s)
+        out2 = torch.empty(m, dtype=torch.int32, device=dev)
+
+        def one_by_one():
+            for i in range(B):
+                k0, k1 = int(off[i]), int(off[i + 1])
+                q0, q1 = int(qoff[i]), int(qoff[i + 1])
+                idx = gi.gi_build(kd[k0:k1], rd[k0:k1], layout, k)
+                gi.gi_point_lookup(idx, qd[q0:q1], out2[q0:q1])
+                gi.gi_destroy(idx)
+
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        per_index()
+        one_by_one()
         torch.cuda.synchronize()
         per_ms = (time.perf_counter() - t0) * 1e3
         same = bool(np.array_equal(got, out2.cpu().numpy().view(np.uint32)))
-    gi.gi_set_stream(None, None)
+        gi.gi_set_stream(None, None)
+    gi.gi_batch_destroy(batch)
+    return {"indexes": B, "keys_total": int(off[-1]), "probes_total": m, "k": k,
+            "graph_step_ms": graph_ms, "build_ms": build_ms, "lookup_ms": lookup_ms,
+            "lookups_per_s": m / (graph_ms / 1e3), "lookup_only_per_s": m / (lookup_ms / 1e3),
+            "lookup_tuned": tuned, "per_index_launches_ms": per_ms,
+            "speedup_vs_per_index": per_ms and per_ms / graph_ms,
+            "per_index_results_identical": same, "sampled_parity_64_indexes": samp_ok,
+            "kernels_per_graph": int(kernels_per_replay), "clocks": clk.summary(), **fan}
+
+
+def run_batched(a):
+    """The batched form (the survey's C4): 4096 indexes, one JSON line."""
+    import torch
+
+    import paper_2506_01576_gb300 as gi
+    gi.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    r = batched_measure(gi, torch, dev, a.batch_indexes, a.batch_k, a.steps, a.warmup,
+                        tune=not a.no_extras, per_index=not a.no_extras)
+    B, m = r["indexes"], r["probes_total"]
     print(json.dumps({
         "metric": "batched lookups/s (%d indexes, 2^8..2^20 u64 keys, 2^10..2^18 probes each, hit 0.75)" % B,
-        "value": m / (graph_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": graph_ms, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+        "value": r["lookups_per_s"], "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": r["graph_step_ms"], "higher_is_better": True, "dtype": "u64", "data": "synthetic",
         "config": {"workload": "batched build + lookup, one CUDA graph", "indexes": B,
-                   "keys_total": int(off[-1]), "probes_total": m, "k": a.batch_k},
-        "graph_step_ms": graph_ms, "build_ms": build_ms, "lookup_ms": lookup_ms,
-        "lookup_only_per_s": m / (lookup_ms / 1e3), "lookup_tuned": tuned,
-        "per_index_launches_ms": per_ms, "speedup_vs_per_index": per_ms and per_ms / graph_ms,
-        "per_index_results_identical": same, "gpu_launches": int(launches),
-        "clocks": clk.summary()}), flush=True)
-    gi.gi_batch_destroy(batch)
+                   "keys_total": r["keys_total"], "probes_total": m, "k": a.batch_k},
+        "gpu_launches": r["kernels_per_graph"] * a.steps, **r}), flush=True)
 
 
 def _ev_ms(torch, fn, reps, warm=2):
@@ -713,6 +781,41 @@ def _ev_ms(torch, fn, reps, warm=2):
     e1.record()
     e1.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+def ranges_leg(gi, torch, dev, E=16, steps=5, layouts=None):
+    """2^26 unique u32 keys, 2^24 inclusive ranges with E expected rows (CSR output),
+    one call (count + scan + fill) per layout; sampled parity by numpy."""
+    n, m = 1 << 26, 1 << 24
+    seed = W.seed_for(2, 26)
+    keys = W.unique_keys(n, 32, seed)
+    kd = torch.from_numpy(keys.view(np.int32)).to(dev)
+    rd = torch.arange(n, dtype=torch.int32, device=dev)
+    lo, hi, w = W.ranges_with_expected_rows(n, m, E, 32, seed + E)
+    lod, hid = torch.from_numpy(lo.view(np.int32)).to(dev), torch.from_numpy(hi.view(np.int32)).to(dev)
+    off = torch.empty(m + 1, dtype=torch.int64, device=dev)
+    order = np.argsort(keys, kind="stable")
+    sk = keys[order]
+    samp = np.random.default_rng(5).choice(m, size=4096, replace=False)
+    out = {}
+    for name, layout, k in layouts or (("sorted", gi.GI_SORTED, 0), ("EBS", gi.GI_EYTZINGER, 2),
+                                       ("EKS k=16", gi.GI_EYTZINGER_KARY, 16)):
+        idx = gi.gi_build(kd, rd, layout | gi.GI_KEY_U32, k)
+        gi.gi_range_lookup(idx, lod, hid, off)
+        total = int(off[-1].item())
+        rows = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+        ms = _ev_ms(torch, lambda: gi.gi_range_lookup(idx, lod, hid, off, rows), steps)
+        o = off.cpu().numpy().view(np.uint64)
+        rr = rows.cpu().numpy().view(np.uint32)
+        ok = True
+        for i in samp:
+            a, b = np.searchsorted(sk, lo[i], "left"), np.searchsorted(sk, hi[i], "right")
+            ok &= bool(o[i + 1] - o[i] == b - a) and bool(np.array_equal(rr[o[i]:o[i + 1]], order[a:b]))
+        out[name] = {"ms": ms, "ranges_per_s": m / ms * 1e3, "rows_per_s": total / ms * 1e3, "rows": total,
+                     "sampled_parity_4096": ok}
+        del rows
+        gi.gi_destroy(idx)
+    return {"n_keys": n, "key": "u32", "ranges": m, "expected_rows": E, "width": int(w), "layouts": out}
 
 
 def run_ranges(a):
@@ -932,114 +1035,101 @@ def run_skew(a):
         gi.gi_destroy(v)
 
 
-def run_serving(a):
-    """Serving form: resident indexes (2^20..2^27 u64 keys, log-uniform sizes), Poisson
-    arrivals, requests of 1..2^16 probes (log-uniform), 80% point (hit rate 0.5), 20%
-    range (16 expected rows).  For each offered load: the continuous-batching server
-    (gi_server_*) and, as the baseline, one request at a time through gi_point_lookup /
-    gi_range_lookup (a FIFO queue alone).  Reports lookups/s and p50/p99 latency."""
-    import threading
-
-    import torch
-
-    import paper_2506_01576_gb300 as gi
-    gi.load()
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    rng = np.random.default_rng(77)
-    NI = a.serve_indexes
-    sizes = np.exp2(rng.uniform(a.serve_min_log, a.serve_max_log, size=NI)).astype(np.int64)
+def serving_sweep(gi, torch, dev, n_indexes, min_log, max_log, rates, seconds, pool_size, repeats=1,
+                  serial_max_requests=20000, seed=77, threads=4):
+    """The serving form at several offered loads, driven by the library's native
+    open-loop load generator: resident indexes of log-uniform sizes (u64 keys, EKS
+    k = 5), Poisson arrivals, requests of 1..2^16 probes (log-uniform), 80% point
+    (hit rate 0.5), 20% range (16 expected rows).  For each load: the continuous-
+    batching server (gi_server_replay) and, as the baseline, one request at a time
+    through the plain calls (gi_replay_serial; its schedule cut to the first
+    `serial_max_requests` arrivals past its capacity).  Returns one dict per run."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp2(rng.uniform(min_log, max_log, size=n_indexes)).astype(np.int64)
     idx, pool = [], []
     layout = gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64
-    per_index_requests = max(8, 3000 // NI)
+    per_index = max(4, pool_size // n_indexes)
+    pin = lambda x: torch.from_numpy(x.view(np.int64)).pin_memory()
     for i, n in enumerate(sizes):
         keys = W.unique_keys(int(n), 64, W.seed_for(5, 27, i))
         kd = torch.from_numpy(keys.view(np.int64)).to(dev)
         rd = torch.arange(int(n), dtype=torch.int32, device=dev)
         idx.append(gi.gi_build(kd, rd, layout, 5))
         del kd, rd
-        for _ in range(per_index_requests):
+        for _ in range(per_index):
             m = int(np.exp2(rng.uniform(0, 16)))
-            pin = lambda x: torch.from_numpy(x.view(np.int64)).pin_memory()
             if rng.random() < 0.8:
                 q = W.point_probes(keys, m, 0.5, 64, W.seed_for(5, 27, i), int(rng.integers(1 << 30)))
-                pool.append(("point", i, pin(q), torch.empty(m, dtype=torch.int32).pin_memory()))
+                pool.append((i, gi.GI_REQ_POINT, pin(q), torch.empty(m, dtype=torch.int32).pin_memory(),
+                             None, None, 0))
             else:
                 lo, hi, _ = W.ranges_with_expected_rows(int(n), m, 16, 64, int(rng.integers(1 << 30)))
-                cap = 64 * m + 256
-                pool.append(("range", i, pin(lo), pin(hi), torch.empty(m + 1, dtype=torch.int64).pin_memory(),
-                             torch.empty(cap, dtype=torch.int32).pin_memory(), cap))
+                cap = 32 * m + 1024
+                pool.append((i, gi.GI_REQ_RANGE, pin(lo), torch.empty(cap, dtype=torch.int32).pin_memory(),
+                             pin(hi), torch.empty(m + 1, dtype=torch.int64).pin_memory(), cap))
         del keys
     torch.cuda.synchronize()
     order = rng.permutation(len(pool))
-    mean_m = float(np.mean([p[2].numel() for p in pool]))
+    sizes_m = np.array([p[2].numel() for p in pool])
+    mean_m = float(np.mean(sizes_m))
+    results = []
 
-    def schedule(rate):
-        t, out = 0.0, []
-        r2 = np.random.default_rng(int(rate))
-        while t < a.serve_seconds:
-            t += r2.exponential(1.0 / rate)
-            out.append((t, pool[order[len(out) % len(pool)]]))
-        return out
+    def schedule(rate, rep, limit=None):
+        r2 = np.random.default_rng(int(rate) * 7 + rep)
+        cnt = int(rate * seconds * 1.2) + 16
+        t = np.cumsum(r2.exponential(1.0 / rate, size=cnt))
+        t = t[t < seconds]
+        if limit is not None:
+            t = t[:limit]
+        which = order[np.arange(len(t)) % len(pool)]
+        reqs = gi.make_requests([pool[j] for j in which])
+        return reqs, (t * 1e9).astype(np.int64), int(sizes_m[which].sum())
 
-    def summarize(mode, rate, lat, probes, wall):
-        lat = np.array(lat) / 1e6
-        print(json.dumps({"workload": "serve", "mode": mode, "offered_requests_per_s": rate,
-                          "offered_lookups_per_s": rate * mean_m, "requests": len(lat),
-                          "lookups_per_s": probes / wall, "p50_ms": float(np.percentile(lat, 50)),
-                          "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall,
-                          "indexes": NI, "keys_total": int(sizes.sum())}), flush=True)
+    def summary(mode, rate, rep, lat, st, wall, probes, nreq):
+        ok = lat >= 0
+        l = lat[ok] / 1e6
+        return {"mode": mode, "offered_requests_per_s": rate, "offered_lookups_per_s": rate * mean_m,
+                "repeat": rep, "requests": int(nreq), "lookups_per_s": probes / wall,
+                "requests_per_s": nreq / wall, "p50_ms": float(np.percentile(l, 50)),
+                "p99_ms": float(np.percentile(l, 99)), "wall_s": wall,
+                "capacity_exceeded": int((st == gi.GI_ERR_CAPACITY).sum())}
 
-    rates = [float(x) for x in a.serve_rates.split(",")]
     server = gi.gi_server_create(idx, 2 << 30, 3)
     for rate in rates:
-        sched = schedule(rate)
-        tickets = [None] * len(sched)
-        t0 = time.perf_counter()
-
-        def producer():
-            for j, (t, req) in enumerate(sched):
-                d = t - (time.perf_counter() - t0)
-                if d > 0:
-                    time.sleep(d)
-                if req[0] == "point":
-                    tickets[j] = gi.gi_server_submit(server, req[1], gi.GI_REQ_POINT, req[2], out_rowids=req[3])
-                else:
-                    tickets[j] = gi.gi_server_submit(server, req[1], gi.GI_REQ_RANGE, req[2], out_rowids=req[5],
-                                                     hi=req[3], out_offsets=req[4], rows_capacity=req[6])
-
-        th = threading.Thread(target=producer)
-        th.start()
-        lat, probes = [], 0
-        for j in range(len(sched)):
-            while tickets[j] is None:
-                time.sleep(0.0001)
-            st, ts, td = gi.gi_server_wait(server, tickets[j])
-            lat.append(td - ts)
-            probes += sched[j][1][2].numel()
-        th.join()
-        summarize("server (continuous batching)", rate, lat, probes, time.perf_counter() - t0)
+        for rep in range(repeats):
+            reqs, arr, probes = schedule(rate, rep)
+            lat, st, wall = gi.gi_server_replay(server, reqs, arr, threads)
+            results.append(summary("server", rate, rep, lat, st, wall, probes, len(arr)))
     gi.gi_server_destroy(server)
-    # baseline: one request at a time, in arrival order, through the plain calls
     for rate in rates:
-        sched = schedule(rate)
-        t0 = time.perf_counter()
-        lat, probes = [], 0
-        for t, req in sched:
-            now = time.perf_counter() - t0
-            if now > 4 * a.serve_seconds:  # saturated: the queue only grows
-                break
-            if t > now:
-                time.sleep(t - now)
-            if req[0] == "point":
-                gi.gi_point_lookup(idx[req[1]], req[2], req[3])
-            else:
-                gi.gi_range_lookup(idx[req[1]], req[2], req[3], req[4], req[5])
-            lat.append(((time.perf_counter() - t0) - t) * 1e9)
-            probes += req[2].numel()
-        summarize("one request at a time", rate, lat, probes, time.perf_counter() - t0)
+        for rep in range(repeats):
+            reqs, arr, probes = schedule(rate, rep, serial_max_requests)
+            lat, st, wall = gi.gi_replay_serial(idx, reqs, arr)
+            results.append(summary("one at a time", rate, rep, lat, st, wall, probes, len(arr)))
     for ix in idx:
         gi.gi_destroy(ix)
+    meta = {"indexes": n_indexes, "keys_total": int(sizes.sum()), "index_log2_range": [min_log, max_log],
+            "mean_probes_per_request": mean_m, "request_pool": len(pool), "seconds_per_load": seconds,
+            "submit_threads": threads}
+    return meta, results
+
+
+def run_serving(a):
+    """Serving form (the survey's C5): 64 resident indexes of 2^20..2^27 u64 keys, an
+    offered-load sweep past saturation, every load twice; one JSON line per run."""
+    import torch
+
+    import paper_2506_01576_gb300 as gi
+    gi.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rates = [float(x) for x in a.serve_rates.split(",")]
+    meta, results = serving_sweep(gi, torch, dev, a.serve_indexes, a.serve_min_log, a.serve_max_log, rates,
+                                  a.serve_seconds, 3000, repeats=2)
+    for r in results:
+        r.update(meta)
+        r["workload"] = "serve"
+        print(json.dumps(r), flush=True)
 
 
 if __name__ == "__main__":

@@ -308,7 +308,8 @@ int gi_coalescing_probe(const uint32_t* buf, uint64_t entries, uint32_t threads,
  * (e.g. one per partition of a join) with one launch per phase instead of one per
  * index.  Index b holds pairs key_offsets[b] .. key_offsets[b+1]-1 of the
  * concatenated key/rowID arrays.  Layouts: GI_EYTZINGER_KARY with k in
- * {3, 5, 9, 17}, or GI_SORTED; either key width.
+ * {2, 3, 5, 9, 17}, or GI_SORTED, for every index; or a fan-out per index
+ * (gi_batch_set_fanouts below); either key width.
  *
  * gi_batch_create -- sizes and allocates all device memory of the batch from the
  *   HOST array key_offsets[B+1] (key_offsets[0] = 0, non-decreasing, each index
@@ -362,6 +363,43 @@ int gi_batch_tune(gi_batch* batch, const void* queries, const uint64_t* query_of
 void gi_batch_destroy(gi_batch* batch);
 
 /*
+ * Per-index fan-out.  The paper's composite strategy (Section 9: Eytzinger order
+ * while the index fits in L2, k-ary above) is a choice per index size; a batch of
+ * indexes of uneven size makes it per index.  Each index of a batch is laid out
+ * with its own fan-out k_i: 0 (sorted order, binary search), 2 (Eytzinger order,
+ * stored 0-based as the k-ary layout with k = 2), 3, 5, 9 or 17.  The build writes
+ * every index in its own order and the lookup's work items dispatch on it; build
+ * and lookup stay one launch sequence, free of allocation and host round trips
+ * (capturable).
+ * gi_batch_set_fanouts -- ks: B host fan-outs, or NULL for the automatic choice
+ *   per size class floor(log2 n_i): the one gi_batch_tune_fanouts recorded for the
+ *   batch's key width, else k = 3 up to 2^17 key bytes, 2 up to 2^22 key bytes,
+ *   5 above (measured on single u64 indexes).  Takes effect at the next
+ *   gi_batch_build (the indexes must be built again).  Synchronous (waits for the
+ *   batch's stream); call it outside stream capture.
+ *   Errors: GI_ERR_INVALID (a fan-out outside the set), GI_ERR_CUDA.
+ * gi_batch_get_fanouts -- the B fan-outs in use into ks_out (host).
+ * gi_batch_tune_fanouts -- the autotuner for the fan-outs: gathers the probes of
+ *   each size class, builds the batch with every candidate fan-out (2, 3, 5, 9, 17)
+ *   in turn and times each class's lookups alone (best of `reps`, 0: 5), then picks
+ *   per class the fastest.  keys/rowids/queries/query_offsets as in gi_batch_build
+ *   and gi_batch_point_lookup (DEVICE memory).  flags: GI_TUNE_APPLY leaves the
+ *   chosen fan-outs set, otherwise those on entry; GI_TUNE_RECORD stores the
+ *   per-class choice for the automatic choice of later batches with this key
+ *   width.  Either way the batch is left built.  ks_out (may be NULL): the chosen
+ *   B fan-outs; class_ms (may be NULL): 64 x 5 doubles, the best time of size class
+ *   c under candidate j at [c * 5 + j] (-1 where the class has no probes).
+ *   Allocates scratch for the call; synchronous.
+ * gi_batch_fanout_table_clear -- forget every recorded per-class choice.
+ */
+int gi_batch_set_fanouts(gi_batch* batch, const uint32_t* ks);
+int gi_batch_get_fanouts(const gi_batch* batch, uint32_t* ks_out);
+int gi_batch_tune_fanouts(gi_batch* batch, const void* keys, const uint32_t* rowids,
+                          const void* queries, const uint64_t* query_offsets, uint64_t m,
+                          uint32_t reps, int flags, uint32_t* ks_out, double* class_ms);
+void gi_batch_fanout_table_clear(void);
+
+/*
  * Serving form: resident indexes answer a stream of requests with continuous
  * batching.  The paper measures batches of lookups; this form serves requests
  * that arrive at any time from many client threads.
@@ -407,6 +445,32 @@ int gi_server_wait(gi_server* server, uint64_t ticket, int64_t* submit_ns, int64
 int gi_server_stats(const gi_server* server, uint64_t* batches, uint64_t* requests,
                     uint64_t* probes);
 void gi_server_destroy(gi_server* server);
+
+/*
+ * Load generators for the serving form (open loop: arrivals do not wait for
+ * completions), so that latency is measured without an interpreter's jitter.
+ *   reqs[i] is submitted at arrival_ns[i] nanoseconds (>= 0; any order) after a
+ *   common start time set a few milliseconds after the call begins.
+ *   latency_ns[i]: completion time minus that scheduled arrival (queueing and
+ *   service together), or -1 if the request was not accepted; status[i] (may be
+ *   NULL): its return code (GI_ERR_CAPACITY for range rows beyond rows_capacity).
+ *   wall_s (may be NULL): seconds from the start time to the last completion.
+ *   Returns GI_OK, or the first failure other than GI_ERR_CAPACITY.
+ * gi_server_replay -- `threads` native threads (1..64) submit to the server,
+ *   request i by thread i mod threads; this thread collects the completions.
+ *   Latencies come from the server's completion times (gi_server_wait).
+ * gi_replay_serial -- the baseline without the server: one thread takes the
+ *   requests in index order, each at its arrival time or as soon as the previous
+ *   one is done, through gi_point_lookup / gi_range_lookup on indexes[reqs[i].index]
+ *   with the request's host buffers (ranges by the two-call protocol: offsets,
+ *   then rows if they fit rows_capacity).
+ */
+int gi_server_replay(gi_server* server, const gi_request* reqs, const int64_t* arrival_ns,
+                     uint64_t count, uint32_t threads, int64_t* latency_ns, int* status,
+                     double* wall_s);
+int gi_replay_serial(gi_index* const* indexes, uint32_t nindexes, const gi_request* reqs,
+                     const int64_t* arrival_ns, uint64_t count, int64_t* latency_ns, int* status,
+                     double* wall_s);
 
 /*
  * gi_range_lookup_noalloc -- gi_range_lookup for callers that must not allocate.

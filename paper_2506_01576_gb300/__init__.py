@@ -31,9 +31,11 @@ __all__ = [
     "gi_range_lookup_noalloc", "GI_NOALLOC_MAX_RANGES",
     "Batch", "gi_batch_create", "gi_batch_set_stream", "gi_batch_build", "gi_batch_point_lookup",
     "gi_batch_sync", "gi_batch_copy_index", "gi_batch_set_option", "gi_batch_footprint_bytes",
-    "gi_batch_destroy", "GI_BATCH_OPT_CHUNK", "GI_BATCH_OPT_BLOCKS_PER_SM", "GI_BATCH_OPT_SMEM_BUDGET",
+    "gi_batch_destroy", "gi_batch_set_fanouts", "gi_batch_get_fanouts", "gi_batch_tune_fanouts",
+    "gi_batch_fanout_table_clear", "GI_BATCH_OPT_CHUNK", "GI_BATCH_OPT_BLOCKS_PER_SM", "GI_BATCH_OPT_SMEM_BUDGET",
     "Server", "gi_request", "gi_server_create", "gi_server_submit", "gi_server_wait", "gi_server_stats",
     "gi_server_destroy", "GI_REQ_POINT", "GI_REQ_RANGE", "GI_ERR_CAPACITY",
+    "make_requests", "gi_server_replay", "gi_replay_serial",
     "gi_tune_result", "gi_tune", "gi_tune_table_get", "gi_tune_table_clear", "gi_batch_tune",
     "GI_TUNE_APPLY", "GI_TUNE_RECORD", "gi_build_tuned", "gi_tune_table_layout", "gi_debug_fail_alloc",
 ]
@@ -120,11 +122,19 @@ def load(build_if_missing: bool = False):
         "gi_batch_set_option": (I, [P, I, I64]),
         "gi_batch_footprint_bytes": (U64, [P]),
         "gi_batch_destroy": (None, [P]),
+        "gi_batch_set_fanouts": (I, [P, P]),
+        "gi_batch_get_fanouts": (I, [P, P]),
+        "gi_batch_tune_fanouts": (I, [P, P, P, P, P, U64, U32, I, P, P]),
+        "gi_batch_fanout_table_clear": (None, []),
         "gi_server_create": (I, [ctypes.POINTER(P), U32, U64, U32, ctypes.POINTER(P)]),
         "gi_server_submit": (I, [P, ctypes.POINTER(gi_request), ctypes.POINTER(U64)]),
         "gi_server_wait": (I, [P, U64, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "gi_server_stats": (I, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64)]),
         "gi_server_destroy": (None, [P]),
+        "gi_server_replay": (I, [P, ctypes.POINTER(gi_request), P, U64, U32, P, P,
+                                 ctypes.POINTER(ctypes.c_double)]),
+        "gi_replay_serial": (I, [ctypes.POINTER(P), U32, ctypes.POINTER(gi_request), P, U64, P, P,
+                                 ctypes.POINTER(ctypes.c_double)]),
         "gi_tune": (I, [P, P, U64, U32, I, ctypes.POINTER(gi_tune_result)]),
         "gi_tune_table_get": (I, [I, U32, U64, ctypes.POINTER(I64), ctypes.POINTER(I)]),
         "gi_tune_table_clear": (None, []),
@@ -311,6 +321,36 @@ def gi_batch_destroy(batch: Batch) -> None:
     batch.close()
 
 
+def gi_batch_set_fanouts(batch: Batch, ks=None) -> None:
+    """Fan-out of every index (0 sorted, 2, 3, 5, 9, 17); None: by size class."""
+    import numpy as _np
+    arr = None if ks is None else _np.ascontiguousarray(ks, dtype=_np.uint32)
+    _check(load().gi_batch_set_fanouts(batch.handle, None if arr is None else arr.ctypes.data))
+
+
+def gi_batch_get_fanouts(batch: Batch, B: int):
+    import numpy as _np
+    out = _np.zeros(B, dtype=_np.uint32)
+    _check(load().gi_batch_get_fanouts(batch.handle, out.ctypes.data))
+    return out
+
+
+def gi_batch_tune_fanouts(batch: Batch, B: int, keys, rowids, queries, query_offsets, reps: int = 0,
+                          flags: int = 0):
+    """Per-size-class fan-out tuner; returns (chosen fan-outs [B], class_ms [64, 5])."""
+    import numpy as _np
+    ks = _np.zeros(B, dtype=_np.uint32)
+    cms = _np.zeros(64 * 5, dtype=_np.float64)
+    _check(load().gi_batch_tune_fanouts(batch.handle, _ptr(keys), _ptr(rowids), _ptr(queries),
+                                        _ptr(query_offsets), _len(queries), reps, flags,
+                                        ks.ctypes.data, cms.ctypes.data))
+    return ks, cms.reshape(64, 5)
+
+
+def gi_batch_fanout_table_clear() -> None:
+    load().gi_batch_fanout_table_clear()
+
+
 class Server:
     """Handle of a serving engine (owns the C gi_server*)."""
 
@@ -360,6 +400,49 @@ def gi_server_wait(server: Server, ticket: int):
     if rc not in (GI_OK, GI_ERR_CAPACITY):
         _check(rc)
     return rc, int(a.value), int(b.value)
+
+
+def make_requests(reqs):
+    """A ctypes array of gi_request from tuples (index, kind, keys, out_rowids, hi,
+    out_offsets, rows_capacity) of host buffers (torch CPU tensors or numpy arrays)."""
+    arr = (gi_request * len(reqs))()
+    for i, (index, kind, keys, out_rowids, hi, out_offsets, cap) in enumerate(reqs):
+        arr[i] = gi_request(index, kind, _len(keys), _ptr(keys), _ptr(hi), _ptr(out_rowids),
+                            _ptr(out_offsets), cap)
+    return arr
+
+
+def gi_server_replay(server: Server, requests, arrival_ns, threads: int = 4):
+    """Open-loop replay from native threads: request i at arrival_ns[i] (int64 numpy
+    array).  Returns (latency_ns, status, wall_s); latency -1 if not accepted."""
+    import numpy as _np
+    arr = requests if isinstance(requests, ctypes.Array) else make_requests(requests)
+    n = len(arr)
+    arrival = _np.ascontiguousarray(arrival_ns, dtype=_np.int64)
+    lat = _np.zeros(n, dtype=_np.int64)
+    st = _np.zeros(n, dtype=_np.int32)
+    wall = ctypes.c_double()
+    rc = load().gi_server_replay(server.handle, arr, arrival.ctypes.data, n, threads, lat.ctypes.data,
+                                 st.ctypes.data, ctypes.byref(wall))
+    _check(rc)
+    return lat, st, float(wall.value)
+
+
+def gi_replay_serial(indexes, requests, arrival_ns):
+    """The baseline of gi_server_replay: one native thread, the plain calls, one
+    request at a time.  Returns (latency_ns, status, wall_s)."""
+    import numpy as _np
+    arr = requests if isinstance(requests, ctypes.Array) else make_requests(requests)
+    n = len(arr)
+    ix = (ctypes.c_void_p * len(indexes))(*[i.handle for i in indexes])
+    arrival = _np.ascontiguousarray(arrival_ns, dtype=_np.int64)
+    lat = _np.zeros(n, dtype=_np.int64)
+    st = _np.zeros(n, dtype=_np.int32)
+    wall = ctypes.c_double()
+    rc = load().gi_replay_serial(ix, len(indexes), arr, arrival.ctypes.data, n, lat.ctypes.data,
+                                 st.ctypes.data, ctypes.byref(wall))
+    _check(rc)
+    return lat, st, float(wall.value)
 
 
 def gi_server_stats(server: Server):

@@ -12,7 +12,9 @@
 #include <string>
 #include <vector>
 
+#include "gi_alloc.h"
 #include "gi_internal.cuh"
+#include "gi_ptr.h"
 
 // ---------------------------------------------------------------- the index object
 struct GiStaging {
@@ -92,16 +94,25 @@ struct DeviceScope {
 
 enum PtrKind { kDevice, kHost, kBad };
 
-PtrKind pointer_kind(const void* p) {
+// How a call treats pointer p given the index's device `dev`: in place (device
+// memory of `dev`, or managed memory), staged (host memory), or kBad (NULL, or
+// device memory of another device, which a kernel on `dev` must not be given).
+PtrKind pointer_kind(const void* p, int dev) {
   if (!p) return kBad;
   cudaPointerAttributes a;
   cudaError_t e = cudaPointerGetAttributes(&a, p);
+  int type = -1, pdev = -1;
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return kHost;
+  } else {
+    type = (int)a.type;
+    pdev = a.device;
   }
-  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return kDevice;
-  return kHost;
+  switch (gi::classify_pointer(type, pdev, dev)) {
+    case gi::kPtrDevice: return kDevice;
+    case gi::kPtrHost: return kHost;
+    default: return kBad;
+  }
 }
 
 // The device's view of page-locked (registered or cudaHostAlloc'ed) host memory,
@@ -115,11 +126,10 @@ const void* mapped_host(const void* p) {
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
-size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// key arrays carry room for the empty slot and for whole-node vector reads past n
-size_t key_alloc_bytes(uint64_t n, int key_bytes) { return round256((n + 1 + 64) * key_bytes + 64); }
-size_t row_alloc_bytes(uint64_t n) { return round256((n + 64) * 4); }
+using gi::key_alloc_bytes;  // key arrays: room for the empty slot and whole-node reads past n
+using gi::key_used_bytes;
+using gi::round256;
+using gi::row_alloc_bytes;
 
 // Page-locked host scratch of the calling thread for the build's small
 // device-to-host reads (digit flags and counts): copies into pageable memory would
@@ -256,18 +266,23 @@ gi::LookupCfg resolve_cfg(const gi_index* idx) {
   // the per-rank map measured faster except for 256-row ranges on 17-ary trees
   c.range_fill = o[GI_OPT_RANGE_FILL] >= 0 ? (int)o[GI_OPT_RANGE_FILL] : 0;
   c.reorder = o[GI_OPT_REORDER] >= 0 ? (int)o[GI_OPT_REORDER] : 0;
+  int dev = idx->device, l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
   if (o[GI_OPT_HOT_LEVELS] >= 0) {
     c.hot_levels = (int)o[GI_OPT_HOT_LEVELS];
   } else {
-    // evict-last for the top levels that fit in a quarter of L2.  Measured at
-    // 2^26 u64 keys, k = 5: marking the levels within a quarter of L2 (0..8,
-    // 16 MB) is the best setting; marking those within two thirds (0..9, 78 MB)
-    // is 7% slower than no hints at all, as the evict-last lines then crowd out
-    // the lines of the level below that the lookups reuse.
-    int dev = idx->device, l2 = 0;
-    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
-    c.hot_levels = gi::levels_within(idx->geom, idx->key_bytes, (uint64_t)l2 / 4);
+    // evict-last for the top levels that fit in 5/8 of L2.  Measured at 2^26 u64
+    // keys, k = 5, 2^27 probes, with the deep levels kept out of L1 (below):
+    // levels 0..9 (78 MB of the 135 MB L2) evict-last, 5.22 ms; 0..8 (16 MB),
+    // 5.79 ms; 0..7, 5.88 ms.  (While every level was also allocated in L1,
+    // 0..8 and 0..9 measured within 3% of each other.)
+    c.hot_levels = gi::levels_within(idx->geom, idx->key_bytes, (uint64_t)l2 * 5 / 8);
   }
+  // top levels read through L1: those within 128 KB of keys (the L1 of an SM
+  // holds them while no shared memory is used).  Measured at 2^26 u64 keys, k = 5:
+  // levels 0..5 (125 KB) through L1 and the rest not allocated there, 5.78 ms;
+  // every level allocated, 5.97 ms; 0..3, 5.88 ms; 0..7, 6.00 ms.
+  c.l1_levels = gi::levels_within(idx->geom, idx->key_bytes, 128u << 10);
   return c;
 }
 
@@ -542,7 +557,9 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
     *out = idx;
     return GI_OK;
   }
-  const PtrKind kk = pointer_kind(keys), rk = pointer_kind(rowids);
+  const PtrKind kk = pointer_kind(keys, idx->device), rk = pointer_kind(rowids, idx->device);
+  if (kk == kBad || rk == kBad)
+    return bail(fail(GI_ERR_INVALID, "gi_build: keys or rowids are device memory of another device"));
   void* bk[2] = {nullptr, nullptr};
   uint32_t* bv[2] = {nullptr, nullptr};
   void* scratch = nullptr;
@@ -689,7 +706,7 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   }
   {
     // slots past the last key hold the maximum key: whole-node reads need no bounds checks
-    const size_t used = (n + (lay == GI_EYTZINGER ? 1 : 0)) * kb;
+    const size_t used = key_used_bytes(n, kb, lay == GI_EYTZINGER);
     GI_TRY2(cudaMemsetAsync((char*)idx->keys + used, 0xFF, kbytes - used, s), "key padding");
   }
   free_tmp();
@@ -716,7 +733,9 @@ int gi_point_lookup(const gi_index* cidx, const void* queries, uint64_t m, uint3
   if (!queries || !out_rowids) return fail(GI_ERR_INVALID, "gi_point_lookup: NULL pointer");
   DeviceScope ds(idx->device);
   const gi::LookupCfg c = resolve_cfg(idx);
-  const PtrKind qk = pointer_kind(queries), ok = pointer_kind(out_rowids);
+  const PtrKind qk = pointer_kind(queries, idx->device), ok = pointer_kind(out_rowids, idx->device);
+  if (qk == kBad || ok == kBad)
+    return fail(GI_ERR_INVALID, "gi_point_lookup: a buffer is device memory of another device");
   if (qk == kDevice && ok == kDevice) {
     GI_CUDA(launch_point(idx, c, queries, m, out_rowids, idx->stream), "point lookup");
     return GI_OK;
@@ -761,9 +780,12 @@ int gi_range_lookup(const gi_index* cidx, const void* lo, const void* hi, uint64
   const gi::LookupCfg c = resolve_cfg(idx);
   const int kb = idx->key_bytes;
   cudaStream_t s = idx->stream;
-  const PtrKind lk = m ? pointer_kind(lo) : kDevice, hk = m ? pointer_kind(hi) : kDevice;
-  const PtrKind ofk = pointer_kind(out_offsets);
-  const PtrKind rk = out_rowids ? pointer_kind(out_rowids) : kDevice;
+  const int dv = idx->device;
+  const PtrKind lk = m ? pointer_kind(lo, dv) : kDevice, hk = m ? pointer_kind(hi, dv) : kDevice;
+  const PtrKind ofk = pointer_kind(out_offsets, dv);
+  const PtrKind rk = out_rowids ? pointer_kind(out_rowids, dv) : kDevice;
+  if (lk == kBad || hk == kBad || ofk == kBad || rk == kBad)
+    return fail(GI_ERR_INVALID, "gi_range_lookup: a buffer is device memory of another device");
   auto run = [&](const void* dlo, const void* dhi, uint64_t* doff, uint32_t* drows,
                  bool ready) -> cudaError_t {
     if (kb == 4)
@@ -1012,8 +1034,10 @@ int gi_probe_random_sectors(const void* buf, uint64_t bytes, uint32_t chunk_byte
     return fail(GI_ERR_INVALID, "gi_probe_random_sectors: chunk must be 16..256 bytes, a power of two");
   if (((uintptr_t)buf & 255) || bytes < chunk_bytes)
     return fail(GI_ERR_INVALID, "gi_probe_random_sectors: buffer must be 256-byte aligned and hold a chunk");
-  if (pointer_kind(buf) != kDevice || pointer_kind(sink) != kDevice)
-    return fail(GI_ERR_INVALID, "gi_probe_random_sectors: buffers must be device memory");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (pointer_kind(buf, dev) != kDevice || pointer_kind(sink, dev) != kDevice)
+    return fail(GI_ERR_INVALID, "gi_probe_random_sectors: buffers must be device memory of the current device");
   GI_CUDA(gi::probe_random_sectors(buf, bytes, chunk_bytes, loads, seed, sink, (cudaStream_t)stream),
           "probe");
   return GI_OK;
@@ -1025,8 +1049,10 @@ int gi_coalescing_probe(const uint32_t* buf, uint64_t entries, uint32_t threads,
   if (!buf || !sink) return fail(GI_ERR_INVALID, "gi_coalescing_probe: NULL pointer");
   if (group == 0 || group > threads || group > entries || threads == 0)
     return fail(GI_ERR_INVALID, "gi_coalescing_probe: need 0 < group <= threads, group <= entries");
-  if (pointer_kind(buf) != kDevice || pointer_kind(sink) != kDevice)
-    return fail(GI_ERR_INVALID, "gi_coalescing_probe: buffers must be device memory");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (pointer_kind(buf, dev) != kDevice || pointer_kind(sink, dev) != kDevice)
+    return fail(GI_ERR_INVALID, "gi_coalescing_probe: buffers must be device memory of the current device");
   GI_CUDA(gi::coalescing_probe(buf, entries, threads, group, steps, seed, sink, (cudaStream_t)stream),
           "probe");
   return GI_OK;
@@ -1044,22 +1070,71 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[GI_NOALLOC_SCRA
 namespace {
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+struct NoAllocAddr {
+  void* ptr = nullptr;
+  unsigned long long ctx = 0;  // id of the context the address belongs to
+};
+NoAllocAddr g_noalloc_addr[kNoAllocMaxDevices];
 
-// Device address of the scratch array on `dev` (which must be current); looked
-// up once per device.
-int noalloc_scratch(int dev, void** out) {
+// Id of the calling thread's current CUDA context, unique for the life of the
+// process (a context made after cudaDeviceReset gets a new one); 0 if unknown.
+// Taken through the driver entry points the runtime hands out, so the library
+// needs no link against the driver library.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetId)f;
+    cudaGetLastError();
+  });
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array on `dev` (which must be current).  It is
+// looked up once per device and context: after a context change (for example a
+// cudaDeviceReset in the caller's process) the module, and with it the array, is
+// loaded anew at another address, which is looked up again.  The lookup may load
+// the module, which a stream capture in progress must not see: it is refused
+// while `s` is capturing.
+int noalloc_scratch(int dev, cudaStream_t s, void** out) {
   if (dev < 0 || dev >= kNoAllocMaxDevices)
     return fail(GI_ERR_INVALID, "gi_range_lookup_noalloc: device %d out of range", dev);
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  NoAllocAddr& a = g_noalloc_addr[dev];
+  if (!a.ptr || ctx == 0 || a.ctx != ctx) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      cudaGetLastError();
+      return fail(GI_ERR_INVALID,
+                  "gi_range_lookup_noalloc: the first call on a device (or after a context "
+                  "change) looks up the scratch address and must not run during stream "
+                  "capture; make one call before capturing");
+    }
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorUnknown,
                                                  "gi_range_lookup_noalloc: scratch address");
-    g_noalloc_ptr[dev] = p;
+    a.ptr = p;
+    a.ctx = ctx;
   }
-  *out = g_noalloc_ptr[dev];
+  *out = a.ptr;
   return GI_OK;
 }
 }  // namespace
@@ -1077,12 +1152,18 @@ extern "C" int gi_range_lookup_noalloc(const gi_index* idx, const void* lo, cons
     return fail(GI_ERR_INVALID, "gi_range_lookup_noalloc: scratch too small for %llu ranges",
                 (unsigned long long)m);
   DeviceScope ds(idx->device);
-  if ((m && (pointer_kind(lo) != kDevice || pointer_kind(hi) != kDevice)) ||
-      pointer_kind(out_offsets) != kDevice || (out_rowids && pointer_kind(out_rowids) != kDevice))
-    return fail(GI_ERR_INVALID, "gi_range_lookup_noalloc: every buffer must be device memory");
+  const int dv = idx->device;
+  if ((m && (pointer_kind(lo, dv) != kDevice || pointer_kind(hi, dv) != kDevice)) ||
+      pointer_kind(out_offsets, dv) != kDevice ||
+      (out_rowids && pointer_kind(out_rowids, dv) != kDevice))
+    return fail(GI_ERR_INVALID,
+                "gi_range_lookup_noalloc: every buffer must be device memory of the index's device");
   void* scratch = nullptr;
-  int rc = noalloc_scratch(idx->device, &scratch);
+  int rc = noalloc_scratch(idx->device, idx->stream, &scratch);
   if (rc != GI_OK) return rc;
+  // this call writes out_offsets and its own lower ranks, not the index's: a later
+  // gi_range_lookup must not take the two-call shortcut on counts from before
+  const_cast<gi_index*>(idx)->counts_valid = false;
   const gi::LookupCfg c = resolve_cfg(idx);
   // counts_ready = false: another call may have overwritten the shared scratch
   cudaError_t e = idx->key_bytes == 4

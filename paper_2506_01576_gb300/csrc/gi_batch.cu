@@ -26,11 +26,13 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "gi_internal.cuh"
 #include "gi_point_impl.cuh"
+#include "gi_ptr.h"
 
 namespace gi {
 
@@ -40,7 +42,7 @@ struct BatchDesc {
   uint32_t levels;       // tree levels (k-ary) / 0 for sorted
   uint32_t smem_levels;  // top levels pinned in shared memory for this index
   uint32_t smem_slots;   // slots copied to shared memory (0: none)
-  uint32_t pad;
+  uint32_t k;            // fan-out of this index (0: sorted)
 };
 
 namespace bt {
@@ -142,7 +144,23 @@ __device__ __forceinline__ uint32_t bs_one(const K* __restrict__ keys, const uin
   return (lo < d.n && base[lo] == x) ? rows[d.base + lo] : GI_MISS;
 }
 
-// KF == 0: sorted layout (binary search per index, no pinning)
+// One lookup in an index of a batch whose indexes each have their own fan-out
+// (d.k; 0 = sorted).  The work item, and so d.k, is the same for the whole CTA.
+template <class K>
+__device__ __forceinline__ uint32_t any_one(const K* __restrict__ keys, const uint32_t* __restrict__ rows,
+                                            const BatchDesc& d, const K* sm, K x) {
+  switch (d.k) {
+    case 2: return eks_one<K, 2>(keys, rows, d, sm, x);
+    case 3: return eks_one<K, 3>(keys, rows, d, sm, x);
+    case 5: return eks_one<K, 5>(keys, rows, d, sm, x);
+    case 9: return eks_one<K, 9>(keys, rows, d, sm, x);
+    case 17: return eks_one<K, 17>(keys, rows, d, sm, x);
+    default: return bs_one<K>(keys, rows, d, x);
+  }
+}
+
+// KF == 0: sorted layout (binary search per index, no pinning); KF == -1: each
+// index's own fan-out
 template <class K, int KF>
 __global__ void __launch_bounds__(256) k_batch_point(const K* __restrict__ keys,
                                                      const uint32_t* __restrict__ rows,
@@ -173,7 +191,7 @@ __global__ void __launch_bounds__(256) k_batch_point(const K* __restrict__ keys,
     const uint64_t q0 = qoff[b] + (w - cs[b]) * CH;
     const uint64_t q1 = min(q0 + CH, qoff[b + 1]);
     bool staged = true;
-    if (KF > 0 && d.smem_slots) {
+    if (KF != 0 && d.smem_slots) {
       const uint32_t bytes = (uint32_t)(((uint64_t)d.smem_slots * sizeof(K) + 15) & ~15ull);
       if (threadIdx.x == 0) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
@@ -197,7 +215,9 @@ __global__ void __launch_bounds__(256) k_batch_point(const K* __restrict__ keys,
     if (staged) {
       for (uint64_t i = q0 + threadIdx.x; i < q1; i += blockDim.x) {
         const K x = q[i];
-        if constexpr (KF > 0)
+        if constexpr (KF == -1)
+          out[i] = any_one<K>(keys, rows, d, sm, x);
+        else if constexpr (KF > 0)
           out[i] = eks_one<K, KF>(keys, rows, d, sm, x);
         else
           out[i] = bs_one<K>(keys, rows, d, x);
@@ -240,6 +260,8 @@ struct gi_batch {
   uint64_t* d_cs = nullptr;  // B+1 chunk starts of the last lookup
   void* hy_mem = nullptr;    // tables of the hybrid build
   gi::BatchHybrid hy{};
+  std::vector<uint32_t> kidx_host;  // fan-out of every index (0: sorted)
+  uint32_t* d_kidx = nullptr;
   int result = -1;
   // defaults: gi_batch_tune's choice on 4096 indexes of 2^8..2^20 u64 keys with
   // 2^10..2^18 probes each (1.41x over 1024 / 4 / 16384)
@@ -265,17 +287,41 @@ int bcuda(cudaError_t e, const char* what) {
                cudaGetErrorString(e));
 }
 
-bool is_device_ptr(const void* p) {
+// device (or managed) memory that kernels on device `dev` may be given
+bool is_device_ptr(const void* p, int dev) {
   if (!p) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return gi::classify_pointer((int)a.type, a.device, dev) == gi::kPtrDevice;
 }
 
-bool batch_kernel_k(uint32_t k) { return k == 3 || k == 5 || k == 9 || k == 17; }
+bool batch_kernel_k(uint32_t k) { return k == 2 || k == 3 || k == 5 || k == 9 || k == 17; }
+
+// Fan-outs chosen per size class (floor(log2 n)) by gi_batch_tune_fanouts with
+// GI_TUNE_RECORD, per key width; 0 = nothing recorded.  Process-wide.
+std::mutex g_fanout_mu;
+uint32_t g_fanout_table[2][64] = {};
+
+// The fan-out an index of n keys takes when the caller leaves it to the library:
+// the recorded choice of its size class, else the composite strategy measured
+// for single indexes of u64 keys (k = 3 for at most 2^14 keys = 128 KB, Eytzinger
+// order (k = 2) up to 2^19 keys = 4 MB, k = 5 above), by key bytes for u32 keys.
+uint32_t auto_fanout(int key_bytes, uint64_t n) {
+  if (n == 0) return 5;
+  const uint32_t cls = 63 - (uint32_t)__builtin_clzll(n);
+  {
+    std::lock_guard<std::mutex> lk(g_fanout_mu);
+    const uint32_t k = g_fanout_table[key_bytes == 8 ? 1 : 0][cls];
+    if (k) return k;
+  }
+  const uint64_t bytes = n * (uint64_t)key_bytes;
+  if (bytes <= (1ull << 17)) return 3;
+  if (bytes <= (1ull << 22)) return 2;
+  return 5;
+}
 
 // per-index pinning: the top levels whose slots fit in the budget (whole index if small)
 void choose_pinning(gi::BatchDesc& d, uint32_t k, int key_bytes, uint32_t budget) {
@@ -295,12 +341,36 @@ void choose_pinning(gi::BatchDesc& d, uint32_t k, int key_bytes, uint32_t budget
   }
 }
 
+// Per-index descriptors (levels, pinning, fan-out) from b->kidx_host, uploaded
+// with the fan-out table; the bucket-sort variant of the layout is made ready.
+cudaError_t apply_fanouts(gi_batch* b) {
+  bool uniform = true;
+  for (uint32_t i = 1; i < b->B; ++i) uniform &= b->kidx_host[i] == b->kidx_host[0];
+  b->k = uniform ? b->kidx_host[0] : gi::kBatchMixed;
+  b->layout = (uniform && b->k == 0) ? GI_SORTED : GI_EYTZINGER_KARY;
+  for (uint32_t i = 0; i < b->B; ++i) {
+    gi::BatchDesc& d = b->desc_host[i];
+    const uint32_t k = b->kidx_host[i];
+    d.k = k;
+    d.levels = k >= 2 ? gi::make_geom(d.n, k).levels : 0;
+    choose_pinning(d, k, b->key_bytes, b->smem_budget);
+  }
+  cudaError_t e = cudaMemcpy(b->d_desc, b->desc_host.data(), b->B * sizeof(gi::BatchDesc),
+                             cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_kidx, b->kidx_host.data(), b->B * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  b->hy.k = b->k;
+  b->hy.kidx = b->d_kidx;
+  if (e == cudaSuccess) e = gi::batch_local_sort_setup(b->key_bytes, b->hy.k);
+  return e;
+}
+
 void free_batch(gi_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   void* ptrs[] = {b->d_seg_start, b->d_seg_base, b->d_desc, b->d_tiles, b->d_chunks, b->keys,
                   b->rows, b->tmp_k[0], b->tmp_k[1], b->tmp_v[0], b->tmp_v[1], b->scratch,
-                  b->dflags, b->d_cs, b->hy_mem};
+                  b->dflags, b->d_cs, b->hy_mem, b->d_kidx};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaGetLastError();
@@ -318,7 +388,7 @@ int gi_batch_create(const uint64_t* key_offsets, uint32_t B, int layout, uint32_
   const int lay = layout & 0xFF, kw = layout & ~0xFF;
   if (kw != GI_KEY_U32 && kw != GI_KEY_U64) return bfail(GI_ERR_INVALID, "gi_batch_create: bad key width");
   if (lay == GI_EYTZINGER_KARY) {
-    if (!batch_kernel_k(k)) return bfail(GI_ERR_INVALID, "gi_batch_create: k must be 3, 5, 9 or 17");
+    if (!batch_kernel_k(k)) return bfail(GI_ERR_INVALID, "gi_batch_create: k must be 2, 3, 5, 9 or 17");
   } else if (lay == GI_SORTED) {
     k = 0;
   } else {
@@ -353,11 +423,8 @@ int gi_batch_create(const uint64_t* key_offsets, uint32_t B, int layout, uint32_
     d = gi::BatchDesc{};
     d.base = base[i];
     d.n = n;
-    if (lay == GI_EYTZINGER_KARY) {
-      d.levels = gi::make_geom(n, k).levels;
-      choose_pinning(d, k, kb, b->smem_budget);
-    }
   }
+  b->kidx_host.assign(B, lay == GI_SORTED ? 0u : k);
   const uint64_t slots_total = cur + align_slots;
   // tiles (radix) and chunks (histogram), host-built once
   const uint32_t tile = gi::batch_sort_tile(kb);
@@ -397,6 +464,7 @@ int gi_batch_create(const uint64_t* key_offsets, uint32_t B, int layout, uint32_
   GI_B(cudaMalloc((void**)&b->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(gi::BatchTile)), "batch tables");
   GI_B(cudaMalloc((void**)&b->d_chunks, std::max<size_t>(1, chunks.size()) * sizeof(gi::BatchTile)), "batch tables");
   GI_B(cudaMalloc((void**)&b->d_cs, (B + 1) * 8), "batch tables");
+  GI_B(cudaMalloc((void**)&b->d_kidx, B * sizeof(uint32_t)), "batch tables");
   GI_B(cudaMalloc((void**)&b->dflags, 256), "batch status");
   GI_B(cudaMemset(b->dflags, 0, 256), "batch status");
   {  // tables of the hybrid build: per-index plans and slot maps, MSD window counts
@@ -421,12 +489,10 @@ int gi_batch_create(const uint64_t* key_offsets, uint32_t B, int layout, uint32_
     b->hy.out_k = b->keys;
     b->hy.out_v = b->rows;
     b->hy.seg_base = b->d_seg_base;
-    b->hy.k = layout == GI_SORTED ? 0u : k;
-    GI_B(gi::batch_local_sort_setup(kb, b->hy.k), "batch bucket sort");
   }
+  GI_B(apply_fanouts(b), "batch tables");
   GI_B(cudaMemcpy(b->d_seg_start, key_offsets, (B + 1) * 8, cudaMemcpyHostToDevice), "batch tables");
   GI_B(cudaMemcpy(b->d_seg_base, base.data(), B * 8, cudaMemcpyHostToDevice), "batch tables");
-  GI_B(cudaMemcpy(b->d_desc, b->desc_host.data(), B * sizeof(gi::BatchDesc), cudaMemcpyHostToDevice), "batch tables");
   if (!tiles.empty())
     GI_B(cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(gi::BatchTile), cudaMemcpyHostToDevice), "batch tables");
   if (!chunks.empty())
@@ -448,8 +514,8 @@ int gi_batch_set_stream(gi_batch* b, void* stream) {
 int gi_batch_build(gi_batch* b, const void* keys, const uint32_t* rowids) {
   gi::set_last_error("");
   if (!b) return bfail(GI_ERR_INVALID, "gi_batch_build: NULL batch");
-  if (b->n && (!is_device_ptr(keys) || !is_device_ptr(rowids)))
-    return bfail(GI_ERR_INVALID, "gi_batch_build: keys and rowids must be device memory");
+  if (b->n && (!is_device_ptr(keys, b->device) || !is_device_ptr(rowids, b->device)))
+    return bfail(GI_ERR_INVALID, "gi_batch_build: keys and rowids must be device memory of the batch's device");
   cudaStream_t s = b->stream;
   // max-key padding after every index first: the bucket sort writes the layouts
   cudaError_t e = cudaMemsetAsync(b->keys, 0xFF, b->keys_bytes, s);
@@ -472,12 +538,13 @@ int gi_batch_point_lookup(gi_batch* b, const void* queries, const uint64_t* quer
   gi::set_last_error("");
   if (!b) return bfail(GI_ERR_INVALID, "gi_batch_point_lookup: NULL batch");
   if (m == 0) return GI_OK;
-  if (!is_device_ptr(queries) || !is_device_ptr(query_offsets) || !is_device_ptr(out_rowids))
-    return bfail(GI_ERR_INVALID, "gi_batch_point_lookup: queries, offsets and output must be device memory");
+  if (!is_device_ptr(queries, b->device) || !is_device_ptr(query_offsets, b->device) ||
+      !is_device_ptr(out_rowids, b->device))
+    return bfail(GI_ERR_INVALID, "gi_batch_point_lookup: queries, offsets and output must be device memory of the batch's device");
   cudaStream_t s = b->stream;
   gi::bt::k_chunk_starts<<<1, 1024, 0, s>>>(query_offsets, b->B, b->chunk, b->d_cs);
   const unsigned grid = (unsigned)(gi::sm_count() * b->blocks_per_sm);
-  const size_t smem = b->layout == GI_EYTZINGER_KARY ? b->smem_budget + 256 : 0;
+  const size_t smem = b->k != 0 ? b->smem_budget + 256 : 0;
 #define GI_BP(K, KF)                                                                           \
   gi::bt::k_batch_point<K, KF><<<grid, 256, smem, s>>>((const K*)b->keys, b->rows, b->d_desc, \
                                                        query_offsets, b->d_cs, b->B,         \
@@ -485,7 +552,9 @@ int gi_batch_point_lookup(gi_batch* b, const void* queries, const uint64_t* quer
                                                        b->dflags)
   if (b->key_bytes == 8) {
     switch (b->k) {
+      case gi::kBatchMixed: GI_BP(uint64_t, -1); break;
       case 0: GI_BP(uint64_t, 0); break;
+      case 2: GI_BP(uint64_t, 2); break;
       case 3: GI_BP(uint64_t, 3); break;
       case 5: GI_BP(uint64_t, 5); break;
       case 9: GI_BP(uint64_t, 9); break;
@@ -493,7 +562,9 @@ int gi_batch_point_lookup(gi_batch* b, const void* queries, const uint64_t* quer
     }
   } else {
     switch (b->k) {
+      case gi::kBatchMixed: GI_BP(uint32_t, -1); break;
       case 0: GI_BP(uint32_t, 0); break;
+      case 2: GI_BP(uint32_t, 2); break;
       case 3: GI_BP(uint32_t, 3); break;
       case 5: GI_BP(uint32_t, 5); break;
       case 9: GI_BP(uint32_t, 9); break;
@@ -539,6 +610,168 @@ int gi_batch_copy_index(const gi_batch* b, uint32_t i, void* keys_out, uint32_t*
   return GI_OK;
 }
 
+int gi_batch_set_fanouts(gi_batch* b, const uint32_t* ks) {
+  gi::set_last_error("");
+  if (!b) return bfail(GI_ERR_INVALID, "gi_batch_set_fanouts: NULL batch");
+  std::vector<uint32_t> next(b->B);
+  for (uint32_t i = 0; i < b->B; ++i) {
+    next[i] = ks ? ks[i] : auto_fanout(b->key_bytes, b->desc_host[i].n);
+    if (!gi::batch_fanout_ok(next[i]))
+      return bfail(GI_ERR_INVALID, "gi_batch_set_fanouts: index %u: fan-out %u is not 0, 2, 3, 5, 9 or 17",
+                   i, next[i]);
+  }
+  const std::vector<uint32_t> prev = b->kidx_host;
+  b->kidx_host = next;
+  cudaError_t e = cudaStreamSynchronize(b->stream);  // no build or lookup may still read the tables
+  if (e == cudaSuccess) e = apply_fanouts(b);
+  if (e != cudaSuccess) {
+    b->kidx_host = prev;
+    apply_fanouts(b);
+    return bcuda(e, "gi_batch_set_fanouts");
+  }
+  return GI_OK;
+}
+
+int gi_batch_get_fanouts(const gi_batch* b, uint32_t* ks_out) {
+  gi::set_last_error("");
+  if (!b || !ks_out) return bfail(GI_ERR_INVALID, "gi_batch_get_fanouts: NULL argument");
+  std::copy(b->kidx_host.begin(), b->kidx_host.end(), ks_out);
+  return GI_OK;
+}
+
+int gi_batch_tune_fanouts(gi_batch* b, const void* keys, const uint32_t* rowids, const void* queries,
+                          const uint64_t* query_offsets, uint64_t m, uint32_t reps, int flags,
+                          uint32_t* ks_out, double* class_ms) {
+  gi::set_last_error("");
+  if (!b) return bfail(GI_ERR_INVALID, "gi_batch_tune_fanouts: NULL batch");
+  if (flags & ~(GI_TUNE_APPLY | GI_TUNE_RECORD)) return bfail(GI_ERR_INVALID, "gi_batch_tune_fanouts: unknown flags");
+  if (!is_device_ptr(queries, b->device) || !is_device_ptr(query_offsets, b->device) ||
+      (b->n && (!is_device_ptr(keys, b->device) || !is_device_ptr(rowids, b->device))))
+    return bfail(GI_ERR_INVALID, "gi_batch_tune_fanouts: keys, rowids, queries and offsets must be device memory");
+  if (reps == 0) reps = 5;
+  const uint32_t B = b->B;
+  const int kb = b->key_bytes;
+  const cudaStream_t s = b->stream;
+  static const uint32_t cand[5] = {2, 3, 5, 9, 17};
+  std::vector<uint64_t> qo(B + 1);
+  cudaError_t e = cudaMemcpy(qo.data(), query_offsets, (B + 1) * 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bcuda(e, "gi_batch_tune_fanouts: offsets");
+  if (qo[B] != m) return bfail(GI_ERR_INVALID, "gi_batch_tune_fanouts: query_offsets[B] != m");
+  // size classes floor(log2 n); the probes of each class gathered into one run
+  std::vector<int> cls(B, -1);
+  std::vector<uint64_t> cls_probes(64, 0);
+  for (uint32_t i = 0; i < B; ++i) {
+    const uint64_t n = b->desc_host[i].n;
+    if (n) cls[i] = 63 - __builtin_clzll(n);
+    if (cls[i] >= 0) cls_probes[cls[i]] += qo[i + 1] - qo[i];
+  }
+  std::vector<int> present;
+  std::vector<uint64_t> cls_base(64, 0);
+  uint64_t acc = 0;
+  for (int c = 0; c < 64; ++c)
+    if (cls_probes[c]) {
+      present.push_back(c);
+      cls_base[c] = acc;
+      acc += cls_probes[c];
+    }
+  char* qbuf = nullptr;
+  uint64_t* offs = nullptr;
+  uint32_t* dout = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&] {
+    cudaStreamSynchronize(s);
+    cudaFree(qbuf);
+    cudaFree(offs);
+    cudaFree(dout);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  e = cudaMalloc((void**)&qbuf, std::max<uint64_t>(acc, 1) * kb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&offs, std::max<size_t>(present.size(), 1) * (B + 1) * 8);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dout, std::max<uint64_t>(acc, 1) * 4);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cleanup();
+    return bcuda(e, "gi_batch_tune_fanouts: scratch");
+  }
+  std::vector<uint64_t> oc(B + 1);
+  for (size_t ci = 0; ci < present.size() && e == cudaSuccess; ++ci) {
+    const int c = present[ci];
+    uint64_t run = 0;
+    for (uint32_t i = 0; i < B && e == cudaSuccess; ++i) {
+      oc[i] = run;
+      const uint64_t np = cls[i] == c ? qo[i + 1] - qo[i] : 0;
+      if (np)
+        e = cudaMemcpyAsync(qbuf + (cls_base[c] + run) * kb, (const char*)queries + qo[i] * kb, np * kb,
+                            cudaMemcpyDeviceToDevice, s);
+      run += np;
+    }
+    oc[B] = run;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(offs + ci * (B + 1), oc.data(), (B + 1) * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // oc is reused by the next class
+  }
+  if (e != cudaSuccess) {
+    cleanup();
+    return bcuda(e, "gi_batch_tune_fanouts: gathering the probes");
+  }
+  const std::vector<uint32_t> orig = b->kidx_host;
+  std::vector<double> t(64 * 5, -1.0);
+  int rc = GI_OK;
+  for (int ki = 0; ki < 5 && rc == GI_OK; ++ki) {
+    std::vector<uint32_t> all(B, cand[ki]);
+    rc = gi_batch_set_fanouts(b, all.data());
+    if (rc == GI_OK) rc = gi_batch_build(b, keys, rowids);
+    for (size_t ci = 0; ci < present.size() && rc == GI_OK; ++ci) {
+      const int c = present[ci];
+      const void* qc = qbuf + cls_base[c] * kb;
+      double best = 1e30;
+      for (uint32_t r = 0; r <= reps && rc == GI_OK; ++r) {  // the first run is not timed
+        cudaEventRecord(e0, s);
+        rc = gi_batch_point_lookup(b, qc, offs + ci * (B + 1), cls_probes[c], dout);
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) rc = bcuda(e, "gi_batch_tune_fanouts: timing");
+        float ms = 0.f;
+        if (rc == GI_OK && r > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best = std::min(best, (double)ms);
+      }
+      t[c * 5 + ki] = best;
+    }
+    if (rc == GI_OK) rc = gi_batch_sync(b);
+  }
+  cleanup();
+  std::vector<uint32_t> choice(64, 0);
+  for (int c : present) {
+    int bi = 0;
+    for (int ki = 1; ki < 5; ++ki)
+      if (t[c * 5 + ki] < t[c * 5 + bi]) bi = ki;
+    choice[c] = cand[bi];
+  }
+  std::vector<uint32_t> chosen(B);
+  for (uint32_t i = 0; i < B; ++i)
+    chosen[i] = cls[i] >= 0 && choice[cls[i]] ? choice[cls[i]] : auto_fanout(kb, b->desc_host[i].n);
+  // the batch ends with the chosen fan-outs (APPLY) or those it had, built
+  const int rc2 = gi_batch_set_fanouts(b, (flags & GI_TUNE_APPLY) && rc == GI_OK ? chosen.data() : orig.data());
+  if (rc == GI_OK) rc = rc2;
+  if (rc == GI_OK) rc = gi_batch_build(b, keys, rowids);
+  if (rc == GI_OK) rc = gi_batch_sync(b);
+  if (rc != GI_OK) return rc;
+  if (flags & GI_TUNE_RECORD) {
+    std::lock_guard<std::mutex> lk(g_fanout_mu);
+    for (int c : present) g_fanout_table[kb == 8 ? 1 : 0][c] = choice[c];
+  }
+  if (ks_out) std::copy(chosen.begin(), chosen.end(), ks_out);
+  if (class_ms) std::copy(t.begin(), t.end(), class_ms);
+  return GI_OK;
+}
+
+void gi_batch_fanout_table_clear(void) {
+  std::lock_guard<std::mutex> lk(g_fanout_mu);
+  for (auto& row : g_fanout_table)
+    for (uint32_t& k : row) k = 0;
+}
+
 int gi_batch_set_option(gi_batch* b, int option, int64_t v) {
   gi::set_last_error("");
   if (!b) return bfail(GI_ERR_INVALID, "gi_batch_set_option: NULL batch");
@@ -554,7 +787,8 @@ int gi_batch_set_option(gi_batch* b, int option, int64_t v) {
     case GI_BATCH_OPT_SMEM_BUDGET: {
       if (v < 0 || v > 40 * 1024) return bfail(GI_ERR_INVALID, "shared-memory budget must be in [0, 40 KiB]");
       b->smem_budget = (uint32_t)v;
-      for (uint32_t i = 0; i < b->B; ++i) choose_pinning(b->desc_host[i], b->k, b->key_bytes, b->smem_budget);
+      for (uint32_t i = 0; i < b->B; ++i)
+        choose_pinning(b->desc_host[i], b->kidx_host[i], b->key_bytes, b->smem_budget);
       cudaError_t e = cudaMemcpy(b->d_desc, b->desc_host.data(), b->B * sizeof(gi::BatchDesc),
                                  cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return bcuda(e, "gi_batch_set_option");

@@ -21,14 +21,14 @@ cudaError_t GI_EKS_FN(const void* keys, const uint32_t* rows, const Geom& g, con
   // 32-bit slot arithmetic while s*k + k*(k-1) stays below 2^32 - 1
   const bool narrow = (uint64_t)g.n * k + (uint64_t)k * k < 0xFFFFFFFEull;
   const unsigned grid = grid_size((m + R - 1) / R * (uint64_t)G, c.block, c.blocks_per_sm);
-  const uint32_t hot = (uint32_t)c.hot_levels;
+  const uint32_t hot = (uint32_t)c.hot_levels, l1 = (uint32_t)c.l1_levels;
 #define GI_L(KF, GG, RR, IDX)                                                                  \
   {                                                                                            \
     auto kern = k_eks_point<K, KF, GG, RR, IDX>;                                               \
     cudaError_t e = set_smem(kern, smem);                                                      \
     if (e != cudaSuccess) return e;                                                            \
     kern<<<grid, c.block, smem, s>>>((const K*)keys, rows, (IDX)g.n, g.levels, (const K*)q, m, \
-                                     out, smem_levels, (uint32_t)slots, hot, dflags);          \
+                                     out, smem_levels, (uint32_t)slots, hot, l1, dflags);      \
   }
 #define GI_X(KF, GG)                                                                           \
   if (k == KF && G == GG) {                                                                    \

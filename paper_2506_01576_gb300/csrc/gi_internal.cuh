@@ -138,6 +138,22 @@ __host__ __device__ __forceinline__ uint32_t slot_of_rank(uint32_t r, const Slot
   return sm.first[l] + xd * km1 + (x - xd * k) - 1;
 }
 
+// The same map for a fan-out chosen per index (batches whose indexes each have
+// their own k): sm.k == 0 marks the sorted layout (slot = rank); the compiled
+// fan-outs take their constant-divisor forms.  sm.k is uniform over a bucket, so
+// the switch does not diverge.
+__host__ __device__ __forceinline__ uint32_t slot_of_rank_any(uint32_t r, const SlotMap& sm) {
+  switch (sm.k) {
+    case 0: return r;
+    case 2: return slot_of_rank<2>(r, sm);
+    case 3: return slot_of_rank<3>(r, sm);
+    case 5: return slot_of_rank<5>(r, sm);
+    case 9: return slot_of_rank<9>(r, sm);
+    case 17: return slot_of_rank<17>(r, sm);
+    default: return slot_of_rank<0>(r, sm);
+  }
+}
+
 // The 32-bit map of a geometry with n < 2^32 (host or device; on the device
 // fill_slot_map can write straight into shared memory).
 __host__ __device__ inline void fill_slot_map(SlotMap& sm, const Geom& g) {
@@ -275,8 +291,13 @@ struct BatchHybrid {
   uint32_t* buckets;            // [3][nseg * 257] bucket ids per bucket-sort size class
   uint32_t* bucket_count;       // [3]
   unsigned long long* xor_or;   // [nseg] OR over the index of key ^ (its first key)
-  uint32_t k;                   // fan-out; 0 = sorted layout
+  uint32_t k;                   // fan-out; 0 = sorted layout; kBatchMixed: kidx
+  const uint32_t* kidx;         // [nseg] fan-out of every index (0 = sorted), if mixed
 };
+// BatchHybrid::k of a batch whose indexes each have their own fan-out
+constexpr uint32_t kBatchMixed = 0xFFFFFFFFu;
+// the fan-outs a batch lays its indexes out with: 0 (sorted), 2, 3, 5, 9, 17
+inline bool batch_fanout_ok(uint32_t k) { return k == 0 || k == 2 || k == 3 || k == 5 || k == 9 || k == 17; }
 size_t batch_hybrid_bytes(uint32_t nseg, uint64_t ntiles);  // device bytes of the tables
 // hist/offsets/status/counters live in `scratch` (batch_sort_scratch_bytes); no host
 // sync.  hy != NULL: indexes are sorted per their plan (whole / MSD + buckets, written
@@ -296,11 +317,12 @@ cudaError_t batch_local_sort(const void* keys, const uint32_t* vals, const void*
 // Raises the bucket-sort kernels' shared-memory limit (once, before any capture).
 cudaError_t batch_local_sort_setup(int key_bytes, uint32_t k);
 // hy != NULL: only the tiles of the kPlanLsd indexes (of nseg)
+// permute every index into k-ary order (k = 0: sorted; kBatchMixed: hy->kidx) at
+// out + seg_base[s]
 cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t* ov,
                          const BatchTile* tiles, uint64_t ntiles, const uint64_t* seg_start,
                          const uint64_t* seg_base, uint32_t k, int key_bytes, uint32_t* dflags,
                          cudaStream_t s, const BatchHybrid* hy, uint32_t nseg);
-// permute every index into k-ary order (k = 0: sorted) at out + seg_base[s]
 
 
 // Hybrid sort: stable MSD scatter(s) on the top one or two non-trivial digits,
@@ -342,6 +364,7 @@ struct LookupCfg {
   int prefetch;       // EBS prefetch distance
   int early_exit;     // stop on an equal pivot (unique keys only)
   int hot_levels;     // k-ary: top levels kept in L2 (evict_last); the rest streamed
+  int l1_levels;      // k-ary: top levels read through L1; deeper ones not allocated there
   int range_fill;     // 0: rows by rank -> slot; 1: rows by per-level runs
   int reorder;        // point lookups: sort each CTA's probe tile first (Section 7.4)
 };

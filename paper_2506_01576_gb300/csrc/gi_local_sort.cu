@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(T, MINB) k_batch_local_sort(
     const uint64_t start = msd ? offs_w[id] : s0;
     const uint32_t count = (uint32_t)(msd ? hist_w[id] : seg_start[i + 1] - s0);
     if (count <= lo_count || count > hi_count) continue;  // another launch's size class
-    if constexpr (KF != 1) {
+    if constexpr (KF != 1) {  // (KF == -1: the map's k is the index's own fan-out)
       if (tid < (int)(sizeof(SlotMap) / 4)) ((uint32_t*)&s_map)[tid] = ((const uint32_t*)&maps[i])[tid];
     }
     const uint32_t limit = 8u * (uint32_t)__popc(pl.lsd_mask) + 8u;
@@ -352,7 +352,8 @@ __global__ void __launch_bounds__(T, MINB) k_batch_local_sort(
       if (j > 0) dup |= ord.key(m.s_k[ord.direct ? j - 1 : m.s_src[j - 1]]) == key;
       const uint32_t r = r0 + j;
       uint32_t t = r;
-      if constexpr (KF != 1) t = slot_of_rank<KF>(r, s_map);
+      if constexpr (KF == -1) t = slot_of_rank_any(r, s_map);
+      else if constexpr (KF != 1) t = slot_of_rank<KF>(r, s_map);
       out_k[base + t] = key;
       out_v[base + t] = m.s_v[p];
     }
@@ -485,12 +486,14 @@ cudaError_t launch_batch_kf(const void* keys, const uint32_t* vals, const void* 
                             const BatchHybrid& hy, uint32_t* dflags, cudaStream_t s, bool setup) {
 #define GI_B(KF) launch_batch<K, KF>(keys, vals, src_k, src_v, seg_start, nseg, hy, dflags, s, setup)
   switch (hy.k) {
+    case kBatchMixed: return GI_B(-1);  // each index's own fan-out
     case 0: return GI_B(1);
+    case 2: return GI_B(2);
     case 3: return GI_B(3);
     case 5: return GI_B(5);
     case 9: return GI_B(9);
     case 17: return GI_B(17);
-    default: return cudaErrorInvalidValue;  // the batch takes k = 3, 5, 9, 17 only
+    default: return cudaErrorInvalidValue;  // the batch takes k = 2, 3, 5, 9, 17 only
   }
 #undef GI_B
 }

@@ -302,6 +302,49 @@ __device__ __forceinline__ void vec_load_hint(const K* p, K* v, uint64_t pol) {
   }
 }
 
+// The same loads without allocating in L1 (deep tree levels: read once per lookup,
+// they would only push the top levels out of L1).
+template <class K, int P>
+__device__ __forceinline__ void vec_load_hint_na(const K* p, K* v, uint64_t pol) {
+  constexpr int BYTES = P * (int)sizeof(K);
+  if constexpr (BYTES % 32 == 0) {
+#pragma unroll
+    for (int i = 0; i < BYTES / 32; ++i) {
+      if constexpr (sizeof(K) == 8) {
+        unsigned long long a, b, c, d;
+        asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u64 {%0,%1,%2,%3}, [%4], %5;"
+                     : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p + 4 * i), "l"(pol));
+        v[4 * i] = a; v[4 * i + 1] = b; v[4 * i + 2] = c; v[4 * i + 3] = d;
+      } else {
+        uint32_t a[8];
+        asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+                     : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]),
+                       "=r"(a[6]), "=r"(a[7])
+                     : "l"(p + 8 * i), "l"(pol));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[8 * i + j] = a[j];
+      }
+    }
+  } else if constexpr (BYTES == 16 && sizeof(K) == 8) {
+    unsigned long long a, b;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0,%1}, [%2], %3;"
+                 : "=l"(a), "=l"(b) : "l"(p), "l"(pol));
+    v[0] = a; v[1] = b;
+  } else if constexpr (BYTES == 16) {
+    uint32_t a, b, c, d;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(a), "=r"(b), "=r"(c), "=r"(d) : "l"(p), "l"(pol));
+    v[0] = a; v[1] = b; v[2] = c; v[3] = d;
+  } else {
+    vec_load_hint<K, P>(p, v, pol);
+  }
+}
+
+template <class K>
+__device__ __forceinline__ K ld_hint_na(const K* p, uint64_t pol) {
+  return ld_stream<K>(p, pol);
+}
+
 template <class K, int KF, int G>
 struct EksShape {
   static constexpr int N = KF - 1;           // pivots per node
@@ -318,15 +361,21 @@ struct EksShape {
 // level and the shared-memory / global choice is warp-uniform.  Slots past n
 // hold the maximum key (written at build), so a node needs no per-pivot bounds
 // check: c = #{pivots < x}; the lower-bound candidate is slot s+c if it exists;
-// the next node starts at s*k + (c+1)*(k-1).  Equality is resolved once at the
-// end with one load of the candidate key.
+// the next node starts at s*k + (c+1)*(k-1).  With one lane per lookup the
+// candidate's key is kept in a register (pivot c of the node just read), so
+// equality is resolved at the end with no further load of the key array; lane
+// groups load it once at the end.
+// Levels below l1_levels are read through L1 (the top of the tree stays there);
+// deeper levels are not allocated in L1, and neither are rowIDs, probes and
+// results, each read once.
 template <class K, int KF, int G, int R, class IDX>
 __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
                                                    const uint32_t* __restrict__ rows, IDX n,
                                                    uint32_t levels, const K* __restrict__ q,
                                                    uint64_t m, uint32_t* __restrict__ out,
                                                    uint32_t smem_levels, uint32_t smem_slots,
-                                                   uint32_t hot_levels, uint32_t* flags) {
+                                                   uint32_t hot_levels, uint32_t l1_levels,
+                                                   uint32_t* flags) {
   using S = EksShape<K, KF, G>;
   constexpr int N = S::N, P = S::P;
   constexpr IDX kNoCand = ~IDX(0);
@@ -348,7 +397,7 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
   const uint64_t pol_keep = l2_policy(true), pol_stream = l2_policy(false);
 
   for (uint64_t first = gid; first < m; first += groups * R) {
-    K x[R];
+    K x[R], ckey[R];
     IDX s[R], cand[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -356,6 +405,7 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
       x[r] = i < m ? ld_stream<K>(q + i, pol_stream) : K(0);
       s[r] = i < m ? IDX(0) : n;  // s >= n: nothing (more) to do
       cand[r] = kNoCand;
+      ckey[r] = K(0);
     }
     for (uint32_t lv = 0; lv < levels; ++lv) {
       K piv[R][P];
@@ -388,12 +438,15 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
               }
             }
           } else if constexpr (S::VEC) {
-            vec_load_hint<K, P>(keys + at, piv[r], pol);
+            if (lv < l1_levels) vec_load_hint<K, P>(keys + at, piv[r], pol);
+            else vec_load_hint_na<K, P>(keys + at, piv[r], pol);
           } else {
 #pragma unroll
             for (int p = 0; p < P; ++p) {
               const int j = gl + p * G;
-              piv[r][p] = j < N ? ld_hint<K>(keys + at + p * G, pol) : K(0);
+              piv[r][p] = j < N ? (lv < l1_levels ? ld_hint<K>(keys + at + p * G, pol)
+                                                  : ld_hint_na<K>(keys + at + p * G, pol))
+                                : K(0);
             }
           }
         }
@@ -410,7 +463,15 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
           }
 #pragma unroll
           for (int o = 1; o < G; o <<= 1) c += __shfl_xor_sync(gmask, c, o);
-          if (c < (uint32_t)N && s[r] + c < n) cand[r] = s[r] + c;
+          if (c < (uint32_t)N && s[r] + c < n) {
+            cand[r] = s[r] + c;
+            if constexpr (G == 1) {  // pivot c of the node: the candidate's key
+              K mine = piv[r][0];
+#pragma unroll
+              for (int p = 1; p < P; ++p) mine = c == (uint32_t)p ? piv[r][p] : mine;
+              ckey[r] = mine;
+            }
+          }
           s[r] = s[r] * KF + (IDX)((c + 1) * N);
         }
       }
@@ -420,8 +481,10 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
       const uint64_t i = first + r * groups;
       if (i < m && gl == r % G) {
         uint32_t res = GI_MISS;
-        if (cand[r] != kNoCand && ld_hint<K>(keys + cand[r], pol_stream) == x[r])
-          res = ld_hint<uint32_t>(rows + cand[r], pol_stream);
+        // G > 1: the candidate's key is read once here (fetching it from its owner
+        // lane at every level measured 1.4-1.5x slower for 4- and 8-lane groups)
+        if (cand[r] != kNoCand && (G == 1 ? ckey[r] : ld_hint<K>(keys + cand[r], pol_stream)) == x[r])
+          res = ld_stream<uint32_t>(rows + cand[r], pol_stream);
         st_stream(out + i, res, pol_stream);
       }
     }

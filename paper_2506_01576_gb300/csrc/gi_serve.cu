@@ -618,8 +618,10 @@ void server_loop(gi_server* s) {
         slot = &b;
         break;
       }
+    // batches in flight: poll their events without sleeping (a sleep costs the
+    // scheduler's timer slack, 50-100 us, on every request's latency)
     if (!slot) {
-      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      std::this_thread::yield();
       continue;
     }
     uint64_t probes = 0;
@@ -643,7 +645,7 @@ void server_loop(gi_server* s) {
       s->n_probes += probes;
       launch_batch(s, *slot);
     } else {
-      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      std::this_thread::yield();
     }
   }
 }
@@ -776,6 +778,109 @@ int gi_server_stats(const gi_server* s, uint64_t* batches, uint64_t* requests, u
   if (batches) *batches = s->n_batches.load();
   if (requests) *requests = s->n_requests.load();
   if (probes) *probes = s->n_probes.load();
+  return GI_OK;
+}
+
+// ---------------------------------------------------------------- native load generator
+namespace {
+
+// sleep most of the way (the scheduler's timer slack is ~50-100 us), then yield
+// until the time has come
+void sleep_until_ns(int64_t t) {
+  for (;;) {
+    const int64_t d = t - now_ns();
+    if (d <= 0) return;
+    if (d > 300000) std::this_thread::sleep_for(std::chrono::nanoseconds(d - 200000));
+    else std::this_thread::yield();
+  }
+}
+
+int check_trace(const gi_request* reqs, const int64_t* arrival_ns, uint64_t count,
+                const int64_t* latency_ns, const char* who) {
+  if (count && (!reqs || !arrival_ns || !latency_ns))
+    return sfail(GI_ERR_INVALID, "%s: NULL requests, arrivals or latencies", who);
+  for (uint64_t i = 0; i < count; ++i)
+    if (arrival_ns[i] < 0) return sfail(GI_ERR_INVALID, "%s: negative arrival time", who);
+  return GI_OK;
+}
+
+}  // namespace
+
+int gi_server_replay(gi_server* s, const gi_request* reqs, const int64_t* arrival_ns, uint64_t count,
+                     uint32_t threads, int64_t* latency_ns, int* status, double* wall_s) {
+  gi::set_last_error("");
+  if (!s) return sfail(GI_ERR_INVALID, "gi_server_replay: NULL server");
+  if (threads == 0 || threads > 64) return sfail(GI_ERR_INVALID, "gi_server_replay: 1..64 threads");
+  int rc = check_trace(reqs, arrival_ns, count, latency_ns, "gi_server_replay");
+  if (rc != GI_OK) return rc;
+  std::vector<uint64_t> tickets(count, 0);
+  std::unique_ptr<std::atomic<int>[]> state(new std::atomic<int>[count ? count : 1]);
+  for (uint64_t i = 0; i < count; ++i) state[i].store(0, std::memory_order_relaxed);
+  std::vector<int> sub_rc(count, GI_OK);
+  const int64_t t0 = now_ns() + 2000000;  // every submitter is up before the first arrival
+  std::vector<std::thread> pool;
+  for (uint32_t t = 0; t < threads; ++t) {
+    pool.emplace_back([&, t] {
+      for (uint64_t i = t; i < count; i += threads) {
+        sleep_until_ns(t0 + arrival_ns[i]);
+        sub_rc[i] = gi_server_submit(s, &reqs[i], &tickets[i]);
+        state[i].store(sub_rc[i] == GI_OK ? 1 : 2, std::memory_order_release);
+      }
+    });
+  }
+  // this thread collects the completions; latencies come from the server's own
+  // completion times, so the order of collection does not matter
+  int first_bad = GI_OK;
+  for (uint64_t i = 0; i < count; ++i) {
+    int st;
+    while ((st = state[i].load(std::memory_order_acquire)) == 0) std::this_thread::yield();
+    int r = sub_rc[i];
+    int64_t sub = 0, done = 0;
+    if (st == 1) r = gi_server_wait(s, tickets[i], &sub, &done);
+    latency_ns[i] = st == 1 ? done - (t0 + arrival_ns[i]) : -1;
+    if (status) status[i] = r;
+    if (r != GI_OK && r != GI_ERR_CAPACITY && first_bad == GI_OK) first_bad = r;
+  }
+  for (auto& th : pool) th.join();
+  if (wall_s) *wall_s = (double)(now_ns() - t0) * 1e-9;
+  if (first_bad != GI_OK) return sfail(first_bad, "gi_server_replay: a request failed");
+  return GI_OK;
+}
+
+int gi_replay_serial(gi_index* const* indexes, uint32_t nindexes, const gi_request* reqs,
+                     const int64_t* arrival_ns, uint64_t count, int64_t* latency_ns, int* status,
+                     double* wall_s) {
+  gi::set_last_error("");
+  if (!indexes || nindexes == 0) return sfail(GI_ERR_INVALID, "gi_replay_serial: no indexes");
+  int rc = check_trace(reqs, arrival_ns, count, latency_ns, "gi_replay_serial");
+  if (rc != GI_OK) return rc;
+  for (uint64_t i = 0; i < count; ++i)
+    if (reqs[i].index >= nindexes || !indexes[reqs[i].index] || reqs[i].m == 0)
+      return sfail(GI_ERR_INVALID, "gi_replay_serial: request %llu names no index or is empty",
+                   (unsigned long long)i);
+  const int64_t t0 = now_ns() + 1000000;
+  int first_bad = GI_OK;
+  for (uint64_t i = 0; i < count; ++i) {
+    const gi_request& q = reqs[i];
+    sleep_until_ns(t0 + arrival_ns[i]);
+    gi_index* ix = indexes[q.index];
+    int r;
+    if (q.kind == GI_REQ_POINT) {
+      r = gi_point_lookup(ix, q.keys, q.m, q.out_rowids);
+    } else {  // the two-call protocol: offsets, then the rows if they fit
+      r = gi_range_lookup(ix, q.keys, q.hi, q.m, q.out_offsets, nullptr);
+      if (r == GI_OK) {
+        const uint64_t total = q.out_offsets[q.m];
+        if (total > q.rows_capacity) r = GI_ERR_CAPACITY;
+        else if (total) r = gi_range_lookup(ix, q.keys, q.hi, q.m, q.out_offsets, q.out_rowids);
+      }
+    }
+    latency_ns[i] = now_ns() - (t0 + arrival_ns[i]);
+    if (status) status[i] = r;
+    if (r != GI_OK && r != GI_ERR_CAPACITY && first_bad == GI_OK) first_bad = r;
+  }
+  if (wall_s) *wall_s = (double)(now_ns() - t0) * 1e-9;
+  if (first_bad != GI_OK) return sfail(first_bad, "gi_replay_serial: a request failed");
   return GI_OK;
 }
 

@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(256) k_batch_gather(const K* __restrict__ sk,
                                                       const uint64_t* __restrict__ seg_base,
                                                       uint32_t k, uint32_t* __restrict__ flags,
                                                       const BatchPlan* __restrict__ plan,
-                                                      TileMap map) {
+                                                      TileMap map, const uint32_t* __restrict__ kidx) {
   bool dup = false;
   const uint64_t total = map.list ? *map.count : ntiles;
   for (uint64_t ti = blockIdx.x; ti < total; ti += gridDim.x) {
@@ -668,12 +668,15 @@ __global__ void __launch_bounds__(256) k_batch_gather(const K* __restrict__ sk,
     const uint64_t s0 = seg_start[t.seg];
     const uint64_t n = seg_start[t.seg + 1] - s0;
     const uint64_t out0 = seg_base[t.seg];
-    // KF == 1 marks the sorted order; fan-outs below 2 never reach device_geom
-    const Geom g = device_geom(n, KF > 1 ? (uint32_t)KF : (k >= 2 ? k : 2u));
+    // KF == 1 marks the sorted order; KF == -1 each index's own fan-out (0: sorted);
+    // fan-outs below 2 never reach device_geom
+    const uint32_t kk = KF == -1 ? kidx[t.seg] : k;
+    const Geom g = device_geom(n, KF > 1 ? (uint32_t)KF : (kk >= 2 ? kk : 2u));
     for (uint32_t i = threadIdx.x; i < t.count; i += blockDim.x) {
       const uint64_t slot = t.start - s0 + i;
       uint64_t r;
       if constexpr (KF == 1) r = slot;
+      else if constexpr (KF == -1) r = kk >= 2 ? slot_to_rank<0>(slot, g) : slot;
       else r = slot_to_rank<KF>(slot, g);
       const K key = sk[s0 + r];
       ok[out0 + slot] = key;
@@ -727,6 +730,7 @@ __global__ void __launch_bounds__(256) k_batch_xor(const K* __restrict__ keys,
 __global__ void __launch_bounds__(256) k_batch_plan(const unsigned long long* __restrict__ xor_or,
                                                     const uint64_t* __restrict__ seg_start,
                                                     uint32_t nseg, int key_bytes, uint32_t k,
+                                                    const uint32_t* __restrict__ kidx,
                                                     uint32_t cap, BatchPlan* __restrict__ plan,
                                                     SlotMap* __restrict__ maps) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -753,7 +757,10 @@ __global__ void __launch_bounds__(256) k_batch_plan(const unsigned long long* __
     pl.ts = pl.s1 >= 8 ? pl.s1 - 8 : 0u;
   }
   plan[i] = pl;
-  if (k >= 2 && n > 0 && n < (1ull << 32)) fill_slot_map(maps[i], device_geom(n, k));
+  // k == kBatchMixed: each index's own fan-out (its map's k = 0 marks the sorted layout)
+  const uint32_t ki = k == kBatchMixed ? kidx[i] : k;
+  if (ki >= 2 && n > 0 && n < (1ull << 32)) fill_slot_map(maps[i], device_geom(n, ki));
+  else if (k == kBatchMixed) maps[i].k = 0;
 }
 
 // Counts of the MSD window per index (indexes of plan kPlanMsd only).
@@ -1115,7 +1122,7 @@ cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], u
       k_batch_xor<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)keys, chunks, nchunks, seg_start, hy->xor_or);
     else
       k_batch_xor<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)keys, chunks, nchunks, seg_start, hy->xor_or);
-    k_batch_plan<<<(nseg + 255) / 256, 256, 0, s>>>(hy->xor_or, seg_start, nseg, key_bytes, hy->k, cap,
+    k_batch_plan<<<(nseg + 255) / 256, 256, 0, s>>>(hy->xor_or, seg_start, nseg, key_bytes, hy->k, hy->kidx, cap,
                                                    hy->plan, hy->slot_maps);
     if (key_bytes == 4)
       k_batch_window_hist<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)keys, chunks, nchunks, hy->plan, hy->hist_w);
@@ -1180,12 +1187,14 @@ template <class K>
 static void launch_batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t* ov,
                                 const BatchTile* tiles, uint64_t ntiles, const uint64_t* seg_start,
                                 const uint64_t* seg_base, uint32_t k, uint32_t* dflags,
-                                cudaStream_t s, const BatchPlan* plan, TileMap map) {
+                                cudaStream_t s, const BatchPlan* plan, TileMap map,
+                                const uint32_t* kidx) {
   const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)sm_count() * 16);
   const K* a = (const K*)sk;
   K* b = (K*)ok;
-#define GI_BG(KF) k_batch_gather<K, KF><<<grid, 256, 0, s>>>(a, sv, b, ov, tiles, ntiles, seg_start, seg_base, k, dflags, plan, map)
+#define GI_BG(KF) k_batch_gather<K, KF><<<grid, 256, 0, s>>>(a, sv, b, ov, tiles, ntiles, seg_start, seg_base, k, dflags, plan, map, kidx)
   switch (k) {
+    case kBatchMixed: GI_BG(-1); break;  // each index's own fan-out
     case 0: GI_BG(1); break;  // sorted order: rank == slot
     case 2: GI_BG(2); break;
     case 3: GI_BG(3); break;
@@ -1205,10 +1214,12 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
   if (ntiles == 0) return cudaSuccess;
   const BatchPlan* plan = hy ? hy->plan : nullptr;
   const TileMap map = hy ? TileMap{hy->list_lsd, hy->prefix_lsd + nseg} : TileMap{};
+  const uint32_t* kidx = hy ? hy->kidx : nullptr;
+  if (k == kBatchMixed && !kidx) return cudaErrorInvalidValue;
   if (key_bytes == 4)
-    launch_batch_gather<uint32_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s, plan, map);
+    launch_batch_gather<uint32_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s, plan, map, kidx);
   else
-    launch_batch_gather<uint64_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s, plan, map);
+    launch_batch_gather<uint64_t>(sk, sv, ok, ov, tiles, ntiles, seg_start, seg_base, k, dflags, s, plan, map, kidx);
   return cudaGetLastError();
 }
 

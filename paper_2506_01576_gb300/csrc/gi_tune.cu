@@ -192,9 +192,10 @@ int gi_tune(gi_index* idx, const void* queries, uint64_t m, uint32_t reps, int f
   if (m == 0 || !queries) return tfail(GI_ERR_INVALID, "gi_tune: need m >= 1 probes");
   if (flags & ~(GI_TUNE_APPLY | GI_TUNE_RECORD)) return tfail(GI_ERR_INVALID, "gi_tune: unknown flags");
   cudaPointerAttributes pa{};
-  if (cudaPointerGetAttributes(&pa, queries) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+  if (cudaPointerGetAttributes(&pa, queries) != cudaSuccess || pa.type != cudaMemoryTypeDevice ||
+      pa.device != gi::index_device(idx)) {
     cudaGetLastError();
-    return tfail(GI_ERR_INVALID, "gi_tune: probes must be device memory");
+    return tfail(GI_ERR_INVALID, "gi_tune: probes must be device memory of the index's device");
   }
   if (reps == 0) reps = 5;
   gi_info info{};

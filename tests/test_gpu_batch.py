@@ -185,7 +185,8 @@ def test_batched_workload_shape_sampled():
 
 
 @pytest.mark.parametrize("bits", [64, 32])
-@pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER_KARY, 5), (gi.GI_SORTED, 0), (gi.GI_EYTZINGER_KARY, 17)])
+@pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER_KARY, 5), (gi.GI_SORTED, 0), (gi.GI_EYTZINGER_KARY, 17),
+                                      (gi.GI_EYTZINGER_KARY, 2)])
 def test_batch_build_plans_every_path(bits, layout, k):
     # the build sorts each index by a plan chosen on the device from the bits in
     # which its keys differ: whole index in one CTA (<= 5120 pairs), one MSD scatter
@@ -266,4 +267,139 @@ def test_batch_reserved_rowid_reported_by_sync(bits):
     gi.gi_batch_point_lookup(batch, to_dev(np.concatenate(qs)), to_dev(qoff), out)
     gi.gi_batch_sync(batch)
     _check(batch, keys, rows, qs, qoff, out, gi.GI_EYTZINGER_KARY, 5)
+    gi.gi_batch_destroy(batch)
+
+
+def _check_mixed(batch, keys, rows, qs, qoff, out, ks, check_layout=True):
+    """Per index: lookups vs the oracle, and the layout of its own fan-out
+    (0: sorted; 2: the binary tree in 0-based in-order fill; k: k-ary)."""
+    got = to_host(out, np.uint32)
+    for i in range(len(keys)):
+        sk, sr = oracle.sort_pairs(keys[i], rows[i])
+        assert np.array_equal(got[int(qoff[i]):int(qoff[i + 1])], oracle.point_lookup(sk, sr, qs[i])), \
+            ("index", i, len(keys[i]), ks[i])
+        if check_layout and len(keys[i]):
+            n = len(keys[i])
+            kk = torch.empty(n, dtype=torch.int64 if keys[i].dtype == np.uint64 else torch.int32, device=DEV)
+            rr = torch.empty(n, dtype=torch.int32, device=DEV)
+            gi.gi_batch_copy_index(batch, i, kk, rr)
+            lay = oracle.SORTED if ks[i] == 0 else oracle.EYTZINGER_KARY
+            ok, orr = oracle.layout_arrays(keys[i], rows[i], lay, max(int(ks[i]), 2))
+            assert np.array_equal(to_host(kk, keys[i].dtype), ok), ("layout", i, ks[i])
+            assert np.array_equal(to_host(rr, np.uint32), orr), ("layout rows", i, ks[i])
+
+
+@pytest.mark.parametrize("bits", [64, 32])
+def test_batch_fanout_per_index_equals_oracle(bits):
+    """Each index of one batch has its own fan-out (sorted, 2, 3, 5, 9, 17), over
+    every build plan (whole index in one CTA, MSD + buckets, LSD fallback), in one
+    build and one lookup launch; then the same batch with other fan-outs."""
+    dt = np.uint64 if bits == 64 else np.uint32
+    rng = np.random.default_rng(bits)
+    keys = [W.unique_keys(4000, bits, 1), W.unique_keys(60000, bits, 2),
+            np.concatenate([np.arange(9000, dtype=dt), np.array([np.iinfo(dt).max], dt)]),  # LSD
+            W.duplicate_keys(1500, 8, bits, 3)[:12000].astype(dt), np.zeros(0, dt), np.array([7], dt),
+            W.unique_keys(5120, bits, 4), W.unique_keys(100000, bits, 5)]
+    keys += [W.unique_keys(int(n), bits, 10 + i) for i, n in enumerate(rng.integers(1, 30000, size=16))]
+    rows = [rng.permutation(len(x)).astype(np.uint32) for x in keys]
+    off = np.zeros(len(keys) + 1, dtype=np.uint64)
+    np.cumsum(np.array([len(x) for x in keys], dtype=np.uint64), out=off[1:])
+    qs, qoff = _probes(keys, bits, list(rng.integers(100, 3000, size=len(keys))), 31)
+    flag = gi.GI_KEY_U64 if bits == 64 else gi.GI_KEY_U32
+    batch = gi.gi_batch_create(off, gi.GI_EYTZINGER_KARY | flag, 5)
+    kd, rd = to_dev(np.concatenate(keys)), to_dev(np.concatenate(rows))
+    qd, qod = to_dev(np.concatenate(qs)), to_dev(qoff)
+    out = torch.full((int(qoff[-1]),), -5, dtype=torch.int32, device=DEV)
+    cycle = np.array([0, 2, 3, 5, 9, 17], dtype=np.uint32)
+    for shift in (0, 3):
+        ks = cycle[(np.arange(len(keys)) + shift) % len(cycle)]
+        gi.gi_batch_set_fanouts(batch, ks)
+        assert np.array_equal(gi.gi_batch_get_fanouts(batch, len(keys)), ks)
+        gi.gi_batch_build(batch, kd, rd)
+        out.fill_(-5)
+        gi.gi_batch_point_lookup(batch, qd, qod, out)
+        gi.gi_batch_sync(batch)
+        _check_mixed(batch, keys, rows, qs, qoff, out, ks)
+        for opt, v in ((gi.GI_BATCH_OPT_SMEM_BUDGET, 40960), (gi.GI_BATCH_OPT_CHUNK, 96)):
+            gi.gi_batch_set_option(batch, opt, v)
+            out.fill_(-5)
+            gi.gi_batch_point_lookup(batch, qd, qod, out)
+            gi.gi_batch_sync(batch)
+            _check_mixed(batch, keys, rows, qs, qoff, out, ks, check_layout=False)
+        gi.gi_batch_set_option(batch, gi.GI_BATCH_OPT_SMEM_BUDGET, 0)
+        gi.gi_batch_set_option(batch, gi.GI_BATCH_OPT_CHUNK, 2048)
+    with pytest.raises(gi.GIError) as e:
+        gi.gi_batch_set_fanouts(batch, np.full(len(keys), 4, np.uint32))
+    assert e.value.code == gi.GI_ERR_INVALID
+    gi.gi_batch_destroy(batch)
+
+
+def test_batch_fanout_automatic_and_graph_replay():
+    """NULL fan-outs choose by size class (k = 3 up to 2^14 u64 keys, Eytzinger
+    order up to 2^19, k = 5 above, when nothing is recorded); the mixed batch's
+    build + lookup replayed from a CUDA graph gives the oracle's answers."""
+    gi.gi_batch_fanout_table_clear()
+    rng = np.random.default_rng(12)
+    sizes = [int(x) for x in np.exp2(rng.uniform(8, 20, size=40)).astype(np.int64)]
+    keys, rows, off = _make_batch(sizes, 64, 81)
+    qs, qoff = _probes(keys, 64, list(rng.integers(0, 4000, size=len(sizes))), 10)
+    batch = gi.gi_batch_create(off, gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 5)
+    gi.gi_batch_set_fanouts(batch, None)
+    ks = gi.gi_batch_get_fanouts(batch, len(sizes))
+    want = [3 if n <= (1 << 14) else 2 if n <= (1 << 19) else 5 for n in sizes]
+    assert list(ks) == want
+    kd, rd = to_dev(np.concatenate(keys)), to_dev(np.concatenate(rows))
+    qd, qod = to_dev(np.concatenate(qs)), to_dev(qoff)
+    out = torch.full((int(qoff[-1]),), -5, dtype=torch.int32, device=DEV)
+    s = torch.cuda.Stream()
+    gi.gi_batch_set_stream(batch, s)
+    with torch.cuda.stream(s):
+        gi.gi_batch_build(batch, kd, rd)
+        gi.gi_batch_point_lookup(batch, qd, qod, out)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        gi.gi_batch_build(batch, kd, rd)
+        gi.gi_batch_point_lookup(batch, qd, qod, out)
+    for _ in range(2):
+        out.fill_(-5)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        gi.gi_batch_sync(batch)
+        _check_mixed(batch, keys, rows, qs, qoff, out, ks)
+    gi.gi_batch_destroy(batch)
+
+
+def test_batch_fanout_tuner():
+    """gi_batch_tune_fanouts times every candidate fan-out per size class and keeps
+    the fastest per class; with GI_TUNE_APPLY the batch ends built with them (its
+    answers still the oracle's), with GI_TUNE_RECORD a later batch's automatic
+    choice follows the record."""
+    gi.gi_batch_fanout_table_clear()
+    rng = np.random.default_rng(5)
+    sizes = [int(x) for x in np.exp2(rng.uniform(8, 18, size=60)).astype(np.int64)]
+    keys, rows, off = _make_batch(sizes, 64, 91)
+    qs, qoff = _probes(keys, 64, list(rng.integers(500, 3000, size=len(sizes))), 12)
+    batch = gi.gi_batch_create(off, gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 5)
+    kd, rd = to_dev(np.concatenate(keys)), to_dev(np.concatenate(rows))
+    qd, qod = to_dev(np.concatenate(qs)), to_dev(qoff)
+    ks, cms = gi.gi_batch_tune_fanouts(batch, len(sizes), kd, rd, qd, qod, reps=2,
+                                       flags=gi.GI_TUNE_APPLY | gi.GI_TUNE_RECORD)
+    cls = [int(np.floor(np.log2(n))) for n in sizes]
+    cand = [2, 3, 5, 9, 17]
+    for i, c in enumerate(cls):
+        assert cms[c].min() > 0
+        assert ks[i] == cand[int(np.argmin(cms[c]))]  # the fastest candidate of its class
+    assert np.array_equal(gi.gi_batch_get_fanouts(batch, len(sizes)), ks)
+    out = torch.full((int(qoff[-1]),), -5, dtype=torch.int32, device=DEV)
+    gi.gi_batch_point_lookup(batch, qd, qod, out)
+    gi.gi_batch_sync(batch)
+    _check_mixed(batch, keys, rows, qs, qoff, out, ks, check_layout=False)
+    # a new batch of the same sizes takes the recorded choices automatically
+    b2 = gi.gi_batch_create(off, gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 5)
+    gi.gi_batch_set_fanouts(b2, None)
+    assert np.array_equal(gi.gi_batch_get_fanouts(b2, len(sizes)), ks)
+    gi.gi_batch_destroy(b2)
+    gi.gi_batch_fanout_table_clear()
     gi.gi_batch_destroy(batch)

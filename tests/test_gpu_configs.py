@@ -8,8 +8,9 @@
     configuration the benchmark times.
   * 2^28 uint64 keys: with unique keys and rowID j for key j, a hit on keys[j]
     must return j and every miss GI_MISS -- a property that holds at any size.
-  * 2^26 uint32 keys, 2^24 ranges with 1, 16 and 256 expected rows: all offsets
-    against the oracle; all rows for 1 and 16; rows of a 2^14-range sample for 256.
+  * 2^26 uint32 keys, 2^24 ranges with 1, 16 and 256 expected rows: every offset
+    and every row against the oracle (for 256 rows, about 2^32 rows per layout,
+    compared in chunks of 2^20 ranges).
 """
 import numpy as np
 import pytest
@@ -133,24 +134,18 @@ def ranges_u32():
     return n, m, seed, keys, rows, sk, sr
 
 
-@pytest.mark.parametrize("E", [1, 16, 256])
+RANGE_LAYOUTS = ((gi.GI_SORTED, 0), (gi.GI_EYTZINGER, 2), (gi.GI_EYTZINGER_KARY, 16),
+                 (gi.GI_EYTZINGER_KARY, 17))
+
+
+@pytest.mark.parametrize("E", [1, 16])
 def test_range_config_u32(ranges_u32, E):
     n, m, seed, keys, rows, sk, sr = ranges_u32
     lo, hi, w = W.ranges_with_expected_rows(n, m, E, 32, seed + E)
-    woff = np.empty(m + 1, dtype=np.uint64)
-    if E <= 16:
-        woff, wrows = oracle.range_lookup(sk, sr, lo, hi, THREADS)
-    else:
-        # offsets of every range; rows of a sample of ranges
-        c = np.searchsorted(sk, hi, side="right") - np.searchsorted(sk, lo, side="left")
-        woff[0] = 0
-        np.cumsum(c, out=woff[1:])
-        samp = np.random.default_rng(E).choice(m, size=1 << 14, replace=False)
-        soff, srows = oracle.range_lookup(sk, sr, lo[samp], hi[samp], THREADS)
+    woff, wrows = oracle.range_lookup(sk, sr, lo, hi, THREADS)
     assert abs(float(woff[-1]) / m / E - 1) < 0.02
     kd, rd, lod, hid = to_dev(keys), to_dev(rows), to_dev(lo), to_dev(hi)
-    for layout, k in ((gi.GI_SORTED, 0), (gi.GI_EYTZINGER, 2), (gi.GI_EYTZINGER_KARY, 16),
-                      (gi.GI_EYTZINGER_KARY, 17)):
+    for layout, k in RANGE_LAYOUTS:
         idx = gi.gi_build(kd, rd, layout | gi.GI_KEY_U32, k)
         off = torch.empty(m + 1, dtype=torch.int64, device=DEV)
         gi.gi_range_lookup(idx, lod, hid, off)
@@ -159,13 +154,38 @@ def test_range_config_u32(ranges_u32, E):
         gi.gi_range_lookup(idx, lod, hid, off, out)
         torch.cuda.synchronize()
         assert np.array_equal(to_host(off, np.uint64), woff), (layout, k)
-        if E <= 16:
-            assert np.array_equal(to_host(out, np.uint32), wrows), (layout, k)
-        else:
-            # gather the sampled ranges' rows on the device, compare on the host
-            o = to_host(off, np.uint64).astype(np.int64)
-            ix = np.concatenate([np.arange(o[i], o[i + 1]) for i in samp])
-            got = to_host(out[torch.from_numpy(ix).to(DEV)], np.uint32)
-            assert np.array_equal(got, srows), (layout, k)
+        assert np.array_equal(to_host(out, np.uint32), wrows), (layout, k)
         del out
         gi.gi_destroy(idx)
+
+
+def test_range_config_u32_256_rows_every_row(ranges_u32):
+    """E = 256: about 2^32 rows (16 GiB) per layout.  Every offset and every row of
+    every layout is compared with the oracle, 2^20 ranges at a time: the oracle
+    answers one chunk, and each layout's CSR slice for it is copied back and
+    compared."""
+    n, m, seed, keys, rows, sk, sr = ranges_u32
+    E = 256
+    lo, hi, w = W.ranges_with_expected_rows(n, m, E, 32, seed + E)
+    kd, rd, lod, hid = to_dev(keys), to_dev(rows), to_dev(lo), to_dev(hi)
+    outs = []
+    for layout, k in RANGE_LAYOUTS:
+        idx = gi.gi_build(kd, rd, layout | gi.GI_KEY_U32, k)
+        off = torch.empty(m + 1, dtype=torch.int64, device=DEV)
+        gi.gi_range_lookup(idx, lod, hid, off)
+        total = int(off[-1].item())
+        out = torch.empty(total, dtype=torch.int32, device=DEV)
+        gi.gi_range_lookup(idx, lod, hid, off, out)
+        torch.cuda.synchronize()
+        gi.gi_destroy(idx)
+        outs.append((layout, k, to_host(off, np.uint64).astype(np.int64), out))
+    assert abs(float(outs[0][2][-1]) / m / E - 1) < 0.02
+    chunk = 1 << 20
+    for a in range(0, m, chunk):
+        b = min(m, a + chunk)
+        coff, crows = oracle.range_lookup(sk, sr, lo[a:b], hi[a:b], THREADS)
+        for layout, k, o, out in outs:
+            assert np.array_equal(o[a:b + 1] - o[a], coff.astype(np.int64)), (layout, k, a)
+            got = to_host(out[int(o[a]):int(o[b])], np.uint32)
+            assert np.array_equal(got, crows), (layout, k, a)
+    del outs

@@ -167,3 +167,46 @@ def test_range_larger_than_its_buffer_reports_capacity():
     assert np.array_equal(off, woff)
     gi.gi_server_destroy(server)
     gi.gi_destroy(idx[0])
+
+
+@pytest.mark.parametrize("threads", [1, 4])
+def test_native_replay_results_match_oracle(threads):
+    """The native load generators (gi_server_replay, gi_replay_serial) submit the
+    same trace; every request has its own host buffers, and every answer equals the
+    oracle's, from the server and from the one-at-a-time baseline alike."""
+    idx, ref = _resident([1 << 14, 70001, 1 << 17], gi.GI_EYTZINGER_KARY, 5)
+    rng = np.random.default_rng(40 + threads)
+    trace = [_make_request(ref, rng, int(rng.integers(0, len(idx)))) for _ in range(300)]
+
+    def buffers():
+        out = []
+        for req in trace:
+            if req[0] == "point":
+                out.append((req[1], gi.GI_REQ_POINT, req[2].copy(), np.full(len(req[2]), 7, np.uint32),
+                            None, None, 0))
+            else:
+                cap = 64 * len(req[2]) + 64
+                out.append((req[1], gi.GI_REQ_RANGE, req[2].copy(), np.zeros(cap, np.uint32), req[3].copy(),
+                            np.zeros(len(req[2]) + 1, np.uint64), cap))
+        return out
+
+    arrival = np.sort(rng.integers(0, 20_000_000, size=len(trace))).astype(np.int64)  # within 20 ms
+    server = gi.gi_server_create(idx, 64 << 20, 3)
+    for replay in ("server", "serial"):
+        bufs = buffers()
+        if replay == "server":
+            lat, st, wall = gi.gi_server_replay(server, bufs, arrival, threads)
+        else:
+            lat, st, wall = gi.gi_replay_serial(idx, bufs, arrival)
+        assert (st == gi.GI_OK).all() and (lat >= 0).all() and wall > 0
+        for req, b in zip(trace, bufs):
+            want = _want(ref, req)
+            if req[0] == "point":
+                assert np.array_equal(b[3], want[0])
+            else:
+                off = b[5]
+                assert np.array_equal(off, want[0])
+                assert np.array_equal(b[3][: int(off[-1])], want[1])
+    gi.gi_server_destroy(server)
+    for ix in idx:
+        gi.gi_destroy(ix)

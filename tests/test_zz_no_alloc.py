@@ -8,12 +8,20 @@ library, so its results must equal gi_range_lookup's exactly (integer CSR
 output: offsets and rowIDs, bit for bit), on every call, including two calls in
 a row that reuse the same array.  This file is collected last on purpose.
 """
+import os
+import subprocess
+import sys
+import textwrap
+
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2506_01576_gb300 as gi
 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 pytestmark = pytest.mark.gpu
 
@@ -45,12 +53,19 @@ def _regular(idx, lo, hi):
 def _noalloc(idx, lo, hi, capacity):
     m = lo.numel()
     off = torch.full((m + 1,), -1, dtype=torch.int64, device=DEV)
-    gi.gi_range_lookup_noalloc(idx, lo, hi, off)  # offsets only
-    total = int(off[-1].item())
-    assert total <= capacity
     rows = torch.full((max(capacity, 1),), -7, dtype=torch.int32, device=DEV)
-    gi.gi_range_lookup_noalloc(idx, lo, hi, off, rows)
     torch.cuda.synchronize()
+    # any allocation the library made from here on would fail (a host-side test
+    # hook: nothing is allocated and no GPU fault is involved); the calls succeed
+    gi.gi_debug_fail_alloc(0)
+    try:
+        gi.gi_range_lookup_noalloc(idx, lo, hi, off)  # offsets only
+        total = int(off[-1].item())
+        assert total <= capacity
+        gi.gi_range_lookup_noalloc(idx, lo, hi, off, rows)
+        torch.cuda.synchronize()
+    finally:
+        gi.gi_debug_fail_alloc(-1)
     return off.cpu().numpy(), rows.cpu().numpy()[:total]
 
 
@@ -96,3 +111,70 @@ def test_noalloc_rejects_what_it_cannot_do_without_allocating():
     torch.cuda.synchronize()
     assert int(off0[0].item()) == 0
     gi.gi_destroy(idx)
+
+
+def test_regular_call_after_noalloc_recounts():
+    """Regular offsets-only call, then a noalloc call with other bounds into the
+    same offsets array, then the regular call with rows and the first bounds: the
+    last call must count again (the offsets were overwritten), not reuse the
+    first call's counts.  Checked against the oracle."""
+    n = 50_000
+    keys = W.unique_keys(n, 64, 5)
+    rows = np.arange(n, dtype=np.uint32)
+    idx = gi.gi_build(_dev(keys), _dev(rows), gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 5)
+    m = 4096
+    lo1, hi1, _ = W.ranges_with_expected_rows(n, m, 3.0, 64, 11)
+    lo2, hi2, _ = W.ranges_with_expected_rows(n, m, 30.0, 64, 12)
+    sk, sr = oracle.sort_pairs(keys, rows)
+    want_off, want_rows = oracle.range_lookup(sk, sr, lo1, hi1)
+    t1, u1, t2, u2 = _dev(lo1), _dev(hi1), _dev(lo2), _dev(hi2)
+    off = torch.empty(m + 1, dtype=torch.int64, device=DEV)
+    gi.gi_range_lookup(idx, t1, u1, off)  # first call of the two-call protocol
+    total1 = int(off[-1].item())
+    assert total1 == int(want_off[-1])
+    gi.gi_range_lookup_noalloc(idx, t2, u2, off)  # overwrites off with other counts
+    torch.cuda.synchronize()
+    out = torch.full((max(total1, 1),), -7, dtype=torch.int32, device=DEV)
+    gi.gi_range_lookup(idx, t1, u1, off, out)  # same pointers as the first call
+    torch.cuda.synchronize()
+    assert np.array_equal(off.cpu().numpy().view(np.uint64), want_off)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32)[:total1], want_rows)
+    gi.gi_destroy(idx)
+
+
+def test_first_call_during_capture_is_refused():
+    """In a fresh process the first call looks up the scratch array's address;
+    during a stream capture that is refused with a clear error, and the same call
+    made outside the capture then works."""
+    code = textwrap.dedent("""
+        import sys
+        sys.path.insert(0, %r)
+        import numpy as np, torch
+        import paper_2506_01576_gb300 as gi, workloads as W
+        gi.load()
+        dev = torch.device("cuda:0")
+        torch.cuda.set_device(dev)
+        keys = W.unique_keys(1000, 64, 3)
+        t = lambda a: torch.from_numpy(a.view(np.int64) if a.dtype == np.uint64 else a.view(np.int32)).to(dev)
+        idx = gi.gi_build(t(keys), t(np.arange(1000, dtype=np.uint32)), gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 5)
+        lo = t(np.sort(keys)[:16].copy())
+        off = torch.empty(17, dtype=torch.int64, device=dev)
+        s = torch.cuda.Stream()
+        gi.gi_set_stream(idx, s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        err = None
+        with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+            try:
+                gi.gi_range_lookup_noalloc(idx, lo, lo, off)
+            except gi.GIError as e:
+                err = e
+        assert err is not None and err.code == gi.GI_ERR_INVALID and "capture" in str(err), err
+        gi.gi_range_lookup_noalloc(idx, lo, lo, off)
+        torch.cuda.synchronize()
+        assert int(off[-1].item()) == 16
+        gi.gi_destroy(idx)
+        print("capture refusal ok")
+    """) % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "capture refusal ok" in r.stdout, r.stdout + r.stderr

@@ -518,6 +518,20 @@ def oracle_sample_text(n, m, mr, threads, sort_sample, point_sample, range_sampl
                threads, int(math.log2(m)), int(math.log2(range_sample)), threads, int(math.log2(mr))))
 
 
+def oracle_lookup_rates(oracle, sk, sr, q, threads, sample=1 << 20):
+    """std::lower_bound lookups/s of the oracle on 1 thread and on `threads` threads
+    (the same 2^20-probe sample of the workload's probes, over the full index)."""
+    x = q[:sample]
+    t0 = time.perf_counter()
+    oracle.point_lookup(sk, sr, x, 1)
+    t1 = time.perf_counter()
+    oracle.point_lookup(sk, sr, x, threads)
+    t2 = time.perf_counter()
+    return {"lookups_per_s_1_thread": len(x) / (t1 - t0),
+            "lookups_per_s_all_threads": len(x) / (t2 - t1), "threads": threads,
+            "sample_probes": len(x)}
+
+
 def cpu_oracle_sample(keys, q, lo, hi, n, m, a, sort_sample=1 << 22, point_sample=1 << 21,
                       range_sample=1 << 17):
     """The oracle as it stands on the host cores: one sampled step, scaled."""
@@ -531,7 +545,7 @@ def cpu_oracle_sample(keys, q, lo, hi, n, m, a, sort_sample=1 << 22, point_sampl
                                np.random.default_rng(0), sort_sample, point_sample, range_sample)
     return {"value": m / est, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": oracle_sample_text(n, m, mr, threads, sort_sample, point_sample, range_sample),
-            "est_step_s": est}
+            "est_step_s": est, "point_lookups": oracle_lookup_rates(oracle, sk, sr, q, threads)}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -558,17 +572,21 @@ def run_reference(a):
 
     for _ in range(a.warmup):
         step()
+    t0 = time.perf_counter()
     ests = [step() for _ in range(a.steps)]
+    wall = (time.perf_counter() - t0) / a.steps  # the sampled step as timed
     est = float(np.mean(ests))
     value = m / est
-    sample = "per step: " + oracle_sample_text(n, m, mr, threads, sort_sample, point_sample,
-                                               range_sample)
+    sample = ("each step a sample, scaled to the full step (est_full_step_ms): "
+              + oracle_sample_text(n, m, mr, threads, sort_sample, point_sample, range_sample))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
+            "warmup": a.warmup, "ms_per_step": wall * 1e3, "est_full_step_ms": est * 1e3,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "impl": "reference", "config": step_config(a, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample,
+                             "point_lookups": oracle_lookup_rates(oracle, sk, sr, q, threads)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
@@ -692,12 +710,18 @@ def batched_measure(gi, torch, dev, B, k, steps, warmup, tune=False, per_index=T
             gi.gi_batch_sync(batch)
             return t, out.cpu().numpy().view(np.uint32)
 
+        def parts_now():
+            return (ev(lambda: gi.gi_batch_build(batch, kd, rd), max(2, steps // 2)),
+                    ev(lambda: gi.gi_batch_point_lookup(batch, qd, qod, out), steps))
+
         gi.gi_batch_fanout_table_clear()
         gi.gi_batch_set_fanouts(batch, None)
         ks_auto = gi.gi_batch_get_fanouts(batch, B)
         t_auto, got_auto = graph_ms_now()
+        b_auto, l_auto = parts_now()
         ks_t, cms = gi.gi_batch_tune_fanouts(batch, B, kd, rd, qd, qod, reps=3, flags=gi.GI_TUNE_APPLY)
         t_tuned, got_tuned = graph_ms_now()
+        b_tuned, l_tuned = parts_now()
         classes = {}
         for c in range(64):
             if cms[c].max() > 0:
@@ -705,6 +729,8 @@ def batched_measure(gi, torch, dev, B, k, steps, warmup, tune=False, per_index=T
                                        "ms_by_k": {str(k): round(float(v), 4)
                                                    for k, v in zip((2, 3, 5, 9, 17), cms[c])}}
         fan = {"graph_step_ms_auto_fanouts": t_auto, "graph_step_ms_tuned_fanouts": t_tuned,
+               "build_ms_auto_fanouts": b_auto, "lookup_ms_auto_fanouts": l_auto,
+               "build_ms_tuned_fanouts": b_tuned, "lookup_ms_tuned_fanouts": l_tuned,
                "lookups_per_s_tuned_fanouts": m / (t_tuned / 1e3),
                "auto_fanout_counts": {str(k): int((ks_auto == k).sum()) for k in (2, 3, 5, 9, 17)},
                "tuned_per_class": classes,

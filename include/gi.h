@@ -107,7 +107,9 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
  *   out_rowids  m uint32: the rowID of the first entry whose key equals
  *               queries[i], or GI_MISS.  Written in probe order.
  * SORTED: textbook lower_bound; EYTZINGER: branch-free descent; EYTZINGER_KARY:
- * a lane group loads one node per level and picks the child by ballot/popc.
+ * one node per level, read with vector loads by one thread (default for nodes of
+ * at most 64 bytes) or by a group of lanes (GI_OPT_GROUP) that sums its per-lane
+ * pivot counts; the child is s*k + (c+1)*(k-1) for c pivots below the probe.
  * Errors: GI_ERR_INVALID (null index/pointer), GI_ERR_CUDA, GI_ERR_NOMEM (staging).
  */
 int gi_point_lookup(const gi_index* index, const void* queries, uint64_t m,
@@ -194,7 +196,8 @@ int gi_copy_layout(const gi_index* index, void* keys_out, uint32_t* rowids_out);
  *   GI_OPT_HOT_LEVELS   EYTZINGER_KARY: top levels read with an L2 evict-last hint;
  *                       deeper levels, rowIDs, probes and results use evict-first
  *                       (0 = every level streamed).  Default: the levels whose keys
- *                       fit in a quarter of L2.
+ *                       fit in 5/8 of L2.  (The levels whose keys fit in 128 KB are
+ *                       also the only ones allocated in L1.)
  *   GI_OPT_RANGE_FILL   Eytzinger layouts: 1 writes a range's rows level by level,
  *                       one contiguous slot run per level, a warp taking runs of
  *                       >= 32 slots (Sections 5, 5.1); 0 (default) maps every rank
@@ -373,8 +376,8 @@ void gi_batch_destroy(gi_batch* batch);
  * (capturable).
  * gi_batch_set_fanouts -- ks: B host fan-outs, or NULL for the automatic choice
  *   per size class floor(log2 n_i): the one gi_batch_tune_fanouts recorded for the
- *   batch's key width, else k = 3 up to 2^17 key bytes, 2 up to 2^22 key bytes,
- *   5 above (measured on single u64 indexes).  Takes effect at the next
+ *   batch's key width, else k = 3 up to 32 KB of keys and k = 5 above (measured on
+ *   a batch of 2^8..2^20 u64 keys per index).  Takes effect at the next
  *   gi_batch_build (the indexes must be built again).  Synchronous (waits for the
  *   batch's stream); call it outside stream capture.
  *   Errors: GI_ERR_INVALID (a fan-out outside the set), GI_ERR_CUDA.

@@ -424,12 +424,12 @@ bool eks_group_supported(uint32_t k, int key_bytes, int group) {
 
 int eks_default_group(uint32_t k, int key_bytes) {
   // One thread per lookup reading its whole node with vector loads measured
-  // fastest beyond L2 (fewest instructions per level); nodes wider than 64
-  // bytes are split over lanes in 32-byte pieces, one sector per lane (the
-  // autotuner's choice for 128-byte nodes from 2^16 keys up: 1.4-1.7x over
-  // 16-byte pieces), else 16-byte pieces.
+  // fastest (fewest instructions per level), up to 128-byte nodes: at 2^26 u64
+  // keys and k = 17, 10.9 ms for 2^27 lookups against 12.6 ms with 4 lanes of
+  // 32 bytes (k = 9: 6.7 ms against 10.3 with 2 lanes).  Wider nodes are split
+  // over lanes in 32-byte pieces, one sector per lane, else 16-byte pieces.
   const int node_bytes = (int)(k - 1) * key_bytes;
-  if (node_bytes <= 64 && eks_group_supported(k, key_bytes, 1)) return 1;
+  if (node_bytes <= 128 && eks_group_supported(k, key_bytes, 1)) return 1;
   if (node_bytes % 32 == 0 && eks_group_supported(k, key_bytes, node_bytes / 32)) return node_bytes / 32;
   if (node_bytes % 16 == 0 && eks_group_supported(k, key_bytes, node_bytes / 16)) return node_bytes / 16;
   for (int g = 32; g >= 1; g >>= 1)

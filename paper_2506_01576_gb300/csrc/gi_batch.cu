@@ -7,18 +7,25 @@
 // no allocation, no host synchronisation.  The sequence can be captured in a
 // CUDA graph and replayed.
 //
-//   build : one segmented radix sort over the concatenated pairs (gi_sort.cu:
-//           each tile stays inside its index; look-back stops at the index's
-//           first tile), then the per-index closed-form permutation into a padded
-//           per-index region (max-key padding after every index, 256-byte
-//           aligned starts).
+//   build : every index is sorted by a plan a kernel writes on the device from
+//           the bits in which its keys differ (gi_sort.cu): a whole index of at
+//           most 5120 pairs by one CTA in shared memory; a larger one by a stable
+//           MSD scatter on a window of its highest varying bits, then the same
+//           bucket sort on every window bucket; the LSD passes (segmented: each
+//           tile stays inside its index, look-back stops at the index's first
+//           tile) only when a window bucket is too large.  The bucket sort writes
+//           each pair straight into its index's layout -- the index's own fan-out
+//           (gi_batch_set_fanouts), sorted or k-ary -- in a padded per-index
+//           region (max-key padding after every index, 256-byte aligned starts);
+//           after the LSD passes the closed-form permutation does.
 //   lookup: one persistent launch over (index, chunk of probes) work items.  A
 //           CTA takes a work item, copies the top levels of that index that fit
 //           in its shared-memory budget with one bulk asynchronous copy
-//           (mbarrier, bounded wait), then every thread runs the k-ary descent
-//           for its probes, reading pinned levels from shared memory and the
-//           rest from global memory.  The pinned depth is chosen per index by
-//           its size (small indexes are pinned whole).
+//           (mbarrier, bounded wait), then every thread runs the descent of the
+//           index's layout (binary search, or k-ary with its fan-out) for its
+//           probes, reading pinned levels from shared memory and the rest from
+//           global memory.  The pinned depth is chosen per index by its size
+//           (small indexes are pinned whole).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -306,9 +313,12 @@ std::mutex g_fanout_mu;
 uint32_t g_fanout_table[2][64] = {};
 
 // The fan-out an index of n keys takes when the caller leaves it to the library:
-// the recorded choice of its size class, else the composite strategy measured
-// for single indexes of u64 keys (k = 3 for at most 2^14 keys = 128 KB, Eytzinger
-// order (k = 2) up to 2^19 keys = 4 MB, k = 5 above), by key bytes for u32 keys.
+// the recorded choice of its size class, else k = 3 for at most 32 KB of keys and
+// k = 5 above.  Measured in a batch of 1024 indexes of 2^8..2^20 u64 keys
+// (gi_batch_tune_fanouts, lookups of each size class alone): k = 3 fastest at
+// 2^10..2^12 keys (by 5-10%), k = 5 from 2^15 keys up (by 1-20%), the two within
+// 3% elsewhere; Eytzinger order (k = 2) never fastest in a batch, although it is
+// for single indexes of 2^15..2^19 keys.  Key bytes set the bound for u32 keys.
 uint32_t auto_fanout(int key_bytes, uint64_t n) {
   if (n == 0) return 5;
   const uint32_t cls = 63 - (uint32_t)__builtin_clzll(n);
@@ -317,10 +327,7 @@ uint32_t auto_fanout(int key_bytes, uint64_t n) {
     const uint32_t k = g_fanout_table[key_bytes == 8 ? 1 : 0][cls];
     if (k) return k;
   }
-  const uint64_t bytes = n * (uint64_t)key_bytes;
-  if (bytes <= (1ull << 17)) return 3;
-  if (bytes <= (1ull << 22)) return 2;
-  return 5;
+  return n * (uint64_t)key_bytes <= (1ull << 15) ? 3u : 5u;
 }
 
 // per-index pinning: the top levels whose slots fit in the budget (whole index if small)

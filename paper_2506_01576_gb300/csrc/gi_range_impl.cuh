@@ -9,9 +9,13 @@
 //           block sums, down-sweep; no inter-block waits).
 //   fill  : rows of rank r come from slot(r), the closed-form inverse of p'.
 //           A warp takes 32 consecutive ranges; ranges with at least 32 rows are
-//           emitted by the whole warp with coalesced stores, the others by their
-//           own lane -- the single-thread / warp switch of Section 5.1 applied to
-//           the output pass.
+//           emitted by the whole warp with coalesced stores, one range at a time;
+//           the rows of the shorter ranges are dealt to the lanes together (each
+//           lane finds its row's range by a 5-step shuffle search over the
+//           running counts), so their stores are coalesced too -- the paper's
+//           single-thread / warp switch of Section 5.1 applied to the output
+//           pass.  GI_OPT_RANGE_FILL = 1 instead walks each range level by level,
+//           one contiguous slot run per level (k_range_fill_levels).
 // Rows of a range come out in ascending rank order, i.e. ascending (key, input
 // position) order, for every layout.  (The paper's level-by-level scan emits
 // them level by level instead; Section 5.)

@@ -1,5 +1,5 @@
-// Build path: stable LSD radix sort of (key, rowID) pairs, then the closed-form
-// permutation into Eytzinger / k-ary Eytzinger order.
+// Build path: key-value radix sort of (key, rowID) pairs into the sorted order
+// and, for the Eytzinger layouts, into the closed-form permutation of that order.
 //
 // The paper builds the sorted array with a library key-value sort (Section 3)
 // and moves it into Eytzinger order with one thread per target slot, each
@@ -7,17 +7,24 @@
 // (Section 4, generalised to k in Section 6.1).  Here the sort is our own:
 //
 //   1. sort_prepare: one read of the keys computes the 256-bin histogram of
-//      every 8-bit digit at once, checks the rowIDs for the reserved value, and
-//      scans each histogram into global digit offsets.  Passes whose digit is
-//      the same for every key are skipped.
-//   2. sort_pass (one per remaining digit): a single-pass "onesweep" scatter.
-//      Each CTA takes the next tile in launch order, ranks its keys stably by
-//      digit with warp ballots, publishes its per-digit counts and finds its
-//      global offsets by decoupled look-back over earlier tiles (a bounded wait),
-//      then writes keys and rowIDs through shared memory so that each digit's
-//      run leaves the SM as consecutive addresses.
-//   3. layout_gather: slot t <- sorted[p'(t)], one read and one write per entry,
+//      every 8-bit digit at once and scans each into global digit offsets.
+//      Digits that are the same for every key are skipped by every later pass.
+//   2. Default for large u64 inputs, the hybrid sort (hybrid_sort): one or two
+//      stable MSD scatters on the top non-trivial digits (a plain pass, then a
+//      pass segmented by first-level bucket), after which every bucket holds at
+//      most 5120 pairs and is sorted by one CTA in shared memory
+//      (gi_local_sort.cu), which writes each pair straight to its layout slot.
+//   3. Otherwise (small or narrow inputs, or a bucket too large: the LSD
+//      fallback) sort_pass once per remaining digit: a single-pass "onesweep"
+//      scatter.  Each CTA takes the next tile in launch order, ranks its keys
+//      stably by digit with warp ballots, publishes its per-digit counts and
+//      finds its global offsets by decoupled look-back over earlier tiles (a
+//      bounded wait), then writes keys and rowIDs through shared memory so that
+//      each digit's run leaves the SM as consecutive addresses.  Then
+//      layout_gather: slot t <- sorted[p'(t)], one read and one write per entry,
 //      fused with the duplicate-key check.
+//   The batched form (many indexes at once) uses the same passes segmented by
+//   index, on plans written on the device (gi_batch.cu).
 #include <cuda_runtime.h>
 #include <stdint.h>
 

@@ -335,9 +335,9 @@ def test_batch_fanout_per_index_equals_oracle(bits):
 
 
 def test_batch_fanout_automatic_and_graph_replay():
-    """NULL fan-outs choose by size class (k = 3 up to 2^14 u64 keys, Eytzinger
-    order up to 2^19, k = 5 above, when nothing is recorded); the mixed batch's
-    build + lookup replayed from a CUDA graph gives the oracle's answers."""
+    """NULL fan-outs choose by size class (k = 3 up to 2^12 u64 keys, k = 5 above,
+    when nothing is recorded); the mixed batch's build + lookup replayed from a
+    CUDA graph gives the oracle's answers."""
     gi.gi_batch_fanout_table_clear()
     rng = np.random.default_rng(12)
     sizes = [int(x) for x in np.exp2(rng.uniform(8, 20, size=40)).astype(np.int64)]
@@ -346,7 +346,7 @@ def test_batch_fanout_automatic_and_graph_replay():
     batch = gi.gi_batch_create(off, gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 5)
     gi.gi_batch_set_fanouts(batch, None)
     ks = gi.gi_batch_get_fanouts(batch, len(sizes))
-    want = [3 if n <= (1 << 14) else 2 if n <= (1 << 19) else 5 for n in sizes]
+    want = [3 if n <= (1 << 12) else 5 for n in sizes]
     assert list(ks) == want
     kd, rd = to_dev(np.concatenate(keys)), to_dev(np.concatenate(rows))
     qd, qod = to_dev(np.concatenate(qs)), to_dev(qoff)

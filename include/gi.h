@@ -58,12 +58,14 @@ typedef struct gi_index gi_index;
 /* Build flags, OR-ed into `layout` of gi_build (at most one).  Both give the same
  * index; they choose how the pairs are sorted.
  *   default          u64 keys with at least five non-trivial digits (bytes that
- *                    differ between keys) and 2^24 <= n < 2^32 take the hybrid
- *                    sort: stable scatters on the top two non-trivial digits, then
- *                    every resulting bucket sorted in one CTA's shared memory and
- *                    written straight into the layout.  Smaller or narrower inputs,
- *                    and inputs whose buckets come out larger than 5120 pairs,
- *                    take the plain LSD sort.
+ *                    differ between keys) and 2^24 <= n <= 2^28 + 2^27 (about) take
+ *                    the hybrid sort: a stable scatter on the 8 bits just below the
+ *                    highest bit in which two keys differ, then one on up to 8
+ *                    further bits (as many as split the largest bucket into pieces
+ *                    of about 2048 pairs), then every resulting bucket sorted in
+ *                    one CTA's shared memory and written straight into the layout.
+ *                    Smaller or narrower inputs, and inputs whose buckets come out
+ *                    larger than 5120 pairs, take the plain LSD sort.
  *   GI_BUILD_LSD     always the plain 8-bit LSD radix passes (then the permutation).
  *   GI_BUILD_HYBRID  the hybrid sort whenever it can run (at least two non-trivial
  *                    digits, n < 2^32, buckets of at most 5120 pairs), whatever n

@@ -140,6 +140,7 @@ struct PinnedScratch {
   uint32_t* trivial = nullptr;        // [8]
   unsigned long long* hist = nullptr;  // [8][256]
   unsigned long long* h2 = nullptr;    // [256][256]
+  unsigned long long* win = nullptr;   // [2 + 256]: the MSD window's record
   cudaEvent_t ev = nullptr;
   int device = -1;
   cudaError_t ensure() {
@@ -152,7 +153,7 @@ struct PinnedScratch {
       trivial = nullptr;
     }
     void* p = nullptr;
-    const size_t bytes = 256 + sizeof(uint64_t) * (8 * 256 + 256 * 256);
+    const size_t bytes = 256 + sizeof(uint64_t) * (8 * 256 + 256 * 256 + 2 + 256);
     cudaError_t e = cudaMallocHost(&p, bytes);
     if (e != cudaSuccess) return e;
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -163,6 +164,7 @@ struct PinnedScratch {
     trivial = (uint32_t*)p;
     hist = (unsigned long long*)((char*)p + 256);
     h2 = hist + 8 * 256;
+    win = h2 + 256 * 256;
     device = dev;
     return cudaSuccess;
   }
@@ -617,8 +619,18 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   // the host plans
   PinnedScratch& pin = pinned_scratch();
   GI_TRY2(pin.ensure(), "page-locked scratch");
+  // Where the hybrid sort will likely follow (u64 keys from 2^24 pairs up, or
+  // forced), the histogram pass also finds the bits in which keys differ and a
+  // second read counts the 8-bit window just below the highest of them; the first
+  // MSD scatter on that window is queued at once, before the host has seen any
+  // counts.  Up to 256 x 256 x 7/8 of the bucket capacity pairs: beyond, buckets
+  // of uniform keys would be too large for a CTA and the LSD sort would redo it.
+  const uint64_t spec_max = 256ull * 256ull * gi::local_sort_capacity() / 8 * 7;
+  const bool hybrid_ok = !(flags & GI_BUILD_LSD) && n < (1ull << 32) &&
+                         ((kb == 8 && n >= (1ull << 24) && n <= spec_max) || (flags & GI_BUILD_HYBRID));
   GI_TRY2(gi::sort_prepare(keys_bus ? keys_bus : src_k, keys_bus ? bk[0] : nullptr, n, kb, scratch,
-                           s, pin.trivial, pin.hist),
+                           s, pin.trivial, hybrid_ok ? pin.win : nullptr,
+                           (flags & GI_BUILD_HYBRID) ? 2u : 5u),
           "histogram");
   cudaEvent_t hist_ready = pin.ev;
   GI_TRY2(cudaEventRecord(hist_ready, s), "histogram");
@@ -628,22 +640,15 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   const uint32_t* cv = src_v;
   int cur = -1;  // -1: the data is still the (caller's or staged) input
   int next_dst = staged ? 1 : 0;
-  // Speculate where the hybrid sort will likely follow: u64 keys from 2^24 pairs up,
-  // and at most 128 x 256 x the bucket capacity pairs (beyond, keys spread over
-  // only half the top byte, as uniform ones below 2^63 do, give buckets too large
-  // for a CTA, and the pass would be redone by the LSD sort).
-  const uint64_t spec_max = 128ull * 256ull * gi::local_sort_capacity();
-  bool speculate = !(flags & GI_BUILD_LSD) && kb == 8 && n < (1ull << 32) && n <= spec_max &&
-                   (n >= (1ull << 24) || (flags & GI_BUILD_HYBRID));
-  if (speculate)  // skipped on the device if every key has the same top byte
-    GI_TRY2(gi::sort_msd_pass(ck, cv, bk[next_dst], bv[next_dst], n, kb, kb - 1, scratch,
-                              idx->dflags, true, s),
+  bool speculate = hybrid_ok;
+  if (speculate)  // skipped on the device if every key has the same window value
+    GI_TRY2(gi::sort_window_pass(ck, cv, bk[next_dst], bv[next_dst], n, kb, scratch, idx->dflags, s),
             "radix pass");
   GI_TRY2(cudaEventSynchronize(hist_ready), "histogram");
-  uint32_t trivial = 0;
+  uint32_t trivial = 0;  // digits with one value only: zero bytes of the OR of key ^ keys[0]
   for (int p = 0; p < kb; ++p)
-    if (pin.trivial[p]) trivial |= 1u << p;
-  if (trivial & (1u << (kb - 1))) speculate = false;  // that pass wrote nothing
+    if (hybrid_ok ? ((pin.win[0] >> (8 * p)) & 0xFF) == 0 : pin.trivial[p] != 0) trivial |= 1u << p;
+  if (speculate && (pin.win[1] >> 32)) speculate = false;  // that pass wrote nothing
   bool sorted_done = false, pass1_pending_reset = false;
   if (speculate) {  // the MSD pass ran: a stable permutation into bk[next_dst]
     ck = bk[next_dst];
@@ -656,10 +661,10 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
     bool used = false;
     const uint32_t nontrivial = ~trivial & ((1u << kb) - 1);
     GI_TRY2(gi::hybrid_sort(speculate ? src_k : ck, speculate ? src_v : cv, bk, bv,
-                            speculate ? cur : next_dst, n, kb, nontrivial, pin.hist, scratch,
-                            idx->geom, lay == GI_SORTED, lay == GI_EYTZINGER ? 1u : 0u,
-                            (flags & GI_BUILD_HYBRID) != 0, speculate, pin.h2, idx->dflags, s,
-                            &res, &used),
+                            speculate ? cur : next_dst, n, kb, nontrivial,
+                            hybrid_ok ? pin.win : nullptr, scratch, idx->geom, lay == GI_SORTED,
+                            lay == GI_EYTZINGER ? 1u : 0u, (flags & GI_BUILD_HYBRID) != 0,
+                            speculate, pin.h2, idx->dflags, s, &res, &used),
             "hybrid sort");
     if (res >= 0) {
       ck = bk[res];
@@ -672,6 +677,8 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   if (cur >= 0) next_dst = 1 - cur;
   if (!sorted_done && pass1_pending_reset)  // the LSD passes reuse the MSD pass's ticket
     GI_TRY2(gi::sort_reset_counters(scratch, kb, s), "radix pass");
+  if (!sorted_done && hybrid_ok && (trivial != (1u << kb) - 1))  // digit counts skipped so far
+    GI_TRY2(gi::sort_counts(ck, n, kb, scratch, s), "histogram");
   for (int p = 0; p < kb && !sorted_done; ++p) {
     if (trivial & (1u << p)) continue;  // every key has the same digit here
     const int dst = next_dst;

@@ -220,19 +220,29 @@ struct SortBuffers {
 };
 size_t sort_scratch_bytes(uint64_t n, int key_bytes);
 // Histogram all digits and scan them on the device, then copy the per-digit
-// "one value only" flags and the counts to host_trivial[key_bytes] /
-// host_hist[key_bytes][256] (page-locked; valid once the stream gets there: no
-// synchronisation inside).  copy_to != NULL: `keys` is page-locked host memory,
-// copied to copy_to by the same pass.
+// "one value only" flags to host_trivial[key_bytes] (page-locked; valid once the
+// stream gets there: no synchronisation inside).  copy_to != NULL: `keys` is
+// page-locked host memory, copied to copy_to by the same pass.
+// host_win != NULL (the hybrid sort may follow): instead no digit counts (see
+// sort_counts), but the counts of the 8-bit window just below the highest bit in
+// which two keys differ, into host_win[2..257], with host_win[0] = the OR of
+// key ^ keys[0] (its zero bytes are the trivial digits) and host_win[1] = window
+// shift | (1 if one value only) << 32 (page-locked, 258 words); min_bytes: with
+// fewer differing key bytes the window is marked trivial (the hybrid sort does not
+// apply, and the window pass skips).
 cudaError_t sort_prepare(const void* keys, void* copy_to, uint64_t n, int key_bytes,
                          void* scratch, cudaStream_t s, uint32_t* host_trivial,
-                         unsigned long long* host_hist);
-// One stable MSD pass on `digit` (offsets from sort_prepare), reading the input
-// rowIDs (checked for the reserved value).  skip_if_trivial: the kernel returns
-// at once (nothing written) if sort_prepare found one value only in that digit.
-cudaError_t sort_msd_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
-                          uint64_t n, int key_bytes, int digit, void* scratch, uint32_t* dflags,
-                          bool skip_if_trivial, cudaStream_t s);
+                         unsigned long long* host_win, uint32_t min_bytes);
+// The digit counts and offsets the LSD passes use, after a sort_prepare with
+// host_win (`keys`: any permutation of the input, on the device).
+cudaError_t sort_counts(const void* keys, uint64_t n, int key_bytes, void* scratch, cudaStream_t s);
+// The stable MSD scatter on that window (after sort_prepare with host_win; its
+// shift and offsets are read on the device, so it can be queued before the host
+// has seen them), reading the input rowIDs (checked for the reserved value).
+// Skipped on the device if every key has the same window value.
+cudaError_t sort_window_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
+                             uint64_t n, int key_bytes, void* scratch, uint32_t* dflags,
+                             cudaStream_t s);
 // Tile tickets back to zero (before LSD passes that follow an MSD pass).
 cudaError_t sort_reset_counters(void* scratch, int key_bytes, cudaStream_t s);
 // check_rows: this pass reads the caller's rowIDs; flag any equal to GI_MISS.
@@ -325,14 +335,15 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
                          cudaStream_t s, const BatchHybrid* hy, uint32_t nseg);
 
 
-// Hybrid sort: stable MSD scatter(s) on the top one or two non-trivial digits,
-// (by default only where it measured faster; force = GI_BUILD_HYBRID: wherever it
-// can run),
-// then every bucket sorted in shared memory and written straight into the final
-// layout (gi_local_sort.cu): slot = rank for the sorted layout, else the k-ary
-// (k = g.k; Eytzinger for k = 2, keys shifted by key_off) slot of the rank.
-// pass1_done: the caller already ran the MSD pass on the top byte into
-// bk[first_dst].  host_h2: page-locked room for 256 x 256 counts.
+// Hybrid sort: stable MSD scatter(s) on one or two 8-bit windows just below the
+// highest bit in which two keys differ (by default only where it measured
+// faster; force = GI_BUILD_HYBRID: wherever it can run), then every bucket
+// sorted in shared memory and written straight into the final layout
+// (gi_local_sort.cu): slot = rank for the sorted layout, else the k-ary (k = g.k;
+// Eytzinger for k = 2, keys shifted by key_off) slot of the rank.
+// host_win: sort_prepare's window record (NULL: not applicable).  pass1_done: the
+// caller already ran sort_window_pass into bk[first_dst].  host_h2: page-locked
+// room for 256 x 256 counts.
 // *used = true: bk[*result] / bv[*result] hold the finished layout and the
 // duplicate flag is set.  *used = false and *result = -1: not applicable,
 // nothing launched.  *used = false and *result >= 0: bk[*result] holds the data
@@ -340,17 +351,21 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
 // bucket too large), for a full LSD sort (counters reset only in the latter).
 cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], uint32_t* bv[2],
                         int first_dst, uint64_t n, int key_bytes, uint32_t nontrivial,
-                        const unsigned long long* host_hist, void* scratch, const Geom& g,
+                        const unsigned long long* host_win, void* scratch, const Geom& g,
                         bool sorted_layout, uint32_t key_off, bool force, bool pass1_done,
                         unsigned long long* host_h2, uint32_t* dflags, cudaStream_t s,
                         int* result, bool* used);
-// Shared-memory sort of buckets of at most local_sort_capacity() pairs that
-// agree on every digit outside local_mask, written into the layout (see above).
+// Shared-memory sort of buckets of at most local_sort_capacity() pairs whose keys
+// agree on every bit outside the bytes of lsd_mask and above top_shift + 8: one
+// stable split on the 8 bits at top_shift, then count ranking (or, with a large
+// sub-bucket, one ballot pass per byte of lsd_mask; single: the split alone
+// sorts), written into the layout (see above).
 uint32_t local_sort_capacity();
 cudaError_t local_sort(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
                        const BatchTile* segs, uint64_t nseg, uint64_t max_count,
-                       uint32_t local_mask, int key_bytes, const Geom& g, bool sorted_layout,
-                       uint32_t key_off, uint32_t* dflags, cudaStream_t s);
+                       uint32_t top_shift, uint32_t lsd_mask, bool single, int key_bytes,
+                       const Geom& g, bool sorted_layout, uint32_t key_off, uint32_t* dflags,
+                       cudaStream_t s);
 
 // Point lookups (gi_point.cu).
 struct LookupCfg {

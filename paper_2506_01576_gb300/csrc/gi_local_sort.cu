@@ -273,21 +273,20 @@ template <class K, int ITEMS, int T, int MINB, int KF>
 __global__ void __launch_bounds__(T, MINB) k_local_sort(
     const K* __restrict__ src_k, const uint32_t* __restrict__ src_v, K* __restrict__ dst_k,
     uint32_t* __restrict__ dst_v, const BatchTile* __restrict__ segs, uint64_t nseg,
-    uint32_t local_mask, uint32_t limit, SlotMap sm, uint32_t key_off, uint32_t* __restrict__ flags) {
+    uint32_t top_shift, uint32_t lsd_mask, uint32_t single, uint32_t limit, SlotMap sm,
+    uint32_t key_off, uint32_t* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BucketSmem<K, ITEMS, T> m(smem_raw);
   __shared__ SlotMap s_map;  // the slot map from shared memory: 12% faster than from the
                              // kernel parameters in the layout write (measured)
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid < (int)(sizeof(SlotMap) / 4)) ((uint32_t*)&s_map)[tid] = ((const uint32_t*)&sm)[tid];
-  const uint32_t top = local_mask ? 31u - (uint32_t)__clz(local_mask) : 0u;
-  const bool single = __popc(local_mask) <= 1;  // the top pass alone sorts the bucket
   bool dup = false;
   for (uint64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
     const BatchTile seg = segs[sg];
     const BucketOrder<K> ord = sort_bucket<K, ITEMS, T>(m, src_k, src_v, seg.start, seg.count,
-                                                        8u * top, local_mask, single, limit, false,
-                                                        flags);
+                                                        top_shift, lsd_mask, single != 0, limit,
+                                                        false, flags);
     // sorted position j -> rank seg.start + j -> its slot in the layout
     for (uint32_t j = tid; j < seg.count; j += T) {
       const uint32_t p = ord.direct ? j : m.s_src[j];
@@ -396,10 +395,20 @@ __global__ void __launch_bounds__(256) k_batch_bucket_lists(
 // SM), up to 4096 (256 x 16, 2 per SM), up to 5120 (512 x 10, 2 per SM).
 #define GI_LOCAL_CLASSES(X) X(12, 256, 3, 0u, 3072u) X(16, 256, 2, 3072u, 4096u) X(10, 512, 2, 4096u, 5120u)
 
+// Size classes of the single-index bucket sort (one launch takes the class of the
+// largest bucket): smaller buckets in narrower classes leave room for more CTAs
+// per SM.  Up to 1536 pairs: 256 threads x 6, 5 CTAs per SM; 2560: x 10, 4 per SM
+// (2.6% faster than the 3072 class on 2048-pair buckets); 4096: 512 threads x 8,
+// 2 per SM (twice the threads of the batch's 256 x 16 class); then as the batch.
+#define GI_LOCAL_CLASSES_SINGLE(X) \
+  X(6, 256, 5, 0u, 1536u) X(10, 256, 4, 1536u, 2560u) X(12, 256, 3, 2560u, 3072u) \
+  X(8, 512, 2, 3072u, 4096u) X(10, 512, 2, 4096u, 5120u)
+
 template <class K, int KF>
 cudaError_t launch(const K* sk, const uint32_t* sv, K* dk, uint32_t* dv, const BatchTile* segs,
-                   uint64_t nseg, uint64_t max_count, uint32_t mask, uint32_t limit,
-                   const SlotMap& sm, uint32_t key_off, uint32_t* dflags, cudaStream_t s) {
+                   uint64_t nseg, uint64_t max_count, uint32_t top_shift, uint32_t mask,
+                   uint32_t single, uint32_t limit, const SlotMap& sm, uint32_t key_off,
+                   uint32_t* dflags, cudaStream_t s) {
   bool done = false;
 #define GI_LS(IT, T, MB, LO, HI)                                                               \
   if (!done && max_count <= HI) {                                                              \
@@ -409,10 +418,11 @@ cudaError_t launch(const K* sk, const uint32_t* sv, K* dk, uint32_t* dv, const B
                                          (int)smem);                                           \
     if (e != cudaSuccess) return e;                                                            \
     const unsigned grid = (unsigned)std::min<uint64_t>(nseg, (uint64_t)sm_count() * MB * 4);   \
-    kern<<<grid, T, smem, s>>>(sk, sv, dk, dv, segs, nseg, mask, limit, sm, key_off, dflags);  \
+    kern<<<grid, T, smem, s>>>(sk, sv, dk, dv, segs, nseg, top_shift, mask, single, limit, sm,  \
+                               key_off, dflags);                                               \
     done = true;                                                                               \
   }
-  GI_LOCAL_CLASSES(GI_LS)
+  GI_LOCAL_CLASSES_SINGLE(GI_LS)
 #undef GI_LS
   if (!done) return cudaErrorInvalidValue;
   count_launch();
@@ -421,13 +431,14 @@ cudaError_t launch(const K* sk, const uint32_t* sv, K* dk, uint32_t* dv, const B
 
 template <class K>
 cudaError_t launch_kf(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
-                      const BatchTile* segs, uint64_t nseg, uint64_t max_count, uint32_t mask,
-                      uint32_t limit, const Geom& g, bool sorted, uint32_t key_off,
-                      uint32_t* dflags, cudaStream_t s) {
+                      const BatchTile* segs, uint64_t nseg, uint64_t max_count, uint32_t top_shift,
+                      uint32_t mask, uint32_t single, uint32_t limit, const Geom& g, bool sorted,
+                      uint32_t key_off, uint32_t* dflags, cudaStream_t s) {
   const K* a = (const K*)sk;
   K* b = (K*)dk;
   const SlotMap sm = make_slot_map(g);
-#define GI_L(KF, OFF) launch<K, KF>(a, sv, b, dv, segs, nseg, max_count, mask, limit, sm, OFF, dflags, s)
+#define GI_L(KF, OFF) \
+  launch<K, KF>(a, sv, b, dv, segs, nseg, max_count, top_shift, mask, single, limit, sm, OFF, dflags, s)
   if (sorted) return GI_L(1, 0);
   switch (g.k) {
     case 2: return GI_L(2, key_off);
@@ -504,18 +515,19 @@ uint32_t local_sort_capacity() { return kCapacity; }
 
 cudaError_t local_sort(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
                        const BatchTile* segs, uint64_t nseg, uint64_t max_count,
-                       uint32_t local_mask, int key_bytes, const Geom& g, bool sorted_layout,
-                       uint32_t key_off, uint32_t* dflags, cudaStream_t s) {
+                       uint32_t top_shift, uint32_t lsd_mask, bool single, int key_bytes,
+                       const Geom& g, bool sorted_layout, uint32_t key_off, uint32_t* dflags,
+                       cudaStream_t s) {
   if (nseg == 0) return cudaSuccess;
   if (max_count > local_sort_capacity() || g.n >= (1ull << 32)) return cudaErrorInvalidValue;
   // count ranking costs about one compare per key of the sub-bucket; past this
   // size the remaining ballot passes are cheaper
-  const uint32_t limit = 8u * (uint32_t)__builtin_popcount(local_mask) + 8u;
+  const uint32_t limit = 8u * (uint32_t)__builtin_popcount(lsd_mask) + 8u;
   if (key_bytes == 4)
-    return launch_kf<uint32_t>(sk, sv, dk, dv, segs, nseg, max_count, local_mask, limit, g,
-                               sorted_layout, key_off, dflags, s);
-  return launch_kf<uint64_t>(sk, sv, dk, dv, segs, nseg, max_count, local_mask, limit, g,
-                             sorted_layout, key_off, dflags, s);
+    return launch_kf<uint32_t>(sk, sv, dk, dv, segs, nseg, max_count, top_shift, lsd_mask,
+                               single ? 1u : 0u, limit, g, sorted_layout, key_off, dflags, s);
+  return launch_kf<uint64_t>(sk, sv, dk, dv, segs, nseg, max_count, top_shift, lsd_mask,
+                             single ? 1u : 0u, limit, g, sorted_layout, key_off, dflags, s);
 }
 
 cudaError_t batch_local_sort(const void* keys, const uint32_t* vals, const void* src_k,

@@ -75,17 +75,40 @@ __device__ __forceinline__ void st_volatile_u64(uint64_t* p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// The 8-bit window just below the highest bit in which two keys differ: the
+// first MSD scatter of the hybrid sort (so that no bit of it is wasted on bits
+// every key shares, as the top byte of keys below 2^63 would).
+struct Window {
+  unsigned long long xor_or;  // OR over the keys of key ^ keys[0]
+  uint32_t shift;             // the window is bits [shift, shift + 8)
+  uint32_t trivial;           // 1 if every key has the same window value
+  unsigned long long hist[kRadix];
+  unsigned long long offs[kRadix];
+};
+
+__host__ __device__ inline uint32_t window_shift(unsigned long long xor_or) {
+  if (!xor_or) return 0;
+#ifdef __CUDA_ARCH__
+  const int hb = 63 - __clzll((long long)xor_or);
+#else
+  const int hb = 63 - __builtin_clzll(xor_or);
+#endif
+  return hb >= 7 ? (uint32_t)(hb - 7) : 0u;
+}
+
 // Scratch layout (bytes, each region 256-aligned):
 //   hist    [passes][256] u64   digit counts
 //   offs    [passes][256] u64   exclusive digit offsets
 //   trivial [passes]      u32   1 if one digit holds every key
-//   counter [passes]      u32   tile tickets
+//   counter [passes + 1]  u32   tile tickets (the last: the window pass)
+//   win     Window              the window's counts, offsets and shift
 //   status  [tiles][256]  u64   look-back words (epoch = pass + 1)
 struct ScratchView {
   unsigned long long* hist;
   unsigned long long* offs;
   uint32_t* trivial;
   uint32_t* counter;
+  Window* win;
   uint64_t* status;
 };
 
@@ -108,14 +131,17 @@ inline ScratchView view(void* scratch, int key_bytes) {
   v.trivial = (uint32_t*)p;
   p += align256(sizeof(uint32_t) * passes);
   v.counter = (uint32_t*)p;
-  p += align256(sizeof(uint32_t) * passes);
+  p += align256(sizeof(uint32_t) * (passes + 1));
+  v.win = (Window*)p;
+  p += align256(sizeof(Window));
   v.status = (uint64_t*)p;
   return v;
 }
 
 inline size_t header_bytes(int key_bytes) {
   const int passes = key_bytes;
-  return 2 * align256(sizeof(uint64_t) * passes * kRadix) + 2 * align256(sizeof(uint32_t) * passes);
+  return 2 * align256(sizeof(uint64_t) * passes * kRadix) + align256(sizeof(uint32_t) * passes) +
+         align256(sizeof(uint32_t) * (passes + 1)) + align256(sizeof(Window));
 }
 
 // ---------------------------------------------------------------- histogram
@@ -128,15 +154,22 @@ __device__ __forceinline__ void count_digits(uint32_t (*sh)[kRadix], K key) {
   for (int p = 0; p < (int)sizeof(K); ++p) atomicAdd(&sh[p][(uint32_t)(key >> (8 * p)) & 0xFF], 1u);
 }
 
-template <class K>
+// COUNT = false: only the OR of key ^ keys[0] (and the copy); the digit counts are
+// taken later, and only if the LSD passes need them.
+template <class K, bool COUNT = true>
 __global__ void __launch_bounds__(256) k_histogram(const K* __restrict__ keys,
                                                    K* __restrict__ copy_to, uint64_t n,
-                                                   unsigned long long* __restrict__ hist) {
+                                                   unsigned long long* __restrict__ hist,
+                                                   unsigned long long* __restrict__ xor_or) {
   constexpr int P = sizeof(K);
   constexpr int V = 16 / sizeof(K);  // keys per 16-byte load
   __shared__ uint32_t sh[P][kRadix];
+  __shared__ unsigned long long s_or;
   for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
+  if (threadIdx.x == 0) s_or = 0;
   __syncthreads();
+  const K k0 = n ? keys[0] : K(0);
+  K acc = 0;  // OR of key ^ keys[0]: the bits in which two keys differ
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // 16-byte loads, two in flight per thread, when both pointers allow them
@@ -155,8 +188,11 @@ __global__ void __launch_bounds__(256) k_histogram(const K* __restrict__ keys,
     const K* kb = (const K*)&b;
 #pragma unroll
     for (int j = 0; j < V; ++j) {
-      count_digits<K>(sh, ka[j]);
-      count_digits<K>(sh, kb[j]);
+      if (COUNT) {
+        count_digits<K>(sh, ka[j]);
+        count_digits<K>(sh, kb[j]);
+      }
+      acc |= (ka[j] ^ k0) | (kb[j] ^ k0);
     }
   }
   for (; i < nv; i += stride) {
@@ -164,18 +200,61 @@ __global__ void __launch_bounds__(256) k_histogram(const K* __restrict__ keys,
     if (copy_to) cv[i] = a;
     const K* ka = (const K*)&a;
 #pragma unroll
-    for (int j = 0; j < V; ++j) count_digits<K>(sh, ka[j]);
+    for (int j = 0; j < V; ++j) {
+      if (COUNT) count_digits<K>(sh, ka[j]);
+      acc |= ka[j] ^ k0;
+    }
   }
   for (uint64_t t = nv * V + gtid; t < n; t += stride) {  // the rest one key at a time
     const K key = keys[t];
     if (copy_to) copy_to[t] = key;
-    count_digits<K>(sh, key);
+    if (COUNT) count_digits<K>(sh, key);
+    acc |= key ^ k0;
   }
+  unsigned long long x = (unsigned long long)acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0 && x) atomicOr(&s_or, x);
   __syncthreads();
-  for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) {
-    const uint32_t c = (&sh[0][0])[i];
-    if (c) atomicAdd(&hist[i], (unsigned long long)c);
+  if (COUNT)
+    for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) {
+      const uint32_t c = (&sh[0][0])[i];
+      if (c) atomicAdd(&hist[i], (unsigned long long)c);
+    }
+  if (threadIdx.x == 0 && s_or) atomicOr(xor_or, s_or);
+}
+
+// Counts of the window (Window) over all keys; the window's shift comes from
+// xor_or, which k_histogram has finished.  Block 0 publishes the shift.
+// Keys differing in fewer than min_bytes bytes are not sorted by the hybrid sort:
+// block 0 marks the window trivial then, so the window pass queued behind skips.
+template <class K>
+__global__ void __launch_bounds__(256) k_window_hist(const K* __restrict__ keys, uint64_t n,
+                                                     Window* __restrict__ win, uint32_t min_bytes) {
+  __shared__ uint32_t sh[kRadix];
+  sh[threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned long long xo = win->xor_or;
+  const uint32_t sw = window_shift(xo);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    win->shift = sw;
+    uint32_t bytes = 0;
+    for (int p = 0; p < (int)sizeof(K); ++p) bytes += ((xo >> (8 * p)) & 0xFF) ? 1u : 0u;
+    if (bytes < min_bytes) win->trivial = 1;
   }
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {  // four loads in flight
+    const K a = keys[i], b = keys[i + stride], c = keys[i + 2 * stride], d = keys[i + 3 * stride];
+    atomicAdd(&sh[(uint32_t)(a >> sw) & 0xFF], 1u);
+    atomicAdd(&sh[(uint32_t)(b >> sw) & 0xFF], 1u);
+    atomicAdd(&sh[(uint32_t)(c >> sw) & 0xFF], 1u);
+    atomicAdd(&sh[(uint32_t)(d >> sw) & 0xFF], 1u);
+  }
+  for (; i < n; i += stride) atomicAdd(&sh[(uint32_t)(keys[i] >> sw) & 0xFF], 1u);
+  __syncthreads();
+  const uint32_t c = sh[threadIdx.x];
+  if (c) atomicAdd(&win->hist[threadIdx.x], (unsigned long long)c);
 }
 
 // The reserved-rowID check on its own, for a build in which no sort pass reads
@@ -212,7 +291,7 @@ __global__ void __launch_bounds__(256) k_scan_hist(const unsigned long long* __r
   for (int i = 0; i < w; ++i) base += warp_tot[i];
   offs[p * kRadix + d] = base + x - c;
   __syncthreads();
-  if (d == 0) trivial[p] = any_full;
+  if (d == 0 && any_full) trivial[p] = 1;  // (the flags start zeroed)
 }
 
 // ---------------------------------------------------------------- one onesweep pass
@@ -222,10 +301,12 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
     uint32_t* __restrict__ dst_v, uint64_t n, uint32_t shift,
     const unsigned long long* __restrict__ digit_off, uint64_t* __restrict__ status,
     uint32_t* __restrict__ tile_counter, uint32_t epoch, uint32_t* __restrict__ flags,
-    uint32_t check_rows, const uint32_t* __restrict__ skip_if) {
+    uint32_t check_rows, const uint32_t* __restrict__ skip_if,
+    const uint32_t* __restrict__ shift_ptr) {
   constexpr int ITEMS = SortTile<K>::kItems;
   constexpr int TILE = kSortThreads * ITEMS;
   if (skip_if && *skip_if) return;  // a speculative pass on a digit that turned out trivial
+  if (shift_ptr) shift = *shift_ptr;  // the window pass: its shift was written on the device
   // keys and rowIDs have their own exchange arrays, so one final loop writes both;
   // the per-warp digit counters share space with the rowIDs (dead by then)
   union HistOrVals {
@@ -943,39 +1024,76 @@ size_t sort_scratch_bytes(uint64_t n, int key_bytes) {
 
 cudaError_t sort_prepare(const void* keys, void* copy_to, uint64_t n, int key_bytes,
                          void* scratch, cudaStream_t s, uint32_t* host_trivial,
-                         unsigned long long* host_hist) {
+                         unsigned long long* host_win, uint32_t min_bytes) {
   ScratchView v = view(scratch, key_bytes);
   cudaError_t e = cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, key_bytes), s);
   if (e != cudaSuccess) return e;
   const int grid = grid_for(n, 256, 8);
+  if (host_win) {
+    // the bits in which keys differ (and the copy over the bus), then the counts
+    // of the window below the highest of them; no digit counts (sort_counts
+    // takes them if the LSD passes turn out to be needed)
+    if (key_bytes == 4)
+      k_histogram<uint32_t, false><<<grid, 256, 0, s>>>((const uint32_t*)keys, (uint32_t*)copy_to, n,
+                                                        v.hist, &v.win->xor_or);
+    else
+      k_histogram<uint64_t, false><<<grid, 256, 0, s>>>((const uint64_t*)keys, (uint64_t*)copy_to, n,
+                                                        v.hist, &v.win->xor_or);
+    const void* src = copy_to ? copy_to : keys;  // the copy when the keys came over the bus
+    if (key_bytes == 4)
+      k_window_hist<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)src, n, v.win, min_bytes);
+    else
+      k_window_hist<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)src, n, v.win, min_bytes);
+    k_scan_hist<<<1, 256, 0, s>>>(v.win->hist, v.win->offs, &v.win->trivial, n);
+    count_launch(3);
+    // [0] xor_or, [1] shift | trivial << 32, [2..257] counts
+    e = cudaMemcpyAsync(host_win, v.win, 16 + sizeof(uint64_t) * kRadix, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
   if (key_bytes == 4)
-    k_histogram<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)keys, (uint32_t*)copy_to, n, v.hist);
+    k_histogram<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)keys, (uint32_t*)copy_to, n, v.hist,
+                                               &v.win->xor_or);
   else
-    k_histogram<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)keys, (uint64_t*)copy_to, n, v.hist);
+    k_histogram<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)keys, (uint64_t*)copy_to, n, v.hist,
+                                               &v.win->xor_or);
   k_scan_hist<<<key_bytes, 256, 0, s>>>(v.hist, v.offs, v.trivial, n);
   count_launch(2);
   e = cudaMemcpyAsync(host_trivial, v.trivial, sizeof(uint32_t) * key_bytes, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(host_hist, v.hist, sizeof(uint64_t) * key_bytes * kRadix, cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
-cudaError_t sort_msd_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
-                          uint64_t n, int key_bytes, int digit, void* scratch, uint32_t* dflags,
-                          bool skip_if_trivial, cudaStream_t s) {
+cudaError_t sort_counts(const void* keys, uint64_t n, int key_bytes, void* scratch, cudaStream_t s) {
   ScratchView v = view(scratch, key_bytes);
-  const uint32_t* skip = skip_if_trivial ? v.trivial + digit : nullptr;
-  // its own epoch (20 + digit), so a later LSD pass on the same digit, after
-  // sort_reset_counters, never mistakes its status words
+  const int grid = grid_for(n, 256, 8);
+  cudaError_t e = cudaMemsetAsync(v.hist, 0, sizeof(uint64_t) * key_bytes * kRadix, s);
+  if (e != cudaSuccess) return e;
+  // (the OR lands on the window record's, which nothing reads any more)
+  unsigned long long* scratch_or = &v.win->xor_or;
+  if (key_bytes == 4)
+    k_histogram<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)keys, nullptr, n, v.hist, scratch_or);
+  else
+    k_histogram<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)keys, nullptr, n, v.hist, scratch_or);
+  k_scan_hist<<<key_bytes, 256, 0, s>>>(v.hist, v.offs, v.trivial, n);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t sort_window_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uint32_t* dst_v,
+                             uint64_t n, int key_bytes, void* scratch, uint32_t* dflags,
+                             cudaStream_t s) {
+  ScratchView v = view(scratch, key_bytes);
+  // its own ticket counter and epoch (30): later passes never mistake its words;
+  // skipped on the device when every key has the same window value
   if (key_bytes == 4)
     k_sort_pass<uint32_t><<<(unsigned)tiles_for(n, 4), kSortThreads, 0, s>>>(
-        (const uint32_t*)src_k, src_v, (uint32_t*)dst_k, dst_v, n, 8u * digit,
-        v.offs + digit * kRadix, v.status, v.counter + digit, 20u + digit, dflags, 1u, skip);
+        (const uint32_t*)src_k, src_v, (uint32_t*)dst_k, dst_v, n, 0u, v.win->offs, v.status,
+        v.counter + key_bytes, 30u, dflags, 1u, &v.win->trivial, &v.win->shift);
   else
     k_sort_pass<uint64_t><<<(unsigned)tiles_for(n, 8), kSortThreads, 0, s>>>(
-        (const uint64_t*)src_k, src_v, (uint64_t*)dst_k, dst_v, n, 8u * digit,
-        v.offs + digit * kRadix, v.status, v.counter + digit, 20u + digit, dflags, 1u, skip);
+        (const uint64_t*)src_k, src_v, (uint64_t*)dst_k, dst_v, n, 0u, v.win->offs, v.status,
+        v.counter + key_bytes, 30u, dflags, 1u, &v.win->trivial, &v.win->shift);
   count_launch();
   return cudaGetLastError();
 }
@@ -997,12 +1115,12 @@ cudaError_t sort_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uin
     k_sort_pass<uint32_t><<<(unsigned)tiles, kSortThreads, 0, s>>>(
         (const uint32_t*)src_k, src_v, (uint32_t*)dst_k, dst_v, n, 8u * pass,
         v.offs + pass * kRadix, v.status, v.counter + pass, (uint32_t)pass + 1, dflags,
-        check_rows ? 1u : 0u, nullptr);
+        check_rows ? 1u : 0u, nullptr, nullptr);
   else
     k_sort_pass<uint64_t><<<(unsigned)tiles, kSortThreads, 0, s>>>(
         (const uint64_t*)src_k, src_v, (uint64_t*)dst_k, dst_v, n, 8u * pass,
         v.offs + pass * kRadix, v.status, v.counter + pass, (uint32_t)pass + 1, dflags,
-        check_rows ? 1u : 0u, nullptr);
+        check_rows ? 1u : 0u, nullptr, nullptr);
   count_launch();
   return cudaGetLastError();
 }
@@ -1234,56 +1352,65 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
 // ---------------------------------------------------------------- hybrid sort, host side
 cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], uint32_t* bv[2],
                         int first_dst, uint64_t n, int key_bytes, uint32_t nontrivial,
-                        const unsigned long long* host_hist, void* scratch, const Geom& g,
+                        const unsigned long long* host_win, void* scratch, const Geom& g,
                         bool sorted_layout, uint32_t key_off, bool force, bool pass1_done,
                         unsigned long long* host_h2, uint32_t* dflags, cudaStream_t s,
                         int* result, bool* used) {
   *used = false;
   *result = pass1_done ? first_dst : -1;
-  // digits from the most significant down
-  int digits[8], nd = 0;
-  for (int p = key_bytes - 1; p >= 0; --p)
-    if (nontrivial & (1u << p)) digits[nd++] = p;
+  const int nd = __builtin_popcount(nontrivial);  // bytes in which two keys differ
   // The bucket sort's slot map is 32-bit: larger indexes take the LSD sort.
-  if (nd < 2 || n >= (1ull << 32)) return cudaSuccess;
-  if (pass1_done && digits[0] != key_bytes - 1) return cudaSuccess;  // the top byte was trivial
+  if (nd < 2 || n >= (1ull << 32) || !host_win) return cudaSuccess;
   // Measured crossovers (GB300, u64 keys): below 2^24 pairs the buckets are too
   // small to pay for the extra passes and the host round trip; with four
   // non-trivial digits or fewer (u32 keys) the two MSD passes save at most two
   // LSD passes and measured no faster.
   if (!force && (nd < 5 || n < (1ull << 24))) return cudaSuccess;
+  if (host_win[1] >> 32) return cudaSuccess;  // one window value only (the pass was skipped)
   const uint64_t cap = local_sort_capacity();
-  const int d1 = digits[0];
-  const bool two = nd >= 3 && n / 256 > cap / 4;  // a second MSD digit keeps buckets small
-  const int d2 = two ? digits[1] : -1;
-  // level-1 buckets straight from the full histogram
+  // MSD windows: the 8 bits just below the highest bit in which two keys differ
+  // (s1), then the next 8 (s2), so that no scatter spends a bit every key shares
+  const uint32_t s1 = (uint32_t)(host_win[1] & 0xFFFFFFFFu);
+  const unsigned long long* hw = host_win + 2;
+  // level-1 buckets straight from the window's counts
   std::vector<uint64_t> start1(kRadix + 1, 0);
   uint64_t mx1 = 0;
   for (int d = 0; d < kRadix; ++d) {
-    start1[d + 1] = start1[d] + host_hist[d1 * kRadix + d];
-    mx1 = std::max<uint64_t>(mx1, host_hist[d1 * kRadix + d]);
+    start1[d + 1] = start1[d] + hw[d];
+    mx1 = std::max<uint64_t>(mx1, hw[d]);
   }
-  // the largest level-1 bucket decides: with one MSD digit it must fit a CTA;
-  // with two, the mean of its level-2 buckets must (else one of them cannot)
-  if (!two && mx1 > cap) return cudaSuccess;
-  if (two && mx1 / kRadix > cap) return cudaSuccess;
-  uint32_t local_mask = 0;
-  for (int i = two ? 2 : 1; i < nd; ++i) local_mask |= 1u << digits[i];
+  // A second window of w2 <= 8 bits just below the first, as wide as it takes to
+  // split the largest level-1 bucket into pieces of about 2048 pairs (narrower
+  // means fewer, fuller buckets: 2^24..2^27 uniform keys give ~2048-pair buckets,
+  // 2^28 ~4096); none if that bucket fits a CTA as it is.
+  uint32_t w2 = 0;
+  while (w2 < 8 && w2 < s1 && (mx1 >> w2) > 2048) ++w2;
+  if ((mx1 >> w2) > cap) return cudaSuccess;  // its level-2 buckets (on average) cannot fit
+  const bool two = w2 > 0;
+  const uint32_t s2 = s1 - w2;  // the digit at s2 takes the w2 new bits (those above are fixed)
+  // keys of one bucket agree on the bits at and above bshift; the bucket sort
+  // splits on the 8 bits below, then ranks, or sorts the lower bytes one by one
+  const uint32_t bshift = two ? s2 : s1;
+  const uint32_t top_shift = bshift >= 8 ? bshift - 8 : 0;
+  uint32_t lsd_mask = 0;
+  for (int p = 0; p < key_bytes; ++p)
+    if ((nontrivial >> p & 1u) && 8u * (uint32_t)p < bshift) lsd_mask |= 1u << p;
+  const bool single = bshift <= 8;
 
   ScratchView v = view(scratch, key_bytes);
   cudaError_t e;
-  // pass 1: a plain global pass on digit d1 (its offsets are in v.offs), unless the
-  // caller ran it already, on the top byte, while the histogram came back
+  // pass 1: the window scatter, unless the caller ran it already while the
+  // histograms came back
   const int dst1 = first_dst;
   if (!pass1_done) {
-    e = sort_msd_pass(src_k, src_v, bk[dst1], bv[dst1], n, key_bytes, d1, scratch, dflags, false, s);
+    e = sort_window_pass(src_k, src_v, bk[dst1], bv[dst1], n, key_bytes, scratch, dflags, s);
     if (e != cudaSuccess) return e;
   }
   int cur = dst1;
   std::vector<BatchTile> segs;  // the buckets the shared-memory sort takes
   if (two) {
-    // tables of the level-1 buckets for the segmented pass on d2 (host-built
-    // from the full histogram while pass 1 runs)
+    // tables of the level-1 buckets for the segmented pass on s2 (host-built
+    // from the window counts while pass 1 runs)
     std::vector<BatchTile> tiles, chunks;
     std::vector<uint64_t> seg_start;
     const uint32_t tile = batch_sort_tile(key_bytes);
@@ -1323,12 +1450,12 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
       cudaFreeAsync(blob, s);
       return e;
     }
-    // per-bucket histogram of d2 and its scan into absolute offsets
+    // per-bucket counts of the second window and their scan into absolute offsets
     const int hgrid = (int)std::min<uint64_t>(chunks.size(), (uint64_t)sm_count() * 8);
     if (key_bytes == 4)
-      k_seg_hist1<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)bk[cur], d_chunks, chunks.size(), 8u * d2, d_hist);
+      k_seg_hist1<uint32_t><<<hgrid, 256, 0, s>>>((const uint32_t*)bk[cur], d_chunks, chunks.size(), s2, d_hist);
     else
-      k_seg_hist1<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)bk[cur], d_chunks, chunks.size(), 8u * d2, d_hist);
+      k_seg_hist1<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)bk[cur], d_chunks, chunks.size(), s2, d_hist);
     k_batch_scan_hist<<<nseg1, 256, 0, s>>>(d_hist, d_offs, d_seg_start, 1);
     count_launch(2);
     // the level-2 counts come back while pass 2 runs (it is a correct stable
@@ -1342,16 +1469,16 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
       cudaFreeAsync(blob, s);
       return e;
     }
-    // pass 2: segmented on d2; tiles.size() <= tiles_for(n) + 256, which the
+    // pass 2: segmented on s2; tiles.size() <= tiles_for(n) + 256, which the
     // status array is sized for
     const int dst2 = 1 - cur;
     if (key_bytes == 4)
       k_batch_sort_pass<uint32_t><<<(unsigned)tiles.size(), kSortThreads, 0, s>>>(
-          (const uint32_t*)bk[cur], bv[cur], (uint32_t*)bk[dst2], bv[dst2], n, 8u * d2, d_tiles,
+          (const uint32_t*)bk[cur], bv[cur], (uint32_t*)bk[dst2], bv[dst2], n, s2, d_tiles,
           d_offs, 0, 1, v.status, d_counter, 40u, dflags, nullptr, 0u, 0u, TileMap{}, 0u);
     else
       k_batch_sort_pass<uint64_t><<<(unsigned)tiles.size(), kSortThreads, 0, s>>>(
-          (const uint64_t*)bk[cur], bv[cur], (uint64_t*)bk[dst2], bv[dst2], n, 8u * d2, d_tiles,
+          (const uint64_t*)bk[cur], bv[cur], (uint64_t*)bk[dst2], bv[dst2], n, s2, d_tiles,
           d_offs, 0, 1, v.status, d_counter, 40u, dflags, nullptr, 0u, 0u, TileMap{}, 0u);
     count_launch();
     cur = dst2;
@@ -1363,7 +1490,7 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
     uint64_t mx = 0;
     for (size_t j = 0; j < (size_t)nseg1 * kRadix; ++j) mx = std::max<uint64_t>(mx, h2[j]);
     if (mx > cap) {  // a bucket too large for one CTA: the caller runs the full LSD sort
-      *result = cur;  // the data after the stable scatters on d1 and d2
+      *result = cur;  // the data after the stable scatters on both windows
       return sort_reset_counters(scratch, key_bytes, s);
     }
     // level-2 buckets, built while pass 2 runs
@@ -1391,8 +1518,8 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
   e = cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, s);
   const int dst3 = 1 - cur;
   if (e == cudaSuccess)
-    e = local_sort(bk[cur], bv[cur], bk[dst3], bv[dst3], d_segs, segs.size(), max_count, local_mask,
-                   key_bytes, g, sorted_layout, key_off, dflags, s);
+    e = local_sort(bk[cur], bv[cur], bk[dst3], bv[dst3], d_segs, segs.size(), max_count, top_shift,
+                   lsd_mask, single, key_bytes, g, sorted_layout, key_off, dflags, s);
   cudaFreeAsync(d_segs, s);
   if (e != cudaSuccess) return e;
   *result = dst3;

@@ -6,8 +6,10 @@
     every output of every layout against the oracle (the answer does not depend on
     the layout, so the oracle runs once per probe set), in the launch
     configuration the benchmark times.
-  * 2^28 uint64 keys: with unique keys and rowID j for key j, a hit on keys[j]
-    must return j and every miss GI_MISS -- a property that holds at any size.
+  * 2^28 uint64 keys: the hybrid build's layout against the oracle's in-order
+    fill, slot by slot; and with unique keys and rowID j for key j, a hit on
+    keys[j] must return j and every miss GI_MISS -- a property that holds at any
+    size.
   * 2^26 uint32 keys, 2^24 ranges with 1, 16 and 256 expected rows: every offset
     and every row against the oracle (for 256 rows, about 2^32 rows per layout,
     compared in chunks of 2^20 ranges).
@@ -103,6 +105,33 @@ def test_layout_at_scale_matches_inorder_fill(big_u64):
         assert np.array_equal(to_host(lk, np.uint64), sk[r])
         assert np.array_equal(to_host(lr, np.uint32), sr[r])
         gi.gi_destroy(idx)
+
+
+def test_layout_at_2e28_hybrid_matches_inorder_fill():
+    """2^28 u64 keys, k = 5: the default build takes the hybrid sort (two MSD
+    scatters on the 8-bit windows below the highest differing bit, 65536 buckets of
+    about 4096 pairs, each sorted in shared memory and written into the layout), in
+    fewer launches than the LSD sort's eight passes would take; every slot's key and
+    rowID against the oracle's in-order fill."""
+    n = 1 << 28
+    keys = W.unique_keys(n, 64, W.seed_for(1, 28))
+    rows = np.arange(n, dtype=np.uint32)
+    kd, rd = to_dev(keys), to_dev(rows)
+    c0 = gi.gi_launch_count()
+    idx = gi.gi_build(kd, rd, gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 5)
+    launches = gi.gi_launch_count() - c0
+    del kd, rd
+    assert launches <= 10, launches  # the LSD path takes at least 8 passes + 6 other launches
+    lk = torch.empty(n, dtype=torch.int64, device=DEV)
+    lr = torch.empty(n, dtype=torch.int32, device=DEV)
+    gi.gi_copy_layout(idx, lk, lr)
+    gi.gi_destroy(idx)
+    got_k, got_r = to_host(lk, np.uint64), to_host(lr, np.uint32)
+    del lk, lr
+    sk, sr = oracle.sort_pairs(keys, rows)
+    r = oracle.layout_slot_rank(n, 5)
+    assert np.array_equal(got_k, sk[r])
+    assert np.array_equal(got_r, sr[r])
 
 
 def test_largest_build_size_property():

@@ -469,14 +469,15 @@ def test_hybrid_build_writes_every_layout(dtype, layout, k):
 @pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER_KARY, 5), (gi.GI_SORTED, 0)])
 def test_default_build_takes_the_hybrid_sort_at_2e24_u64(layout, k):
     # the default path at the size where it starts to pay: 2^24 u64 keys.  The
-    # launch count shows which sort ran (hybrid: histogram, scan, two MSD passes,
-    # one per-bucket histogram + scan, the bucket sort = 7 kernels; LSD: histogram,
-    # scan, 8 passes and the permutation or duplicate check = 11).
+    # launch count shows which sort ran (hybrid: the pass finding the differing
+    # bits, the window's counts + scan, two MSD passes, one per-bucket histogram +
+    # scan, the bucket sort = 8 kernels; LSD: histogram, scan, 8 passes and the
+    # permutation or duplicate check = 11).
     n = 1 << 24
     keys = W.unique_keys(n, 64, 77)
     rows = np.random.default_rng(3).permutation(n).astype(np.uint32)
     ok, orr = _oracle_layout(keys, rows, layout, k)
-    for flag, launches in ((0, 7), (gi.GI_BUILD_LSD, 11)):
+    for flag, launches in ((0, 8), (gi.GI_BUILD_LSD, 11)):
         c0 = gi.gi_launch_count()
         idx = build(keys, rows, layout | flag, k)
         assert gi.gi_launch_count() - c0 == launches, flag
@@ -495,16 +496,20 @@ def test_build_flags_are_exclusive():
 
 @pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER_KARY, 5), (gi.GI_SORTED, 0)])
 def test_hybrid_buckets_above_4096_take_the_512_thread_sort(layout, k):
-    # 6 values in the top byte x 16 in the next: 96 MSD buckets of ~4600 pairs, the
-    # bucket sort's 512-thread class (up to 5120 pairs); random low 48 bits
-    n = 96 * 4600
+    # 2^20 uniform keys plus a cluster of 4400 keys that agree on every bit from
+    # bit 13 up: the cluster and ~512 uniform keys share one bucket after both MSD
+    # windows (the first 8 bits below bit 62, then 3 more: its level-1 bucket holds
+    # ~8700 pairs), ~4900 pairs, which takes the bucket sort's 512-thread class (up
+    # to 5120 pairs); random low 13 bits within the cluster
     rng = np.random.default_rng(23)
-    hi = (rng.integers(0, 6, size=n).astype(np.uint64) << np.uint64(56)) | \
-         (rng.integers(0, 16, size=n).astype(np.uint64) << np.uint64(48))
-    keys = hi | rng.integers(0, 1 << 48, size=n, dtype=np.uint64)
+    base = rng.integers(0, 1 << 62, size=1, dtype=np.uint64)[0] & ~np.uint64(0x1FFF)
+    cluster = base | np.arange(4400, dtype=np.uint64)
+    keys = np.unique(np.concatenate([W.unique_keys(1 << 20, 64, 29), cluster]))
+    n = len(keys)
+    keys = keys[rng.permutation(n)]
     rows = rng.permutation(n).astype(np.uint32)
     ok, orr = _oracle_layout(keys, rows, layout, k)
-    for flag, launches in ((gi.GI_BUILD_HYBRID, 7), (gi.GI_BUILD_LSD, 11)):
+    for flag, launches in ((gi.GI_BUILD_HYBRID, 8), (gi.GI_BUILD_LSD, 11)):
         c0 = gi.gi_launch_count()
         idx = build(keys, rows, layout | flag, k)
         assert gi.gi_launch_count() - c0 == launches, flag  # the hybrid sort did run
@@ -514,10 +519,12 @@ def test_hybrid_buckets_above_4096_take_the_512_thread_sort(layout, k):
 
 
 def test_default_build_skips_the_speculative_pass_when_the_top_byte_is_trivial():
-    # 2^24 u64 keys below 2^32: the build queues its MSD pass on the top byte before it
-    # sees the histogram; every key has top byte 0, so the kernel returns at once, and
-    # with four differing bytes the LSD passes sort from the input (histogram, scan,
-    # the no-op pass, 4 passes, permutation = 8 launches)
+    # 2^24 u64 keys below 2^32: the build queues its MSD pass on the window below the
+    # highest differing bit before the host sees any counts; the keys differ in only
+    # four bytes, where the LSD sort is used, so the window counting marks the window
+    # trivial and the pass returns at once; the LSD passes sort from the input
+    # (the pass finding the differing bits, window counts + scan, the no-op pass,
+    # the digit counts + scan, 4 passes, permutation = 11 launches)
     n = 1 << 24
     keys = W.unique_keys(n, 32, 91).astype(np.uint64)
     rows = np.random.default_rng(3).permutation(n).astype(np.uint32)
@@ -528,7 +535,7 @@ def test_default_build_skips_the_speculative_pass_when_the_top_byte_is_trivial()
     ok, orr = _oracle_layout(keys, rows, gi.GI_EYTZINGER_KARY, 5)
     c0 = gi.gi_launch_count()
     idx = build(keys, rows, gi.GI_EYTZINGER_KARY, 5)
-    assert gi.gi_launch_count() - c0 == 8
+    assert gi.gi_launch_count() - c0 == 11
     lk, lr = layout_arrays(idx, n, np.uint64)
     assert np.array_equal(lk, ok) and np.array_equal(lr, orr)
     gi.gi_destroy(idx)

@@ -153,23 +153,32 @@ __device__ __forceinline__ uint32_t bs_one(const K* __restrict__ keys, const uin
 
 // One lookup in an index of a batch whose indexes each have their own fan-out
 // (d.k; 0 = sorted).  The work item, and so d.k, is the same for the whole CTA.
-template <class K>
+// WIDE = false: fan-outs up to 5 only (their pivots fit the registers of 8 CTAs
+// per SM; the host takes the wide form when an index has k = 9 or 17).
+template <class K, bool WIDE>
 __device__ __forceinline__ uint32_t any_one(const K* __restrict__ keys, const uint32_t* __restrict__ rows,
                                             const BatchDesc& d, const K* sm, K x) {
   switch (d.k) {
     case 2: return eks_one<K, 2>(keys, rows, d, sm, x);
     case 3: return eks_one<K, 3>(keys, rows, d, sm, x);
     case 5: return eks_one<K, 5>(keys, rows, d, sm, x);
-    case 9: return eks_one<K, 9>(keys, rows, d, sm, x);
-    case 17: return eks_one<K, 17>(keys, rows, d, sm, x);
+    case 9: if constexpr (WIDE) return eks_one<K, 9>(keys, rows, d, sm, x); else return GI_MISS;
+    case 17: if constexpr (WIDE) return eks_one<K, 17>(keys, rows, d, sm, x); else return GI_MISS;
     default: return bs_one<K>(keys, rows, d, x);
   }
 }
 
-// KF == 0: sorted layout (binary search per index, no pinning); KF == -1: each
-// index's own fan-out
+// CTAs per SM the registers of a lookup variant allow: 8 (the default grid) for
+// node widths up to 4 keys, 5 for wider nodes.
+template <int KF>
+constexpr int batch_point_min_blocks() {
+  return (KF == -2 || KF >= 9) ? 5 : 8;
+}
+
+// KF == 0: sorted layout (binary search per index, no pinning); KF == -1 / -2:
+// each index's own fan-out (-1: up to 5; -2: any)
 template <class K, int KF>
-__global__ void __launch_bounds__(256) k_batch_point(const K* __restrict__ keys,
+__global__ void __launch_bounds__(256, batch_point_min_blocks<KF>()) k_batch_point(const K* __restrict__ keys,
                                                      const uint32_t* __restrict__ rows,
                                                      const BatchDesc* __restrict__ desc,
                                                      const uint64_t* __restrict__ qoff,
@@ -222,8 +231,8 @@ __global__ void __launch_bounds__(256) k_batch_point(const K* __restrict__ keys,
     if (staged) {
       for (uint64_t i = q0 + threadIdx.x; i < q1; i += blockDim.x) {
         const K x = q[i];
-        if constexpr (KF == -1)
-          out[i] = any_one<K>(keys, rows, d, sm, x);
+        if constexpr (KF < 0)
+          out[i] = any_one<K, KF == -2>(keys, rows, d, sm, x);
         else if constexpr (KF > 0)
           out[i] = eks_one<K, KF>(keys, rows, d, sm, x);
         else
@@ -557,9 +566,13 @@ int gi_batch_point_lookup(gi_batch* b, const void* queries, const uint64_t* quer
                                                        query_offsets, b->d_cs, b->B,         \
                                                        (const K*)queries, out_rowids, b->chunk, \
                                                        b->dflags)
+  const bool wide = b->k == gi::kBatchMixed &&
+                    std::any_of(b->kidx_host.begin(), b->kidx_host.end(), [](uint32_t k) { return k >= 9; });
   if (b->key_bytes == 8) {
     switch (b->k) {
-      case gi::kBatchMixed: GI_BP(uint64_t, -1); break;
+      case gi::kBatchMixed:
+        if (wide) GI_BP(uint64_t, -2); else GI_BP(uint64_t, -1);
+        break;
       case 0: GI_BP(uint64_t, 0); break;
       case 2: GI_BP(uint64_t, 2); break;
       case 3: GI_BP(uint64_t, 3); break;
@@ -569,7 +582,9 @@ int gi_batch_point_lookup(gi_batch* b, const void* queries, const uint64_t* quer
     }
   } else {
     switch (b->k) {
-      case gi::kBatchMixed: GI_BP(uint32_t, -1); break;
+      case gi::kBatchMixed:
+        if (wide) GI_BP(uint32_t, -2); else GI_BP(uint32_t, -1);
+        break;
       case 0: GI_BP(uint32_t, 0); break;
       case 2: GI_BP(uint32_t, 2); break;
       case 3: GI_BP(uint32_t, 3); break;

@@ -283,8 +283,11 @@ gi::LookupCfg resolve_cfg(const gi_index* idx) {
   // top levels read through L1: those within 128 KB of keys (the L1 of an SM
   // holds them while no shared memory is used).  Measured at 2^26 u64 keys, k = 5:
   // levels 0..5 (125 KB) through L1 and the rest not allocated there, 5.78 ms;
-  // every level allocated, 5.97 ms; 0..3, 5.88 ms; 0..7, 6.00 ms.
-  c.l1_levels = gi::levels_within(idx->geom, idx->key_bytes, 128u << 10);
+  // every level allocated, 5.97 ms; 0..3, 5.88 ms; 0..7, 6.00 ms.  An index whose
+  // keys and rowIDs fit in 192 KB keeps everything in L1 (rowIDs included).
+  const uint64_t index_bytes = idx->n * (uint64_t)(idx->key_bytes + 4);
+  c.l1_levels = index_bytes <= (192u << 10) ? (int)idx->geom.levels
+                                            : gi::levels_within(idx->geom, idx->key_bytes, 128u << 10);
   return c;
 }
 
@@ -426,12 +429,15 @@ bool eks_group_supported(uint32_t k, int key_bytes, int group) {
 
 int eks_default_group(uint32_t k, int key_bytes) {
   // One thread per lookup reading its whole node with vector loads measured
-  // fastest (fewest instructions per level), up to 128-byte nodes: at 2^26 u64
-  // keys and k = 17, 10.9 ms for 2^27 lookups against 12.6 ms with 4 lanes of
-  // 32 bytes (k = 9: 6.7 ms against 10.3 with 2 lanes).  Wider nodes are split
-  // over lanes in 32-byte pieces, one sector per lane, else 16-byte pieces.
+  // fastest (fewest instructions per level), up to 128-byte nodes of whole
+  // 32-byte vectors: at 2^26 u64 keys and k = 17, 10.9 ms for 2^27 lookups
+  // against 12.6 ms with 4 lanes of 32 bytes (k = 9: 6.7 ms against 10.3 with 2
+  // lanes).  Other nodes wider than 64 bytes are split over lanes in 32-byte
+  // pieces, one sector per lane, else 16-byte pieces.
   const int node_bytes = (int)(k - 1) * key_bytes;
-  if (node_bytes <= 128 && eks_group_supported(k, key_bytes, 1)) return 1;
+  if ((node_bytes <= 64 || (node_bytes <= 128 && node_bytes % 32 == 0)) &&
+      eks_group_supported(k, key_bytes, 1))
+    return 1;
   if (node_bytes % 32 == 0 && eks_group_supported(k, key_bytes, node_bytes / 32)) return node_bytes / 32;
   if (node_bytes % 16 == 0 && eks_group_supported(k, key_bytes, node_bytes / 16)) return node_bytes / 16;
   for (int g = 32; g >= 1; g >>= 1)

@@ -443,12 +443,12 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
             if (lv < l1_levels) vec_load_hint<K, P>(keys + at, piv[r], pol);
             else vec_load_hint_na<K, P>(keys + at, piv[r], pol);
           } else {
+            // one key per load: a node's keys share sectors, so they go through L1
+            // at every level (without it each key is its own L2 request)
 #pragma unroll
             for (int p = 0; p < P; ++p) {
               const int j = gl + p * G;
-              piv[r][p] = j < N ? (lv < l1_levels ? ld_hint<K>(keys + at + p * G, pol)
-                                                  : ld_hint_na<K>(keys + at + p * G, pol))
-                                : K(0);
+              piv[r][p] = j < N ? ld_hint<K>(keys + at + p * G, pol) : K(0);
             }
           }
         }
@@ -486,7 +486,8 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
         // G > 1: the candidate's key is read once here (fetching it from its owner
         // lane at every level measured 1.4-1.5x slower for 4- and 8-lane groups)
         if (cand[r] != kNoCand && (G == 1 ? ckey[r] : ld_hint<K>(keys + cand[r], pol_stream)) == x[r])
-          res = ld_stream<uint32_t>(rows + cand[r], pol_stream);
+          res = l1_levels >= levels ? ld_hint<uint32_t>(rows + cand[r], pol_stream)  // small: via L1
+                                    : ld_stream<uint32_t>(rows + cand[r], pol_stream);
         st_stream(out + i, res, pol_stream);
       }
     }

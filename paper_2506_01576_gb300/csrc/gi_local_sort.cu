@@ -40,13 +40,12 @@ constexpr uint32_t kCapacity = 5120;  // pairs per bucket: 512 threads x 10
 template <int T>
 struct LocalSmem {
   template <class K>
-  __host__ __device__ static constexpr size_t bytes(int items, bool prefetch = false) {
+  static size_t bytes(int items) {
     const size_t tile = (size_t)T * items;
     return tile * sizeof(K) + tile * 4 +              // keys, rowIDs
            sizeof(uint32_t) * kRadix * (T / 32) +     // per-warp digit counts
            sizeof(uint32_t) * (2 * kRadix + T / 32) +  // sub-bucket starts / ends, warp totals
-           sizeof(uint16_t) * tile +                  // sorted position -> current position
-           (prefetch ? tile * (sizeof(K) + 4) : 0);   // the next bucket's keys and rowIDs
+           sizeof(uint16_t) * tile;                   // sorted position -> current position
   }
 };
 
@@ -174,13 +173,12 @@ __device__ __forceinline__ BucketOrder<K> sort_bucket(const BucketSmem<K, ITEMS,
                                             const uint32_t* __restrict__ src_v, uint64_t start,
                                             uint32_t count, uint32_t top_shift, uint32_t lsd_mask,
                                             bool single, uint32_t limit, bool check_rows,
-                                            uint32_t* __restrict__ flags, bool loaded = false) {
+                                            uint32_t* __restrict__ flags) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t items = (count + T - 1) / T;  // <= ITEMS
   const uint32_t used = items * T;
   bool bad = false;  // an input rowID equal to the reserved miss value
-  // loaded: pairs [0, count) are in shared memory already (copied ahead)
-  for (uint32_t j = loaded ? count + tid : tid; j < used; j += T) {
+  for (uint32_t j = tid; j < used; j += T) {
     const bool in = j < count;
     m.s_k[j] = in ? src_k[start + j] : ~K(0);  // padding sorts last, stably
     const uint32_t v = in ? src_v[start + j] : 0u;
@@ -271,69 +269,24 @@ __device__ __forceinline__ BucketOrder<K> sort_bucket(const BucketSmem<K, ITEMS,
 
 // KF: 1 = sorted layout (slot = rank); >= 2 = k-ary Eytzinger with that fan-out
 // (2 = Eytzinger); 0 = k-ary with the fan-out read at run time.
-// Asynchronous copies of a bucket's pairs into shared memory (one group per thread).
-template <class K, int T>
-__device__ __forceinline__ void copy_bucket_async(K* dk, uint32_t* dv, const K* __restrict__ src_k,
-                                                  const uint32_t* __restrict__ src_v, uint64_t start,
-                                                  uint32_t count) {
-  for (uint32_t j = threadIdx.x; j < count; j += T) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
-                     (uint32_t)__cvta_generic_to_shared(dk + j)),
-                 "l"(src_k + start + j), "n"((int)sizeof(K))
-                 : "memory");
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
-                     (uint32_t)__cvta_generic_to_shared(dv + j)),
-                 "l"(src_v + start + j)
-                 : "memory");
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-// PF: the next bucket's pairs are copied into a second pair of buffers while the
-// current one is sorted (two buffer sets alternate), so a CTA no longer waits for
-// its bucket's loads.
-template <class K, int ITEMS, int T, int MINB, int KF, bool PF = false>
+template <class K, int ITEMS, int T, int MINB, int KF>
 __global__ void __launch_bounds__(T, MINB) k_local_sort(
     const K* __restrict__ src_k, const uint32_t* __restrict__ src_v, K* __restrict__ dst_k,
     uint32_t* __restrict__ dst_v, const BatchTile* __restrict__ segs, uint64_t nseg,
     uint32_t top_shift, uint32_t lsd_mask, uint32_t single, uint32_t limit, SlotMap sm,
     uint32_t key_off, uint32_t* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int TILE = T * ITEMS;
-  BucketSmem<K, ITEMS, T> m(smem_raw);
-  // PF: the two buffer sets; the second lies after everything else
-  K* const bk0 = m.s_k;
-  uint32_t* const bv0 = m.s_v;
-  K* const bk1 = (K*)(smem_raw + LocalSmem<T>::template bytes<K>(ITEMS));
-  uint32_t* const bv1 = (uint32_t*)(bk1 + TILE);
+  const BucketSmem<K, ITEMS, T> m(smem_raw);
   __shared__ SlotMap s_map;  // the slot map from shared memory: 12% faster than from the
                              // kernel parameters in the layout write (measured)
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid < (int)(sizeof(SlotMap) / 4)) ((uint32_t*)&s_map)[tid] = ((const uint32_t*)&sm)[tid];
   bool dup = false;
-  int cur = 0;
-  if (PF && blockIdx.x < nseg) {
-    const BatchTile s0 = segs[blockIdx.x];
-    copy_bucket_async<K, T>(bk0, bv0, src_k, src_v, s0.start, s0.count);
-  }
   for (uint64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
     const BatchTile seg = segs[sg];
-    if (PF) {
-      m.s_k = cur ? bk1 : bk0;
-      m.s_v = cur ? bv1 : bv0;
-      const uint64_t nx = sg + gridDim.x;
-      if (nx < nseg) {
-        const BatchTile s1 = segs[nx];
-        copy_bucket_async<K, T>(cur ? bk0 : bk1, cur ? bv0 : bv1, src_k, src_v, s1.start, s1.count);
-        asm volatile("cp.async.wait_group 1;" ::: "memory");  // this bucket's copies are in
-      } else {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-      }
-      __syncthreads();  // every thread's copies of this bucket have landed
-    }
     const BucketOrder<K> ord = sort_bucket<K, ITEMS, T>(m, src_k, src_v, seg.start, seg.count,
                                                         top_shift, lsd_mask, single != 0, limit,
-                                                        false, flags, PF);
+                                                        false, flags);
     // sorted position j -> rank seg.start + j -> its slot in the layout
     for (uint32_t j = tid; j < seg.count; j += T) {
       const uint32_t p = ord.direct ? j : m.s_src[j];
@@ -346,7 +299,6 @@ __global__ void __launch_bounds__(T, MINB) k_local_sort(
       dst_v[t] = m.s_v[p];
     }
     __syncthreads();
-    if (PF) cur ^= 1;
   }
   if (key_off && blockIdx.x == 0 && tid == 0) dst_k[0] = K(0);  // Eytzinger's empty slot
   if (__any_sync(0xffffffffu, dup) && lane == 0) atomicOr(flags, kFlagDuplicate);
@@ -445,12 +397,12 @@ __global__ void __launch_bounds__(256) k_batch_bucket_lists(
 
 // Size classes of the single-index bucket sort (one launch takes the class of the
 // largest bucket): smaller buckets in narrower classes leave room for more CTAs
-// per SM.  Up to 1536 pairs: 256 threads x 6, 4 CTAs per SM; 2560: x 10, 3 per SM;
-// both copy the next bucket ahead (the last argument).  4096: 512 threads x 8, 2 per
-// SM (twice the threads of the batch's 256 x 16 class); then as the batch.
+// per SM.  Up to 1536 pairs: 256 threads x 6, 5 CTAs per SM; 2560: x 10, 4 per SM
+// (2.6% faster than the 3072 class on 2048-pair buckets); 4096: 512 threads x 8,
+// 2 per SM (twice the threads of the batch's 256 x 16 class); then as the batch.
 #define GI_LOCAL_CLASSES_SINGLE(X) \
-  X(6, 256, 4, 0u, 1536u, true) X(10, 256, 3, 1536u, 2560u, true) X(12, 256, 3, 2560u, 3072u, false) \
-  X(8, 512, 2, 3072u, 4096u, false) X(10, 512, 2, 4096u, 5120u, false)
+  X(6, 256, 5, 0u, 1536u) X(10, 256, 4, 1536u, 2560u) X(12, 256, 3, 2560u, 3072u) \
+  X(8, 512, 2, 3072u, 4096u) X(10, 512, 2, 4096u, 5120u)
 
 template <class K, int KF>
 cudaError_t launch(const K* sk, const uint32_t* sv, K* dk, uint32_t* dv, const BatchTile* segs,
@@ -458,10 +410,10 @@ cudaError_t launch(const K* sk, const uint32_t* sv, K* dk, uint32_t* dv, const B
                    uint32_t single, uint32_t limit, const SlotMap& sm, uint32_t key_off,
                    uint32_t* dflags, cudaStream_t s) {
   bool done = false;
-#define GI_LS(IT, T, MB, LO, HI, PF)                                                           \
+#define GI_LS(IT, T, MB, LO, HI)                                                               \
   if (!done && max_count <= HI) {                                                              \
-    auto kern = k_local_sort<K, IT, T, MB, KF, PF>;                                            \
-    const size_t smem = LocalSmem<T>::template bytes<K>(IT, PF);                               \
+    auto kern = k_local_sort<K, IT, T, MB, KF>;                                                \
+    const size_t smem = LocalSmem<T>::template bytes<K>(IT);                                   \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                          (int)smem);                                           \
     if (e != cudaSuccess) return e;                                                            \

@@ -66,10 +66,6 @@ struct TileMap {
   const uint32_t* count;
 };
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
 __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p) {
   uint64_t v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -122,24 +118,6 @@ inline uint64_t tiles_for(uint64_t n, int key_bytes) {
   const uint64_t tile = (uint64_t)kSortThreads *
                         (key_bytes == 4 ? SortTile<uint32_t>::kItems : SortTile<uint64_t>::kItems);
   return (n + tile - 1) / tile;
-}
-
-// Dynamic shared memory of a sort pass: the tile's rowIDs copied ahead.  Its
-// static arrays plus this exceed the default 48 KB, so the limit is raised once
-// (4 CTAs per SM still fit).
-template <class K>
-constexpr size_t sort_pass_smem() {
-  return sizeof(uint32_t) * kSortThreads * SortTile<K>::kItems;
-}
-template <class K>
-__global__ void k_sort_pass(const K*, const uint32_t*, K*, uint32_t*, uint64_t, uint32_t,
-                            const unsigned long long*, uint64_t*, uint32_t*, uint32_t, uint32_t*,
-                            uint32_t, const uint32_t*, const uint32_t*);
-template <class K>
-cudaError_t sort_pass_setup() {
-  static cudaError_t e = cudaFuncSetAttribute(k_sort_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)sort_pass_smem<K>());
-  return e;
 }
 
 inline ScratchView view(void* scratch, int key_bytes) {
@@ -341,7 +319,6 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
   __shared__ unsigned long long s_gbase[kRadix];  // global position of local position 0 per digit
   __shared__ uint32_t s_warp_tot[kSortWarps];
   __shared__ uint32_t s_tile;
-  extern __shared__ uint32_t s_vpre[];            // [TILE] the rowIDs, copied ahead
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
@@ -356,19 +333,6 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
   K key[ITEMS];
   uint32_t rnk[ITEMS];
   const uint64_t wbase = tile_base + (uint64_t)warp * 32 * ITEMS + lane;
-  const uint32_t lbase = (uint32_t)warp * 32 * ITEMS + lane;
-  // The rowIDs go to shared memory by asynchronous copies issued now, so they land
-  // while the keys are ranked and the look-back waits; each thread copies the
-  // entries it reads back itself.
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const uint64_t idx = wbase + (uint64_t)i * 32;
-    if (idx < n)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(s_vpre + lbase + i * 32)),
-                   "l"(src_v + idx)
-                   : "memory");
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint64_t idx = wbase + (uint64_t)i * 32;
@@ -456,13 +420,12 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
     rnk[i] += s_start[dd] + hv.h[warp][dd];
     s_keys[rnk[i]] = key[i];
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");  // this thread's rowID copies
   __syncthreads();  // the digit counters are dead: their space takes the rowIDs
   bool bad = false;  // a rowID equal to the reserved miss value (first pass only)
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint64_t idx = wbase + (uint64_t)i * 32;
-    const uint32_t v = idx < n ? s_vpre[lbase + i * 32] : 0u;
+    const uint32_t v = idx < n ? src_v[idx] : 0u;
     bad |= check_rows && idx < n && v == GI_MISS;
     hv.vals[rnk[i]] = v;
   }
@@ -1121,16 +1084,14 @@ cudaError_t sort_window_pass(const void* src_k, const uint32_t* src_v, void* dst
                              uint64_t n, int key_bytes, void* scratch, uint32_t* dflags,
                              cudaStream_t s) {
   ScratchView v = view(scratch, key_bytes);
-  cudaError_t e = key_bytes == 4 ? sort_pass_setup<uint32_t>() : sort_pass_setup<uint64_t>();
-  if (e != cudaSuccess) return e;
   // its own ticket counter and epoch (30): later passes never mistake its words;
   // skipped on the device when every key has the same window value
   if (key_bytes == 4)
-    k_sort_pass<uint32_t><<<(unsigned)tiles_for(n, 4), kSortThreads, sort_pass_smem<uint32_t>(), s>>>(
+    k_sort_pass<uint32_t><<<(unsigned)tiles_for(n, 4), kSortThreads, 0, s>>>(
         (const uint32_t*)src_k, src_v, (uint32_t*)dst_k, dst_v, n, 0u, v.win->offs, v.status,
         v.counter + key_bytes, 30u, dflags, 1u, &v.win->trivial, &v.win->shift);
   else
-    k_sort_pass<uint64_t><<<(unsigned)tiles_for(n, 8), kSortThreads, sort_pass_smem<uint64_t>(), s>>>(
+    k_sort_pass<uint64_t><<<(unsigned)tiles_for(n, 8), kSortThreads, 0, s>>>(
         (const uint64_t*)src_k, src_v, (uint64_t*)dst_k, dst_v, n, 0u, v.win->offs, v.status,
         v.counter + key_bytes, 30u, dflags, 1u, &v.win->trivial, &v.win->shift);
   count_launch();
@@ -1149,16 +1110,14 @@ cudaError_t sort_pass(const void* src_k, const uint32_t* src_v, void* dst_k, uin
   const uint64_t tiles = tiles_for(n, key_bytes);
   if (tiles == 0) return cudaSuccess;
   if (tiles > 0x7fffffffull) return cudaErrorInvalidValue;
-  cudaError_t e = key_bytes == 4 ? sort_pass_setup<uint32_t>() : sort_pass_setup<uint64_t>();
-  if (e != cudaSuccess) return e;
   // every pass reuses the status array; the epoch (pass + 1) tells its words apart
   if (key_bytes == 4)
-    k_sort_pass<uint32_t><<<(unsigned)tiles, kSortThreads, sort_pass_smem<uint32_t>(), s>>>(
+    k_sort_pass<uint32_t><<<(unsigned)tiles, kSortThreads, 0, s>>>(
         (const uint32_t*)src_k, src_v, (uint32_t*)dst_k, dst_v, n, 8u * pass,
         v.offs + pass * kRadix, v.status, v.counter + pass, (uint32_t)pass + 1, dflags,
         check_rows ? 1u : 0u, nullptr, nullptr);
   else
-    k_sort_pass<uint64_t><<<(unsigned)tiles, kSortThreads, sort_pass_smem<uint64_t>(), s>>>(
+    k_sort_pass<uint64_t><<<(unsigned)tiles, kSortThreads, 0, s>>>(
         (const uint64_t*)src_k, src_v, (uint64_t*)dst_k, dst_v, n, 8u * pass,
         v.offs + pass * kRadix, v.status, v.counter + pass, (uint32_t)pass + 1, dflags,
         check_rows ? 1u : 0u, nullptr, nullptr);

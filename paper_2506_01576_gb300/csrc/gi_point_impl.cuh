@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
   // Top `hot_levels` levels are kept in L2 (evict_last); deeper levels, rowIDs,
   // probes and results are touched once per lookup and evicted first.
   const uint64_t pol_keep = l2_policy(true), pol_stream = l2_policy(false);
+  const bool in_l1 = l1_levels >= levels;  // the whole index read through L1
 
   for (uint64_t first = gid; first < m; first += groups * R) {
     K x[R], ckey[R];
@@ -468,10 +469,12 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
           if (c < (uint32_t)N && s[r] + c < n) {
             cand[r] = s[r] + c;
             if constexpr (G == 1) {  // pivot c of the node: the candidate's key
-              K mine = piv[r][0];
+              if (!in_l1) {
+                K mine = piv[r][0];
 #pragma unroll
-              for (int p = 1; p < P; ++p) mine = c == (uint32_t)p ? piv[r][p] : mine;
-              ckey[r] = mine;
+                for (int p = 1; p < P; ++p) mine = c == (uint32_t)p ? piv[r][p] : mine;
+                ckey[r] = mine;
+              }
             }
           }
           s[r] = s[r] * KF + (IDX)((c + 1) * N);
@@ -483,11 +486,14 @@ __global__ void __launch_bounds__(512) k_eks_point(const K* __restrict__ keys,
       const uint64_t i = first + r * groups;
       if (i < m && gl == r % G) {
         uint32_t res = GI_MISS;
-        // G > 1: the candidate's key is read once here (fetching it from its owner
-        // lane at every level measured 1.4-1.5x slower for 4- and 8-lane groups)
-        if (cand[r] != kNoCand && (G == 1 ? ckey[r] : ld_hint<K>(keys + cand[r], pol_stream)) == x[r])
-          res = l1_levels >= levels ? ld_hint<uint32_t>(rows + cand[r], pol_stream)  // small: via L1
-                                    : ld_stream<uint32_t>(rows + cand[r], pol_stream);
+        // G > 1, or an index held in L1: the candidate's key is read once here
+        // (an L1 hit for a small index, cheaper than selecting it at every level;
+        // fetching it from its owner lane at every level measured 1.4-1.5x slower
+        // for 4- and 8-lane groups)
+        if (cand[r] != kNoCand &&
+            ((G == 1 && !in_l1) ? ckey[r] : ld_hint<K>(keys + cand[r], pol_stream)) == x[r])
+          res = in_l1 ? ld_hint<uint32_t>(rows + cand[r], pol_stream)  // small: via L1
+                      : ld_stream<uint32_t>(rows + cand[r], pol_stream);
         st_stream(out + i, res, pol_stream);
       }
     }

@@ -10,7 +10,9 @@
 //               batch; one batch is a handful of launches shared by all of its
 //               requests (lookups and range counts in one kernel, a per-request
 //               scan, a range fill), with the copies in and out on the batch's
-//               own stream.
+//               own stream: the requests' probes and bounds are gathered on the
+//               host into one staging copy, and point results come back in one
+//               copy that the host scatters (range offsets and rows per request).
 //   overlap     up to `max_inflight` batches are on the GPU at once, each on its
 //               own stream, so requests that arrive while others run are admitted
 //               into the next batch as soon as arena space frees up.
@@ -19,6 +21,7 @@
 // Each request's submit and completion times are recorded for latency figures.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 #include <atomic>
@@ -51,11 +54,11 @@ struct ServeIndex {  // device descriptor of a resident index
 enum : uint32_t { kItemPoint = 0, kItemCount = 1, kItemFill = 2 };
 
 struct ServeItem {  // one request's share of a batch (device copy of the table)
-  uint64_t in_off;     // arena byte offsets
-  uint64_t in2_off;
-  uint64_t out_off;    // point: results; count/fill: offsets (m+1)
-  uint64_t aux_off;    // count/fill: lower ranks; fill: rows at out2
-  uint64_t rows_off;   // fill: rows
+  const void* in;      // probes or lower bounds (the batch's staging or the arena)
+  const void* in2;     // upper bounds
+  void* out;           // point: results; count/fill: offsets (m+1)
+  uint64_t* aux;       // count/fill: lower ranks
+  uint32_t* rows;      // fill: rows
   uint64_t m;
   uint64_t work_start;  // first work item of this request in the batch
   uint32_t index;
@@ -130,9 +133,9 @@ __global__ void __launch_bounds__(256) k_serve_lookup(const ServeIndex* __restri
     const K* keys = (const K*)d.keys;
     const uint64_t i0 = (w - it.work_start) * kChunk;
     const uint64_t i1 = min(i0 + kChunk, it.m);
-    const K* q = (const K*)(arena + it.in_off);
+    const K* q = (const K*)it.in;
     if (it.kind == kItemPoint) {
-      uint32_t* out = (uint32_t*)(arena + it.out_off);
+      uint32_t* out = (uint32_t*)it.out;
       for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const K x = q[i];
         uint32_t res = GI_MISS;
@@ -146,9 +149,9 @@ __global__ void __launch_bounds__(256) k_serve_lookup(const ServeIndex* __restri
         out[i] = res;
       }
     } else {  // range count: lower rank of L, upper rank of U
-      const K* hi = (const K*)(arena + it.in2_off);
-      uint64_t* cnt = (uint64_t*)(arena + it.out_off);
-      uint64_t* lo_rank = (uint64_t*)(arena + it.aux_off);
+      const K* hi = (const K*)it.in2;
+      uint64_t* cnt = (uint64_t*)it.out;
+      uint64_t* lo_rank = it.aux;
       const Geom g = device_geom(d.n, KF > 1 ? (uint32_t)KF : 2u);
       for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const K L = q[i], U = hi[i];
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(1024) k_serve_scan(const ServeItem* __restrict
                                                      unsigned char* __restrict__ arena) {
   __shared__ uint64_t s_warp[32];
   const ServeItem it = items[count_items[blockIdx.x]];
-  uint64_t* a = (uint64_t*)(arena + it.out_off);
+  uint64_t* a = (uint64_t*)it.out;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   uint64_t carry = 0;
   for (uint64_t base = 0; base < it.m; base += blockDim.x) {
@@ -223,9 +226,9 @@ __global__ void __launch_bounds__(256) k_serve_fill(const ServeIndex* __restrict
     if (threadIdx.x == 0 && it.kind == kItemFill && KF > 0 && narrow) fill_slot_map(sm, g);
     __syncthreads();
     if (it.kind != kItemFill) continue;
-    const uint64_t* offs = (const uint64_t*)(arena + it.out_off);
-    const uint64_t* lo_rank = (const uint64_t*)(arena + it.aux_off);
-    uint32_t* out = (uint32_t*)(arena + it.rows_off);
+    const uint64_t* offs = (const uint64_t*)it.out;
+    const uint64_t* lo_rank = it.aux;
+    uint32_t* out = it.rows;
     const uint64_t i0 = (w - it.work_start) * kChunk;
     const uint64_t i1 = min(i0 + kChunk, it.m);
     for (uint64_t wb = i0 + (threadIdx.x >> 5) * 32; wb < i1; wb += (blockDim.x >> 5) * 32) {
@@ -349,6 +352,10 @@ struct Req {
   int phase = 0;  // 0 queued, 1 point/count in flight, 2 counted, 3 fill in flight, 4 done
   int status = GI_OK;
   Block in, in2, out, aux, rows;
+  // staged: the inputs (and a point request's results) go through the batch's
+  // staging buffers at these byte offsets, with one copy each way per batch
+  bool staged = false;
+  uint64_t st_in = 0, st_out = 0;
   uint64_t total = 0;
   int64_t t_submit = 0, t_done = 0;
 };
@@ -361,6 +368,15 @@ struct Batch {
   uint32_t* h_count_items = nullptr;     // pinned
   uint32_t* d_count_items = nullptr;
   uint32_t capacity = 0;
+  // staging: the requests' inputs gathered on the host into h_in (pinned) and
+  // copied in once; point results copied out once into h_out and scattered on
+  // the host (a copy call per request cost the server thread more than the GPU
+  // spent on the lookups)
+  unsigned char* h_in = nullptr;
+  unsigned char* d_in = nullptr;
+  unsigned char* h_out = nullptr;
+  unsigned char* d_out = nullptr;
+  uint64_t in_cap = 0, out_cap = 0, in_used = 0, out_used = 0;
   std::vector<std::shared_ptr<Req>> reqs;
   bool busy = false;
 };
@@ -416,11 +432,14 @@ bool take_block(gi_server* s, Block& b, uint64_t bytes) {
   return true;
 }
 
-// reserve arena room for a request's next phase; false if it does not fit now
-bool admit(gi_server* s, Req& q) {
+// reserve arena room for a request's next phase; false if it does not fit now.
+// staged: its inputs (and a point request's results) use the batch's staging
+// buffers instead of the arena.
+bool admit(gi_server* s, Req& q, bool staged) {
   const int kb = s->key_bytes;
   const uint64_t m = q.r.m;
   if (q.phase == 0 && q.r.kind == GI_REQ_POINT) {
+    if (staged) return true;
     if (!take_block(s, q.in, m * kb)) return false;
     if (!take_block(s, q.out, m * 4)) {
       free_block(s, q.in);
@@ -429,11 +448,22 @@ bool admit(gi_server* s, Req& q) {
     return true;
   }
   if (q.phase == 0) {  // range count
-    if (!take_block(s, q.in, m * kb)) return false;
-    if (!take_block(s, q.in2, m * kb)) { free_block(s, q.in); return false; }
-    if (!take_block(s, q.out, (m + 1) * 8)) { free_block(s, q.in); free_block(s, q.in2); return false; }
+    if (!staged) {
+      if (!take_block(s, q.in, m * kb)) return false;
+      if (!take_block(s, q.in2, m * kb)) {
+        free_block(s, q.in);
+        return false;
+      }
+    }
+    if (!take_block(s, q.out, (m + 1) * 8)) {
+      free_block(s, q.in);
+      free_block(s, q.in2);
+      return false;
+    }
     if (!take_block(s, q.aux, m * 8)) {
-      free_block(s, q.in); free_block(s, q.in2); free_block(s, q.out);
+      free_block(s, q.in);
+      free_block(s, q.in2);
+      free_block(s, q.out);
       return false;
     }
     return true;
@@ -441,6 +471,13 @@ bool admit(gi_server* s, Req& q) {
   // fill: rows of the counted ranges
   return take_block(s, q.rows, std::max<uint64_t>(q.total, 1) * 4);
 }
+
+// staging bytes of a request's inputs / results (no results for ranges)
+uint64_t stage_in_bytes(const Req& q, int kb) {
+  return q.r.m * kb * (q.r.kind == GI_REQ_RANGE ? 2u : 1u);
+}
+uint64_t stage_out_bytes(const Req& q) { return q.r.kind == GI_REQ_POINT ? q.r.m * 4 : 0; }
+uint64_t up16(uint64_t x) { return (x + 15) & ~15ull; }
 
 // bytes a request needs at its largest phase (for the can-never-fit check)
 uint64_t peak_bytes(const gi_request& r, int kb) {
@@ -456,34 +493,45 @@ void launch_batch(gi_server* s, Batch& b) {
   uint32_t n = 0, ncount = 0;
   uint64_t work = 0, fill_work = 0;
   // lookups and counts first, then fills (two work ranges in one table)
+  unsigned char* const arena = s->arena;
   for (auto& q : b.reqs) {
     if (q->phase == 3) continue;
     ServeItem& it = b.h_items[n++];
     it.index = q->r.index;
     it.m = q->r.m;
-    it.in_off = q->in.off;
-    it.in2_off = q->in2.off;
-    it.out_off = q->out.off;
-    it.aux_off = q->aux.off;
-    it.rows_off = 0;
+    const uint64_t mb = q->r.m * kb;
+    if (q->staged) {  // inputs gathered here, copied with the batch's one copy below
+      memcpy(b.h_in + q->st_in, q->r.keys, mb);
+      if (q->r.kind == GI_REQ_RANGE) memcpy(b.h_in + q->st_in + mb, q->r.hi, mb);
+      it.in = b.d_in + q->st_in;
+      it.in2 = b.d_in + q->st_in + mb;
+    } else {
+      cudaMemcpyAsync(arena + q->in.off, q->r.keys, mb, cudaMemcpyHostToDevice, st);
+      if (q->r.kind == GI_REQ_RANGE)
+        cudaMemcpyAsync(arena + q->in2.off, q->r.hi, mb, cudaMemcpyHostToDevice, st);
+      it.in = arena + q->in.off;
+      it.in2 = arena + q->in2.off;
+    }
+    const bool staged_out = q->staged && q->r.kind == GI_REQ_POINT;
+    it.out = staged_out ? (void*)(b.d_out + q->st_out) : (void*)(arena + q->out.off);
+    it.aux = (uint64_t*)(arena + q->aux.off);
+    it.rows = nullptr;
     it.kind = q->r.kind == GI_REQ_POINT ? kItemPoint : kItemCount;
     it.work_start = work;
     work += (q->r.m + kChunk - 1) / kChunk;
     if (it.kind == kItemCount) b.h_count_items[ncount++] = n - 1;
-    cudaMemcpyAsync(s->arena + q->in.off, q->r.keys, q->r.m * kb, cudaMemcpyHostToDevice, st);
-    if (it.kind == kItemCount)
-      cudaMemcpyAsync(s->arena + q->in2.off, q->r.hi, q->r.m * kb, cudaMemcpyHostToDevice, st);
   }
+  if (b.in_used) cudaMemcpyAsync(b.d_in, b.h_in, b.in_used, cudaMemcpyHostToDevice, st);
   const uint32_t nlook = n;
   for (auto& q : b.reqs) {
     if (q->phase != 3) continue;
     ServeItem& it = b.h_items[n++];
     it.index = q->r.index;
     it.m = q->r.m;
-    it.out_off = q->out.off;
-    it.aux_off = q->aux.off;
-    it.rows_off = q->rows.off;
-    it.in_off = it.in2_off = 0;
+    it.out = arena + q->out.off;
+    it.aux = (uint64_t*)(arena + q->aux.off);
+    it.rows = (uint32_t*)(arena + q->rows.off);
+    it.in = it.in2 = nullptr;
     it.kind = kItemFill;
     it.work_start = fill_work;
     fill_work += (q->r.m + kChunk - 1) / kChunk;
@@ -527,13 +575,16 @@ void launch_batch(gi_server* s, Batch& b) {
     }
   }
 #undef GI_SV
-  // results back to the callers' host buffers
+  // results back: staged point results in one copy (scattered by retire_batch),
+  // the rest straight into the callers' host buffers
+  if (b.out_used) cudaMemcpyAsync(b.h_out, b.d_out, b.out_used, cudaMemcpyDeviceToHost, st);
   for (auto& q : b.reqs) {
     if (q->phase == 3) {
       if (q->total)
         cudaMemcpyAsync(q->r.out_rowids, s->arena + q->rows.off, q->total * 4, cudaMemcpyDeviceToHost, st);
     } else if (q->r.kind == GI_REQ_POINT) {
-      cudaMemcpyAsync(q->r.out_rowids, s->arena + q->out.off, q->r.m * 4, cudaMemcpyDeviceToHost, st);
+      if (!q->staged)
+        cudaMemcpyAsync(q->r.out_rowids, s->arena + q->out.off, q->r.m * 4, cudaMemcpyDeviceToHost, st);
     } else {
       cudaMemcpyAsync(q->r.out_offsets, s->arena + q->out.off, (q->r.m + 1) * 8, cudaMemcpyDeviceToHost, st);
     }
@@ -555,6 +606,7 @@ void retire_batch(gi_server* s, Batch& b, std::deque<std::shared_ptr<Req>>& fill
   std::vector<std::shared_ptr<Req>> done;
   for (auto& q : b.reqs) {
     if (q->r.kind == GI_REQ_POINT) {
+      if (q->staged) memcpy(q->r.out_rowids, b.h_out + q->st_out, q->r.m * 4);
       free_block(s, q->in);
       free_block(s, q->out);
       q->phase = 4;
@@ -625,9 +677,10 @@ void server_loop(gi_server* s) {
       continue;
     }
     uint64_t probes = 0;
+    slot->in_used = slot->out_used = 0;
     while (!fills.empty() && slot->reqs.size() < slot->capacity && probes < s->max_batch) {
       auto& q = fills.front();
-      if (!admit(s, *q)) break;
+      if (!admit(s, *q, false)) break;
       q->phase = 3;
       probes += q->r.m;
       slot->reqs.push_back(q);
@@ -635,7 +688,20 @@ void server_loop(gi_server* s) {
     }
     while (!queue.empty() && slot->reqs.size() < slot->capacity && probes < s->max_batch) {
       auto& q = queue.front();
-      if (!admit(s, *q)) break;  // first-in first-out: later requests wait too
+      // inputs (and point results) through the batch's staging while it has room
+      const uint64_t ib = stage_in_bytes(*q, s->key_bytes), ob = stage_out_bytes(*q);
+      const uint64_t at_in = up16(slot->in_used), at_out = up16(slot->out_used);
+      const bool staged = at_in + ib <= slot->in_cap && at_out + ob <= slot->out_cap;
+      if (!admit(s, *q, staged)) break;  // first-in first-out: later requests wait too
+      q->staged = staged;
+      if (staged) {
+        q->st_in = at_in;
+        slot->in_used = at_in + ib;
+        if (ob) {
+          q->st_out = at_out;
+          slot->out_used = at_out + ob;
+        }
+      }
       q->phase = 1;
       probes += q->r.m;
       slot->reqs.push_back(q);
@@ -701,6 +767,10 @@ int gi_server_create(gi_index* const* indexes, uint32_t count, uint64_t arena_by
       cudaFree(b.d_items);
       cudaFreeHost(b.h_count_items);
       cudaFree(b.d_count_items);
+      cudaFreeHost(b.h_in);
+      cudaFree(b.d_in);
+      cudaFreeHost(b.h_out);
+      cudaFree(b.d_out);
     }
     cudaFree(s->d_idx);
     cudaFree(s->arena);
@@ -723,6 +793,13 @@ int gi_server_create(gi_index* const* indexes, uint32_t count, uint64_t arena_by
     if ((e = cudaMalloc((void**)&b.d_items, b.capacity * sizeof(gi::sv::ServeItem))) != cudaSuccess) return fail_cuda(e, "tables");
     if ((e = cudaMallocHost((void**)&b.h_count_items, b.capacity * 4)) != cudaSuccess) return fail_cuda(e, "tables");
     if ((e = cudaMalloc((void**)&b.d_count_items, b.capacity * 4)) != cudaSuccess) return fail_cuda(e, "tables");
+    // staging for a batch's worth of inputs (ranges: two bounds each) and point results
+    b.in_cap = s->max_batch * 2ull * (uint64_t)s->key_bytes;
+    b.out_cap = s->max_batch * 4ull;
+    if ((e = cudaMallocHost((void**)&b.h_in, b.in_cap)) != cudaSuccess) return fail_cuda(e, "staging");
+    if ((e = cudaMalloc((void**)&b.d_in, b.in_cap)) != cudaSuccess) return fail_cuda(e, "staging");
+    if ((e = cudaMallocHost((void**)&b.h_out, b.out_cap)) != cudaSuccess) return fail_cuda(e, "staging");
+    if ((e = cudaMalloc((void**)&b.d_out, b.out_cap)) != cudaSuccess) return fail_cuda(e, "staging");
   }
   s->worker = std::thread(server_loop, s);
   *out = s;
@@ -900,6 +977,10 @@ void gi_server_destroy(gi_server* s) {
     cudaFree(b.d_items);
     cudaFreeHost(b.h_count_items);
     cudaFree(b.d_count_items);
+    cudaFreeHost(b.h_in);
+    cudaFree(b.d_in);
+    cudaFreeHost(b.h_out);
+    cudaFree(b.d_out);
   }
   cudaFree(s->d_idx);
   cudaFree(s->arena);

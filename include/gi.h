@@ -109,9 +109,11 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
  *   out_rowids  m uint32: the rowID of the first entry whose key equals
  *               queries[i], or GI_MISS.  Written in probe order.
  * SORTED: textbook lower_bound; EYTZINGER: branch-free descent; EYTZINGER_KARY:
- * one node per level, read with vector loads by one thread (default for nodes of
- * at most 64 bytes) or by a group of lanes (GI_OPT_GROUP) that sums its per-lane
- * pivot counts; the child is s*k + (c+1)*(k-1) for c pivots below the probe.
+ * one node per level, read by one thread (the default wherever that kernel is
+ * compiled: k in {3, 4, 5, 8, 9, 16, 17}), with vector loads where the node is
+ * whole 16- or 32-byte vectors, or by a group of lanes (GI_OPT_GROUP) that sums
+ * its per-lane pivot counts; the child is s*k + (c+1)*(k-1) for c pivots below
+ * the probe.
  * Errors: GI_ERR_INVALID (null index/pointer), GI_ERR_CUDA, GI_ERR_NOMEM (staging).
  */
 int gi_point_lookup(const gi_index* index, const void* queries, uint64_t m,

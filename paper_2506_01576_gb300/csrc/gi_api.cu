@@ -428,16 +428,16 @@ bool eks_group_supported(uint32_t k, int key_bytes, int group) {
 }
 
 int eks_default_group(uint32_t k, int key_bytes) {
-  // One thread per lookup reading its whole node with vector loads measured
-  // fastest (fewest instructions per level), up to 128-byte nodes of whole
-  // 32-byte vectors: at 2^26 u64 keys and k = 17, 10.9 ms for 2^27 lookups
-  // against 12.6 ms with 4 lanes of 32 bytes (k = 9: 6.7 ms against 10.3 with 2
-  // lanes).  Other nodes wider than 64 bytes are split over lanes in 32-byte
+  // One thread per lookup reading its whole node measured fastest wherever that
+  // kernel is compiled: with vector loads up to 128-byte nodes (2^26 u64 keys,
+  // k = 17: 10.9 ms for 2^27 lookups against 12.6 ms with 4 lanes of 32 bytes;
+  // k = 9: 6.7 ms against 10.3 with 2 lanes), and with one load per key for nodes
+  // that are not whole 16-byte vectors (k = 16, u64, 120-byte nodes: 8.2 G
+  // lookups/s against 4.2 with 16 lanes at 2^26 keys, 48.9 against 9.3 at 2^10).
+  // Fan-outs without a one-lane kernel split the node over lanes in 32-byte
   // pieces, one sector per lane, else 16-byte pieces.
   const int node_bytes = (int)(k - 1) * key_bytes;
-  if ((node_bytes <= 64 || (node_bytes <= 128 && node_bytes % 32 == 0)) &&
-      eks_group_supported(k, key_bytes, 1))
-    return 1;
+  if (eks_group_supported(k, key_bytes, 1)) return 1;
   if (node_bytes % 32 == 0 && eks_group_supported(k, key_bytes, node_bytes / 32)) return node_bytes / 32;
   if (node_bytes % 16 == 0 && eks_group_supported(k, key_bytes, node_bytes / 16)) return node_bytes / 16;
   for (int g = 32; g >= 1; g >>= 1)

@@ -5,11 +5,18 @@
 // takes one bucket at a time:
 //
 //   1. it loads the bucket into shared memory (padding keys ~0 sort last);
-//   2. it scatters the bucket stably on its top local digit with the warp-ballot
-//      ranking of the radix passes, which splits it into 256 sub-buckets;
+//   2. it splits the bucket on its top local digit into 256 sub-buckets: for
+//      64-bit keys whose lower bits and a 13-bit load position fit in 64 bits
+//      (the single-index build of u64 keys), by shared-memory atomics, in any
+//      order, each key carried as (lower bits << 13 | load position), whose
+//      order is the (key, input position) order, while the rowIDs stay where
+//      they were loaded (2^26 u64 keys: 2.41 ms per build against 2.58 with the
+//      stable ballot scatter; 2^28: 10.1 against 10.6); otherwise stably with
+//      the warp-ballot ranking of the radix passes;
 //   3. count ranking: every key's final place inside its sub-bucket is the number
 //      of keys there that are smaller, or equal and earlier (earlier = first in
-//      the input, since every scatter so far was stable).  Sub-buckets hold a few
+//      the input: every scatter so far was stable, or the position is part of
+//      the compared value).  Sub-buckets hold a few
 //      keys on average, so this costs a few compares per key instead of one
 //      ballot pass per remaining digit.  A bucket with a sub-bucket larger than
 //      `limit` instead runs the ballot pass for every local digit (LSD order);
@@ -158,7 +165,11 @@ struct BucketOrder {
   bool direct;
   bool packed;
   K hi;
+  bool orig;  // packed, and the rowIDs stayed in load order: rowID of s_k[p] is s_v[s_k[p] & 8191]
   __device__ __forceinline__ K key(K stored) const { return packed ? (K)(hi | (stored >> 13)) : stored; }
+  __device__ __forceinline__ uint32_t val(const uint32_t* s_v, K stored, uint32_t p) const {
+    return orig ? s_v[(uint32_t)stored & 8191u] : s_v[p];
+  }
 };
 
 // Sorts the `count` pairs at src + start (count <= T * ITEMS) in shared memory.
@@ -216,7 +227,7 @@ __device__ __forceinline__ BucketOrder<K> sort_bucket(const BucketSmem<K, ITEMS,
       }
     }
   }
-  BucketOrder<K> ord{direct, false, K(0)};
+  BucketOrder<K> ord{direct, false, K(0), false};
   if (!direct) {
     const uint32_t wofs = (uint32_t)warp * 32 * items + lane;
     // 64-bit keys: inside a sub-bucket only the bits below top_shift + 8 differ.
@@ -267,6 +278,96 @@ __device__ __forceinline__ BucketOrder<K> sort_bucket(const BucketSmem<K, ITEMS,
   return ord;
 }
 
+// The same sort for 64-bit keys whose low bits (below top_shift + 8) and a 13-bit
+// position fit in 64 bits, without the ballot pass: every key becomes the composite
+// (low bits << 13 | its load position) in a register, the top window is counted
+// with shared-memory atomics and the composites are scattered to their window's
+// sub-bucket in any order (the split need not be stable: the load position inside
+// the composite breaks ties between equal keys, so count ranking restores input
+// order); the rowIDs never move (the composite names their slot).  Returns false,
+// with nothing sorted, if a sub-bucket is larger than `limit` (the caller then
+// takes sort_bucket).
+template <class K, int ITEMS, int T>
+__device__ __forceinline__ bool sort_bucket_split(const BucketSmem<K, ITEMS, T>& m,
+                                                  const K* __restrict__ src_k,
+                                                  const uint32_t* __restrict__ src_v, uint64_t start,
+                                                  uint32_t count, uint32_t top_shift, uint32_t limit,
+                                                  BucketOrder<K>& ord) {
+  static_assert(sizeof(K) == 8, "64-bit keys");
+  static_assert(ITEMS * T <= 8192, "a position takes 13 bits");
+  static_assert(ITEMS <= 16, "the 16-bit order fits in the histogram words");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t low = top_shift + 8;
+  const uint64_t lmask = (1ull << low) - 1;
+  uint32_t* cnt = m.s_end;  // counters first; ends after the scan
+  if (tid < kRadix) cnt[tid] = 0;
+  __syncthreads();
+  // composites stay in registers; each pair's place in its sub-bucket waits in s_src
+  uint64_t comp[ITEMS];
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t j = tid + i * T;
+    if (j < count) {
+      const uint64_t key = (uint64_t)src_k[start + j];
+      m.s_v[j] = src_v[start + j];
+      comp[i] = ((key & lmask) << 13) | j;
+      if (j == 0) ((K*)m.s_wt)[0] = (K)(key & ~lmask);  // the bits every key shares
+      m.s_src[j] = (uint16_t)atomicAdd(&cnt[(uint32_t)(key >> top_shift) & 0xFF], 1u);
+    }
+  }
+  __syncthreads();
+  // exclusive scan of the 256 counts (thread d owns digit d)
+  bool big = false;
+  uint32_t c = 0, x = 0;
+  if (tid < kRadix) {
+    c = cnt[tid];
+    big = c > limit;
+    x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+  }
+  __shared__ uint32_t s_wsum[kRadix / 32];
+  if (tid < kRadix && lane == 31) s_wsum[warp] = x;
+  if (__syncthreads_or(big)) return false;
+  if (tid < kRadix) {
+    uint32_t pre = 0;
+#pragma unroll
+    for (int w = 0; w < kRadix / 32; ++w) pre += w < warp ? s_wsum[w] : 0u;
+    m.s_start[tid] = pre + x - c;
+    cnt[tid] = pre + x;  // now the sub-bucket's end
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t j = tid + i * T;
+    if (j < count) {
+      const uint32_t d = (uint32_t)(comp[i] >> (top_shift + 13)) & 0xFF;
+      m.s_k[m.s_start[d] + m.s_src[j]] = (K)comp[i];
+    }
+  }
+  __syncthreads();
+  // count ranking inside each sub-bucket: one 64-bit compare per pair
+#pragma unroll 1
+  for (uint32_t p = tid; p < count; p += T) {
+    const K cp = m.s_k[p];
+    const uint32_t d = (uint32_t)(cp >> (top_shift + 13)) & 0xFF;
+    const uint32_t b = m.s_start[d], e = m.s_end[d];
+    uint32_t r = 0, j = b;
+    for (; j + 1 < e; j += 2) r += (m.s_k[j] < cp ? 1u : 0u) + (m.s_k[j + 1] < cp ? 1u : 0u);
+    if (j < e) r += m.s_k[j] < cp ? 1u : 0u;
+    m.s_src[b + r] = (uint16_t)p;
+  }
+  ord.direct = false;
+  ord.packed = true;
+  ord.orig = true;
+  ord.hi = ((const K*)m.s_wt)[0];
+  __syncthreads();
+  return true;
+}
+
 // KF: 1 = sorted layout (slot = rank); >= 2 = k-ary Eytzinger with that fan-out
 // (2 = Eytzinger); 0 = k-ary with the fan-out read at run time.
 template <class K, int ITEMS, int T, int MINB, int KF>
@@ -281,22 +382,32 @@ __global__ void __launch_bounds__(T, MINB) k_local_sort(
                              // kernel parameters in the layout write (measured)
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid < (int)(sizeof(SlotMap) / 4)) ((uint32_t*)&s_map)[tid] = ((const uint32_t*)&sm)[tid];
+  // the atomic split where its composites fit (64-bit keys, low bits + 13 <= 64)
+  const bool split = sizeof(K) == 8 && !single && lsd_mask != 0 && top_shift + 8 + 13 <= 64;
   bool dup = false;
   for (uint64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
     const BatchTile seg = segs[sg];
-    const BucketOrder<K> ord = sort_bucket<K, ITEMS, T>(m, src_k, src_v, seg.start, seg.count,
-                                                        top_shift, lsd_mask, single != 0, limit,
-                                                        false, flags);
+    BucketOrder<K> ord{false, false, K(0), false};
+    bool done = false;
+    if constexpr (sizeof(K) == 8) {
+      if (split)
+        done = sort_bucket_split<K, ITEMS, T>(m, src_k, src_v, seg.start, seg.count, top_shift,
+                                              limit, ord);
+    }
+    if (!done)
+      ord = sort_bucket<K, ITEMS, T>(m, src_k, src_v, seg.start, seg.count, top_shift, lsd_mask,
+                                     single != 0, limit, false, flags);
     // sorted position j -> rank seg.start + j -> its slot in the layout
     for (uint32_t j = tid; j < seg.count; j += T) {
       const uint32_t p = ord.direct ? j : m.s_src[j];
-      const K key = ord.key(m.s_k[p]);
+      const K stored = m.s_k[p];
+      const K key = ord.key(stored);
       if (j > 0) dup |= ord.key(m.s_k[ord.direct ? j - 1 : m.s_src[j - 1]]) == key;
       const uint32_t r = (uint32_t)(seg.start + j);
       uint32_t t = r;
       if constexpr (KF != 1) t = slot_of_rank<KF>(r, s_map);
       dst_k[t + key_off] = key;
-      dst_v[t] = m.s_v[p];
+      dst_v[t] = ord.val(m.s_v, stored, p);
     }
     __syncthreads();
   }

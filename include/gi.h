@@ -58,8 +58,9 @@ typedef struct gi_index gi_index;
 /* Build flags, OR-ed into `layout` of gi_build (at most one).  Both give the same
  * index; they choose how the pairs are sorted.
  *   default          u64 keys with at least five non-trivial digits (bytes that
- *                    differ between keys) and 2^24 <= n <= 2^28 + 2^27 (about) take
- *                    the hybrid sort: a stable scatter on the 8 bits just below the
+ *                    differ between keys) and 2^21 <= n <= 2^28 + 2^27 (about), and
+ *                    u32 keys with four non-trivial digits and 2^26 <= n <= that
+ *                    bound, take the hybrid sort: a stable scatter on the 8 bits just below the
  *                    highest bit in which two keys differ, then one on up to 8
  *                    further bits (as many as split the largest bucket into pieces
  *                    of about 2048 pairs), then every resulting bucket sorted in
@@ -418,7 +419,9 @@ void gi_batch_fanout_table_clear(void);
  *   device memory).  Up to `max_inflight` batches run at once, each on its own
  *   stream.  Starts one server thread.  The indexes must outlive the server.
  * gi_server_submit -- queue a request (thread-safe, returns at once with a
- *   ticket).  All buffers are HOST memory (pinned memory lets copies overlap):
+ *   ticket).  All buffers are HOST memory: page-locked buffers are copied by the
+ *   copy engine straight from and to them; pageable ones are gathered on the
+ *   host into one staging copy per batch (results scattered back likewise):
  *     GI_REQ_POINT: keys[m] probes -> out_rowids[m] (rowID or GI_MISS);
  *     GI_REQ_RANGE: keys[m] lower and hi[m] upper bounds (inclusive) ->
  *       out_offsets[m+1] and, when it fits, out_rowids[rows_capacity] in

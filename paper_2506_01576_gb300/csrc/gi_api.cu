@@ -625,18 +625,18 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   // the host plans
   PinnedScratch& pin = pinned_scratch();
   GI_TRY2(pin.ensure(), "page-locked scratch");
-  // Where the hybrid sort will likely follow (u64 keys from 2^24 pairs up, or
-  // forced), the histogram pass also finds the bits in which keys differ and a
+  // Where the hybrid sort will likely follow (u64 keys from 2^21 pairs up, u32
+  // keys from 2^26, or forced), the histogram pass also finds the bits in which keys differ and a
   // second read counts the 8-bit window just below the highest of them; the first
   // MSD scatter on that window is queued at once, before the host has seen any
   // counts.  Up to 256 x 256 x 7/8 of the bucket capacity pairs: beyond, buckets
   // of uniform keys would be too large for a CTA and the LSD sort would redo it.
   const uint64_t spec_max = 256ull * 256ull * gi::local_sort_capacity() / 8 * 7;
   const bool hybrid_ok = !(flags & GI_BUILD_LSD) && n < (1ull << 32) &&
-                         ((kb == 8 && n >= (1ull << 24) && n <= spec_max) || (flags & GI_BUILD_HYBRID));
+                         ((n >= gi::hybrid_min_pairs(kb) && n <= spec_max) || (flags & GI_BUILD_HYBRID));
   GI_TRY2(gi::sort_prepare(keys_bus ? keys_bus : src_k, keys_bus ? bk[0] : nullptr, n, kb, scratch,
                            s, pin.trivial, hybrid_ok ? pin.win : nullptr,
-                           (flags & GI_BUILD_HYBRID) ? 2u : 5u),
+                           (flags & GI_BUILD_HYBRID) ? 2u : gi::hybrid_min_digits(kb)),
           "histogram");
   cudaEvent_t hist_ready = pin.ev;
   GI_TRY2(cudaEventRecord(hist_ready, s), "histogram");

@@ -1361,11 +1361,9 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
   const int nd = __builtin_popcount(nontrivial);  // bytes in which two keys differ
   // The bucket sort's slot map is 32-bit: larger indexes take the LSD sort.
   if (nd < 2 || n >= (1ull << 32) || !host_win) return cudaSuccess;
-  // Measured crossovers (GB300, u64 keys): below 2^24 pairs the buckets are too
-  // small to pay for the extra passes and the host round trip; with four
-  // non-trivial digits or fewer (u32 keys) the two MSD passes save at most two
-  // LSD passes and measured no faster.
-  if (!force && (nd < 5 || n < (1ull << 24))) return cudaSuccess;
+  // Measured crossovers (GB300): hybrid_min_pairs / hybrid_min_digits.
+  if (!force && (nd < (int)hybrid_min_digits(key_bytes) || n < hybrid_min_pairs(key_bytes)))
+    return cudaSuccess;
   if (host_win[1] >> 32) return cudaSuccess;  // one window value only (the pass was skipped)
   const uint64_t cap = local_sort_capacity();
   // MSD windows: the 8 bits just below the highest bit in which two keys differ

@@ -394,12 +394,13 @@ def test_local_lookup_reordering_changes_nothing(dtype, layout, k):
 
 
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
-@pytest.mark.parametrize("dist", ["uniform", "narrow", "dups", "cluster", "skewed"])
+@pytest.mark.parametrize("dist", ["uniform", "narrow", "dups", "dups64", "cluster", "skewed"])
 def test_hybrid_msd_build_equals_plain_lsd_build(dtype, dist):
     # GI_BUILD_HYBRID scatters by the top digit(s) and sorts each bucket in shared
     # memory (the default does so only from 2^24 u64 keys up); GI_BUILD_LSD forces
     # the plain LSD passes.  Both must give the oracle's layout.  narrow: the top digits are trivial; dups: 16 copies of every key
-    # (stability); cluster: 20000 keys share their top 16 bits, so one level-2 bucket
+    # (stability); dups64: 64 copies, more than a sub-bucket may hold for count
+    # ranking, so every bucket's split gives up and the ballot passes sort it; cluster: 20000 keys share their top 16 bits, so one level-2 bucket
     # is too big for a CTA and the build falls back to LSD after the first scatter;
     # skewed: 70% of the keys below 2^16, so the hybrid sort is not tried at all.
     bits = 8 * np.dtype(dtype).itemsize
@@ -412,6 +413,9 @@ def test_hybrid_msd_build_equals_plain_lsd_build(dtype, dist):
         keys = rng.integers(0, 1 << 24, size=n).astype(dtype)
     elif dist == "dups":
         keys = W.duplicate_keys(n // 16, 16, bits, 8)
+        n = len(keys)
+    elif dist == "dups64":
+        keys = W.duplicate_keys(n // 64, 64, bits, 9)
         n = len(keys)
     elif dist == "cluster":
         keys = rng.integers(0, top, size=n, dtype=dtype, endpoint=True)
@@ -466,14 +470,14 @@ def test_hybrid_build_writes_every_layout(dtype, layout, k):
         gi.gi_destroy(idx)
 
 
+@pytest.mark.parametrize("n", [(1 << 21) + 1000, 1 << 24])
 @pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER_KARY, 5), (gi.GI_SORTED, 0)])
-def test_default_build_takes_the_hybrid_sort_at_2e24_u64(layout, k):
-    # the default path at the size where it starts to pay: 2^24 u64 keys.  The
+def test_default_build_takes_the_hybrid_sort_from_2e21_u64(layout, k, n):
+    # the default path from the size where it starts to pay, 2^21 u64 keys.  The
     # launch count shows which sort ran (hybrid: the pass finding the differing
     # bits, the window's counts + scan, two MSD passes, one per-bucket histogram +
     # scan, the bucket sort = 8 kernels; LSD: histogram, scan, 8 passes and the
     # permutation or duplicate check = 11).
-    n = 1 << 24
     keys = W.unique_keys(n, 64, 77)
     rows = np.random.default_rng(3).permutation(n).astype(np.uint32)
     ok, orr = _oracle_layout(keys, rows, layout, k)

@@ -131,6 +131,57 @@ def test_each_result_same_alone_and_in_the_mix(layout, k):
         gi.gi_destroy(ix)
 
 
+def test_pinned_and_pageable_buffers_mixed():
+    """Page-locked host buffers are copied by the copy engine one by one, pageable
+    ones gathered into the batch's staging copy: requests that mix the two (pinned
+    probes with pageable results and the reverse, one pinned bound with one
+    pageable, pinned probes at an address that is not 8-byte aligned, a small
+    pinned request, which is staged anyway) all answer as the oracle does."""
+    idx, ref = _resident([1 << 12, 70001], gi.GI_EYTZINGER_KARY, 5)
+    server = gi.gi_server_create(idx, 64 << 20, 3)
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    rng = np.random.default_rng(77)
+    pend = []
+    for case in range(8):
+        i = case % 2
+        keys, sk, sr = ref[i]
+        m = 2100 + 37 * case if case < 7 else 700  # above / below the size staged anyway
+        q = W.point_probes(keys, m, 0.5, 64, W.seed_for(4, 1, case), 11 + case)
+        if case in (0, 1, 2):
+            qin = pin(q.copy()) if case != 1 else q.copy()
+            out = np.full(m, 7, np.uint32) if case != 1 else pin(np.full(m, 7, np.uint32))
+            if case == 2:  # pinned probes 4 bytes past an 8-byte boundary
+                raw = pin(np.zeros(8 * m + 8, np.uint8))
+                qin = np.ndarray((m,), dtype=np.uint64, buffer=raw, offset=4)
+                qin[:] = q
+                out = pin(np.full(m, 7, np.uint32))
+            t = gi.gi_server_submit(server, i, gi.GI_REQ_POINT, qin, out_rowids=out)
+            pend.append(("point", t, out, (oracle.point_lookup(sk, sr, q),), qin))
+        else:
+            lo, hi, _ = W.ranges_with_expected_rows(len(keys), m, 16, 64, int(rng.integers(1 << 30)))
+            lo, hi = lo.astype(np.uint64), hi.astype(np.uint64)
+            a = pin(lo.copy()) if case % 2 else lo.copy()
+            b = hi.copy() if case == 3 else pin(hi.copy())  # cases 5, 7: both pinned
+            cap = 64 * m + 64
+            off = pin(np.zeros(m + 1, np.uint64)) if case > 5 else np.zeros(m + 1, np.uint64)
+            rows = np.zeros(cap, np.uint32)
+            t = gi.gi_server_submit(server, i, gi.GI_REQ_RANGE, a, out_rowids=rows, hi=b, out_offsets=off,
+                                    rows_capacity=cap)
+            pend.append(("range", t, (off, rows), oracle.range_lookup(sk, sr, lo, hi), (a, b)))
+    for kind, t, got, want, _keep in pend:
+        st, t0, t1 = gi.gi_server_wait(server, t)
+        assert st == gi.GI_OK
+        if kind == "point":
+            assert np.array_equal(got, want[0])
+        else:
+            off, rows = got
+            assert np.array_equal(off, want[0])
+            assert np.array_equal(rows[: int(off[-1])], want[1])
+    gi.gi_server_destroy(server)
+    for ix in idx:
+        gi.gi_destroy(ix)
+
+
 def test_admission_waits_for_arena_memory():
     # a 1 MiB arena: most requests have to wait for earlier ones to free memory
     idx, ref = _resident([1 << 16, 1 << 14], gi.GI_EYTZINGER_KARY, 5)

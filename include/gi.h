@@ -419,9 +419,10 @@ void gi_batch_fanout_table_clear(void);
  *   device memory).  Up to `max_inflight` batches run at once, each on its own
  *   stream.  Starts one server thread.  The indexes must outlive the server.
  * gi_server_submit -- queue a request (thread-safe, returns at once with a
- *   ticket).  All buffers are HOST memory: page-locked buffers are copied by the
- *   copy engine straight from and to them; pageable ones are gathered on the
- *   host into one staging copy per batch (results scattered back likewise):
+ *   ticket).  All buffers are HOST memory: page-locked buffers of requests of
+ *   more than 2048 probes or ranges are copied by the copy engine straight from
+ *   and to them; the others are gathered on the host into one staging copy per
+ *   batch (point results scattered back likewise):
  *     GI_REQ_POINT: keys[m] probes -> out_rowids[m] (rowID or GI_MISS);
  *     GI_REQ_RANGE: keys[m] lower and hi[m] upper bounds (inclusive) ->
  *       out_offsets[m+1] and, when it fits, out_rowids[rows_capacity] in

@@ -10,13 +10,14 @@
 //               batch; one batch is a handful of launches shared by all of its
 //               requests (lookups and range counts in one kernel, a per-request
 //               scan, a range fill), with the copies in and out on the batch's
-//               own stream.  Inputs and point results in page-locked host memory
-//               are copied by the copy engine, one copy per buffer, with no host
-//               work; those in pageable memory (whose copies the driver would
-//               stage synchronously) are gathered on the host into one staging
-//               copy per batch, and their point results come back in one copy
-//               that the host scatters.  Range offsets and rows come back with one
-//               copy per request.
+//               own stream.  Inputs and point results of large requests in
+//               page-locked host memory are copied by the copy engine, one copy
+//               per buffer, with no host work; small requests, and those in
+//               pageable memory (whose copies the driver would stage
+//               synchronously), are gathered on the host into one staging copy
+//               per batch, and their point results come back in one copy that the
+//               host scatters.  Range offsets and rows come back with one copy per
+//               request.
 //   overlap     up to `max_inflight` batches are on the GPU at once, each on its
 //               own stream, so requests that arrive while others run are admitted
 //               into the next batch as soon as arena space frees up.

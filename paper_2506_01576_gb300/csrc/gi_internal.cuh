@@ -361,6 +361,17 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
 // sub-bucket, one ballot pass per byte of lsd_mask; single: the split alone
 // sorts), written into the layout (see above).
 uint32_t local_sort_capacity();
+// The size classes of the single-index bucket sort: the largest bucket each
+// takes (the launch table in gi_local_sort.cu checks itself against this list).
+constexpr int kLocalClasses = 5;
+constexpr uint32_t kLocalClassMax[kLocalClasses] = {1536u, 2560u, 3072u, 4096u, 5120u};
+// the class (0..kLocalClasses-1) of a bucket of `count` pairs; kLocalClasses if
+// it is too large for any
+inline int local_sort_class(uint64_t count) {
+  int c = 0;
+  for (int i = 0; i < kLocalClasses; ++i) c += count > kLocalClassMax[i] ? 1 : 0;
+  return c;
+}
 cudaError_t local_sort(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
                        const BatchTile* segs, uint64_t nseg, uint64_t max_count,
                        uint32_t top_shift, uint32_t lsd_mask, bool single, int key_bytes,

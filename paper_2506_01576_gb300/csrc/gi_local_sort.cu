@@ -624,6 +624,20 @@ cudaError_t launch_batch_kf(const void* keys, const uint32_t* vals, const void* 
 
 uint32_t local_sort_capacity() { return kCapacity; }
 
+// the launch table and the class list that the host groups buckets by agree
+#define GI_C(IT, T, MB, LO, HI) +1
+static_assert(0 GI_LOCAL_CLASSES_SINGLE(GI_C) == kLocalClasses, "one class per table entry");
+#undef GI_C
+constexpr bool classes_match() {
+  int i = 0;
+  bool ok = true;
+#define GI_C(IT, T, MB, LO, HI) ok = ok && (HI) == kLocalClassMax[i] && (IT) * (T) == (int)(HI); ++i;
+  GI_LOCAL_CLASSES_SINGLE(GI_C)
+#undef GI_C
+  return ok;
+}
+static_assert(classes_match(), "kLocalClassMax lists the launch table's bounds");
+
 cudaError_t local_sort(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
                        const BatchTile* segs, uint64_t nseg, uint64_t max_count,
                        uint32_t top_shift, uint32_t lsd_mask, bool single, int key_bytes,

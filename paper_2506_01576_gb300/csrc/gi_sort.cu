@@ -1405,7 +1405,8 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
     if (e != cudaSuccess) return e;
   }
   int cur = dst1;
-  std::vector<BatchTile> segs;  // the buckets the shared-memory sort takes
+  // the buckets the shared-memory sort takes, by size class (the last: too large)
+  std::vector<BatchTile> segs[kLocalClasses + 1];
   if (two) {
     // tables of the level-1 buckets for the segmented pass on s2 (host-built
     // from the window counts while pass 1 runs)
@@ -1491,33 +1492,44 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
       *result = cur;  // the data after the stable scatters on both windows
       return sort_reset_counters(scratch, key_bytes, s);
     }
-    // level-2 buckets, built while pass 2 runs
-    segs.reserve((size_t)nseg1 * kRadix);
+    // level-2 buckets, built while pass 2 runs, grouped by size class
+    segs[0].reserve((size_t)nseg1 * kRadix);
     for (uint32_t a = 0; a < nseg1; ++a) {
       uint64_t at = seg_start[a];
       for (int d = 0; d < kRadix; ++d) {
         const uint64_t c = h2[(size_t)a * kRadix + d];
-        if (c) segs.push_back(BatchTile{at, 0, (uint32_t)c, 0, 0});
+        if (c) segs[local_sort_class(c)].push_back(BatchTile{at, 0, (uint32_t)c, 0, 0});
         at += c;
       }
     }
   } else {
     for (int d = 0; d < kRadix; ++d) {
       const uint64_t c = start1[d + 1] - start1[d];
-      if (c) segs.push_back(BatchTile{start1[d], 0, (uint32_t)c, 0, 0});
+      if (c) segs[local_sort_class(c)].push_back(BatchTile{start1[d], 0, (uint32_t)c, 0, 0});
     }
   }
-  // every bucket sorted in shared memory and written into the final layout
-  uint64_t max_count = 1;
-  for (const BatchTile& t : segs) max_count = std::max<uint64_t>(max_count, t.count);
+  // every bucket sorted in shared memory and written into the final layout, one
+  // launch per size class, so that a few large buckets do not put every bucket
+  // in the widest class (fewer CTAs per SM)
+  if (!segs[kLocalClasses].empty()) return cudaErrorInvalidValue;  // no class fits
+  size_t total = 0;
+  for (int c = 0; c < kLocalClasses; ++c) total += segs[c].size();
   BatchTile* d_segs = nullptr;
-  e = cudaMallocAsync((void**)&d_segs, std::max<size_t>(1, segs.size()) * sizeof(BatchTile), s);
+  e = cudaMallocAsync((void**)&d_segs, std::max<size_t>(1, total) * sizeof(BatchTile), s);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, s);
   const int dst3 = 1 - cur;
-  if (e == cudaSuccess)
-    e = local_sort(bk[cur], bv[cur], bk[dst3], bv[dst3], d_segs, segs.size(), max_count, top_shift,
-                   lsd_mask, single, key_bytes, g, sorted_layout, key_off, dflags, s);
+  size_t at = 0;
+  for (int c = 0; c < kLocalClasses && e == cudaSuccess; ++c) {
+    const std::vector<BatchTile>& v = segs[c];
+    if (v.empty()) continue;
+    uint64_t max_count = 1;
+    for (const BatchTile& t : v) max_count = std::max<uint64_t>(max_count, t.count);
+    e = cudaMemcpyAsync(d_segs + at, v.data(), v.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = local_sort(bk[cur], bv[cur], bk[dst3], bv[dst3], d_segs + at, v.size(), max_count, top_shift,
+                     lsd_mask, single, key_bytes, g, sorted_layout, key_off, dflags, s);
+    at += v.size();
+  }
   cudaFreeAsync(d_segs, s);
   if (e != cudaSuccess) return e;
   *result = dst3;

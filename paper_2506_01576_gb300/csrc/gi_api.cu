@@ -663,15 +663,25 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
     pass1_pending_reset = true;
   }
   if (!(flags & GI_BUILD_LSD)) {  // hybrid MSD + shared-memory bucket sort where it applies
-    int res = -1;
+    int res = -1, verify = -1;
     bool used = false;
     const uint32_t nontrivial = ~trivial & ((1u << kb) - 1);
     GI_TRY2(gi::hybrid_sort(speculate ? src_k : ck, speculate ? src_v : cv, bk, bv,
                             speculate ? cur : next_dst, n, kb, nontrivial,
                             hybrid_ok ? pin.win : nullptr, scratch, idx->geom, lay == GI_SORTED,
                             lay == GI_EYTZINGER ? 1u : 0u, (flags & GI_BUILD_HYBRID) != 0,
-                            speculate, pin.h2, idx->dflags, s, &res, &used),
+                            speculate, pin.h2, idx->dflags, s, &res, &used, &verify),
             "hybrid sort");
+    if (used && verify >= 0) {
+      // the bucket lists were made on the device: a bucket too large for one CTA
+      // (skewed keys) was left out and counted; then sort from the scattered data
+      GI_TRY2(cudaStreamSynchronize(s), "hybrid sort");
+      if (*(volatile uint32_t*)pin.h2 != 0) {
+        used = false;
+        res = verify;
+        GI_TRY2(gi::sort_reset_counters(scratch, kb, s), "radix pass");
+      }
+    }
     if (res >= 0) {
       ck = bk[res];
       cv = bv[res];

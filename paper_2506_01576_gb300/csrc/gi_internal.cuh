@@ -343,40 +343,49 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
 // Eytzinger for k = 2, keys shifted by key_off) slot of the rank.
 // host_win: sort_prepare's window record (NULL: not applicable).  pass1_done: the
 // caller already ran sort_window_pass into bk[first_dst].  host_h2: page-locked
-// room for 256 x 256 counts.
+// room for one count.
 // *used = true: bk[*result] / bv[*result] hold the finished layout and the
-// duplicate flag is set.  *used = false and *result = -1: not applicable,
-// nothing launched.  *used = false and *result >= 0: bk[*result] holds the data
-// after stable MSD scatter(s) (not applicable after a caller's pass 1, or a
-// bucket too large), for a full LSD sort (counters reset only in the latter).
+// duplicate flag is set -- unless *verify_src >= 0 and, once the stream is done,
+// the count in host_h2 is not zero: then buckets too large for a CTA were left
+// out, and bk[*verify_src] holds the data after both MSD scatters, for a full
+// LSD sort (the caller resets the pass counters).  *used = false and
+// *result = -1: not applicable, nothing launched.  *used = false and
+// *result >= 0: bk[*result] holds the data after stable MSD scatter(s) (not
+// applicable after a caller's pass 1), for a full LSD sort.
 cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], uint32_t* bv[2],
                         int first_dst, uint64_t n, int key_bytes, uint32_t nontrivial,
                         const unsigned long long* host_win, void* scratch, const Geom& g,
                         bool sorted_layout, uint32_t key_off, bool force, bool pass1_done,
                         unsigned long long* host_h2, uint32_t* dflags, cudaStream_t s,
-                        int* result, bool* used);
+                        int* result, bool* used, int* verify_src);
+// The size classes of the single-index bucket sort: the largest bucket each
+// takes (the launch table in gi_local_sort.cu checks itself against this list).
+constexpr int kLocalClasses = 5;
+__host__ __device__ constexpr uint32_t local_class_max(int i) {
+  return i == 0 ? 1536u : i == 1 ? 2560u : i == 2 ? 3072u : i == 3 ? 4096u : 5120u;
+}
+// the class (0..kLocalClasses-1) of a bucket of `count` pairs; kLocalClasses if
+// it is too large for any
+__host__ __device__ inline int local_sort_class(uint64_t count) {
+  int c = 0;
+#pragma unroll
+  for (int i = 0; i < kLocalClasses; ++i) c += count > local_class_max(i) ? 1 : 0;
+  return c;
+}
 // Shared-memory sort of buckets of at most local_sort_capacity() pairs whose keys
 // agree on every bit outside the bytes of lsd_mask and above top_shift + 8: one
 // stable split on the 8 bits at top_shift, then count ranking (or, with a large
 // sub-bucket, one ballot pass per byte of lsd_mask; single: the split alone
 // sorts), written into the layout (see above).
 uint32_t local_sort_capacity();
-// The size classes of the single-index bucket sort: the largest bucket each
-// takes (the launch table in gi_local_sort.cu checks itself against this list).
-constexpr int kLocalClasses = 5;
-constexpr uint32_t kLocalClassMax[kLocalClasses] = {1536u, 2560u, 3072u, 4096u, 5120u};
-// the class (0..kLocalClasses-1) of a bucket of `count` pairs; kLocalClasses if
-// it is too large for any
-inline int local_sort_class(uint64_t count) {
-  int c = 0;
-  for (int i = 0; i < kLocalClasses; ++i) c += count > kLocalClassMax[i] ? 1 : 0;
-  return c;
-}
+// cls >= 0 runs that size class's kernel (buckets of at most local_class_max(cls)
+// pairs), else the class of max_count; nseg_dev != NULL: the number of buckets
+// is read on the device (a list written there), nseg is its upper bound.
 cudaError_t local_sort(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
-                       const BatchTile* segs, uint64_t nseg, uint64_t max_count,
-                       uint32_t top_shift, uint32_t lsd_mask, bool single, int key_bytes,
-                       const Geom& g, bool sorted_layout, uint32_t key_off, uint32_t* dflags,
-                       cudaStream_t s);
+                       const BatchTile* segs, uint64_t nseg, const uint32_t* nseg_dev,
+                       uint64_t max_count, int cls, uint32_t top_shift, uint32_t lsd_mask,
+                       bool single, int key_bytes, const Geom& g, bool sorted_layout,
+                       uint32_t key_off, uint32_t* dflags, cudaStream_t s);
 
 // Point lookups (gi_point.cu).
 struct LookupCfg {

@@ -374,9 +374,10 @@ template <class K, int ITEMS, int T, int MINB, int KF>
 __global__ void __launch_bounds__(T, MINB) k_local_sort(
     const K* __restrict__ src_k, const uint32_t* __restrict__ src_v, K* __restrict__ dst_k,
     uint32_t* __restrict__ dst_v, const BatchTile* __restrict__ segs, uint64_t nseg,
-    uint32_t top_shift, uint32_t lsd_mask, uint32_t single, uint32_t limit, SlotMap sm,
-    uint32_t key_off, uint32_t* __restrict__ flags) {
+    const uint32_t* __restrict__ nseg_dev, uint32_t top_shift, uint32_t lsd_mask, uint32_t single,
+    uint32_t limit, SlotMap sm, uint32_t key_off, uint32_t* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (nseg_dev) nseg = *nseg_dev;  // the list was written on the device
   const BucketSmem<K, ITEMS, T> m(smem_raw);
   __shared__ SlotMap s_map;  // the slot map from shared memory: 12% faster than from the
                              // kernel parameters in the layout write (measured)
@@ -515,24 +516,28 @@ __global__ void __launch_bounds__(256) k_batch_bucket_lists(
   X(6, 256, 5, 0u, 1536u) X(10, 256, 4, 1536u, 2560u) X(12, 256, 3, 2560u, 3072u) \
   X(8, 512, 2, 3072u, 4096u) X(10, 512, 2, 4096u, 5120u)
 
+// cls >= 0: that class's kernel; else the class of the largest bucket (max_count).
+// nseg_dev: the bucket count on the device (nseg is then its upper bound).
 template <class K, int KF>
 cudaError_t launch(const K* sk, const uint32_t* sv, K* dk, uint32_t* dv, const BatchTile* segs,
-                   uint64_t nseg, uint64_t max_count, uint32_t top_shift, uint32_t mask,
-                   uint32_t single, uint32_t limit, const SlotMap& sm, uint32_t key_off,
-                   uint32_t* dflags, cudaStream_t s) {
+                   uint64_t nseg, const uint32_t* nseg_dev, uint64_t max_count, int cls,
+                   uint32_t top_shift, uint32_t mask, uint32_t single, uint32_t limit,
+                   const SlotMap& sm, uint32_t key_off, uint32_t* dflags, cudaStream_t s) {
   bool done = false;
+  int ci = 0;
 #define GI_LS(IT, T, MB, LO, HI)                                                               \
-  if (!done && max_count <= HI) {                                                              \
+  if (!done && (cls >= 0 ? ci == cls : max_count <= HI)) {                                     \
     auto kern = k_local_sort<K, IT, T, MB, KF>;                                                \
     const size_t smem = LocalSmem<T>::template bytes<K>(IT);                                   \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                          (int)smem);                                           \
     if (e != cudaSuccess) return e;                                                            \
     const unsigned grid = (unsigned)std::min<uint64_t>(nseg, (uint64_t)sm_count() * MB * 4);   \
-    kern<<<grid, T, smem, s>>>(sk, sv, dk, dv, segs, nseg, top_shift, mask, single, limit, sm,  \
-                               key_off, dflags);                                               \
+    kern<<<grid, T, smem, s>>>(sk, sv, dk, dv, segs, nseg, nseg_dev, top_shift, mask, single,   \
+                               limit, sm, key_off, dflags);                                    \
     done = true;                                                                               \
-  }
+  }                                                                                            \
+  ++ci;
   GI_LOCAL_CLASSES_SINGLE(GI_LS)
 #undef GI_LS
   if (!done) return cudaErrorInvalidValue;
@@ -542,14 +547,16 @@ cudaError_t launch(const K* sk, const uint32_t* sv, K* dk, uint32_t* dv, const B
 
 template <class K>
 cudaError_t launch_kf(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
-                      const BatchTile* segs, uint64_t nseg, uint64_t max_count, uint32_t top_shift,
-                      uint32_t mask, uint32_t single, uint32_t limit, const Geom& g, bool sorted,
+                      const BatchTile* segs, uint64_t nseg, const uint32_t* nseg_dev,
+                      uint64_t max_count, int cls, uint32_t top_shift, uint32_t mask,
+                      uint32_t single, uint32_t limit, const Geom& g, bool sorted,
                       uint32_t key_off, uint32_t* dflags, cudaStream_t s) {
   const K* a = (const K*)sk;
   K* b = (K*)dk;
   const SlotMap sm = make_slot_map(g);
-#define GI_L(KF, OFF) \
-  launch<K, KF>(a, sv, b, dv, segs, nseg, max_count, top_shift, mask, single, limit, sm, OFF, dflags, s)
+#define GI_L(KF, OFF)                                                                          \
+  launch<K, KF>(a, sv, b, dv, segs, nseg, nseg_dev, max_count, cls, top_shift, mask, single, limit, \
+                sm, OFF, dflags, s)
   if (sorted) return GI_L(1, 0);
   switch (g.k) {
     case 2: return GI_L(2, key_off);
@@ -631,28 +638,31 @@ static_assert(0 GI_LOCAL_CLASSES_SINGLE(GI_C) == kLocalClasses, "one class per t
 constexpr bool classes_match() {
   int i = 0;
   bool ok = true;
-#define GI_C(IT, T, MB, LO, HI) ok = ok && (HI) == kLocalClassMax[i] && (IT) * (T) == (int)(HI); ++i;
+#define GI_C(IT, T, MB, LO, HI) ok = ok && (HI) == local_class_max(i) && (IT) * (T) == (int)(HI); ++i;
   GI_LOCAL_CLASSES_SINGLE(GI_C)
 #undef GI_C
   return ok;
 }
-static_assert(classes_match(), "kLocalClassMax lists the launch table's bounds");
+static_assert(classes_match(), "local_class_max lists the launch table's bounds");
 
 cudaError_t local_sort(const void* sk, const uint32_t* sv, void* dk, uint32_t* dv,
-                       const BatchTile* segs, uint64_t nseg, uint64_t max_count,
-                       uint32_t top_shift, uint32_t lsd_mask, bool single, int key_bytes,
-                       const Geom& g, bool sorted_layout, uint32_t key_off, uint32_t* dflags,
-                       cudaStream_t s) {
+                       const BatchTile* segs, uint64_t nseg, const uint32_t* nseg_dev,
+                       uint64_t max_count, int cls, uint32_t top_shift, uint32_t lsd_mask,
+                       bool single, int key_bytes, const Geom& g, bool sorted_layout,
+                       uint32_t key_off, uint32_t* dflags, cudaStream_t s) {
   if (nseg == 0) return cudaSuccess;
-  if (max_count > local_sort_capacity() || g.n >= (1ull << 32)) return cudaErrorInvalidValue;
+  if (cls >= kLocalClasses) return cudaErrorInvalidValue;
+  if ((cls < 0 && max_count > local_sort_capacity()) || g.n >= (1ull << 32)) return cudaErrorInvalidValue;
   // count ranking costs about one compare per key of the sub-bucket; past this
   // size the remaining ballot passes are cheaper
   const uint32_t limit = 8u * (uint32_t)__builtin_popcount(lsd_mask) + 8u;
   if (key_bytes == 4)
-    return launch_kf<uint32_t>(sk, sv, dk, dv, segs, nseg, max_count, top_shift, lsd_mask,
-                               single ? 1u : 0u, limit, g, sorted_layout, key_off, dflags, s);
-  return launch_kf<uint64_t>(sk, sv, dk, dv, segs, nseg, max_count, top_shift, lsd_mask,
-                             single ? 1u : 0u, limit, g, sorted_layout, key_off, dflags, s);
+    return launch_kf<uint32_t>(sk, sv, dk, dv, segs, nseg, nseg_dev, max_count, cls, top_shift,
+                               lsd_mask, single ? 1u : 0u, limit, g, sorted_layout, key_off,
+                               dflags, s);
+  return launch_kf<uint64_t>(sk, sv, dk, dv, segs, nseg, nseg_dev, max_count, cls, top_shift,
+                             lsd_mask, single ? 1u : 0u, limit, g, sorted_layout, key_off, dflags,
+                             s);
 }
 
 cudaError_t batch_local_sort(const void* keys, const uint32_t* vals, const void* src_k,

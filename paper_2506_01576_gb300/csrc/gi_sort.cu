@@ -1350,13 +1350,39 @@ cudaError_t batch_gather(const void* sk, const uint32_t* sv, void* ok, uint32_t*
 
 
 // ---------------------------------------------------------------- hybrid sort, host side
+// The level-2 buckets of the hybrid sort grouped by size class, on the device:
+// bin i (one per level-1 bucket and second-window value) with hist[i] pairs
+// starting at offs[i] joins the list of its class (lists + class * nbins, order
+// within a list arbitrary); counts[class] ends as each list's length, and
+// counts[kLocalClasses] as the number of buckets too large for any class.
+__global__ void __launch_bounds__(256) k_bucket_classes(const unsigned long long* __restrict__ hist,
+                                                        const unsigned long long* __restrict__ offs,
+                                                        uint32_t nbins, BatchTile* __restrict__ lists,
+                                                        uint32_t* __restrict__ counts) {
+  __shared__ uint32_t s_cnt[kLocalClasses + 1], s_base[kLocalClasses + 1];
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (threadIdx.x <= kLocalClasses) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t c = i < nbins ? hist[i] : 0ull;
+  const int cls = c ? local_sort_class(c) : -1;
+  uint32_t pos = 0;
+  if (cls >= 0) pos = atomicAdd(&s_cnt[cls], 1u);
+  __syncthreads();
+  if (threadIdx.x <= kLocalClasses && s_cnt[threadIdx.x])
+    s_base[threadIdx.x] = atomicAdd(&counts[threadIdx.x], s_cnt[threadIdx.x]);
+  __syncthreads();
+  if (cls >= 0 && cls < kLocalClasses)
+    lists[(uint64_t)cls * nbins + s_base[cls] + pos] = BatchTile{offs[i], 0u, (uint32_t)c, 0u, 0u};
+}
+
 cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], uint32_t* bv[2],
                         int first_dst, uint64_t n, int key_bytes, uint32_t nontrivial,
                         const unsigned long long* host_win, void* scratch, const Geom& g,
                         bool sorted_layout, uint32_t key_off, bool force, bool pass1_done,
                         unsigned long long* host_h2, uint32_t* dflags, cudaStream_t s,
-                        int* result, bool* used) {
+                        int* result, bool* used, int* verify_src) {
   *used = false;
+  *verify_src = -1;
   *result = pass1_done ? first_dst : -1;
   const int nd = __builtin_popcount(nontrivial);  // bytes in which two keys differ
   // The bucket sort's slot map is 32-bit: larger indexes take the LSD sort.
@@ -1427,8 +1453,10 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
     seg_start.push_back(n);
     const size_t tbytes = tiles.size() * sizeof(BatchTile), cbytes = chunks.size() * sizeof(BatchTile);
     const size_t hbytes = (size_t)nseg1 * kRadix * 8;
+    const uint32_t nbins = nseg1 * kRadix;
+    const size_t lbytes = (size_t)kLocalClasses * nbins * sizeof(BatchTile);
     char* blob = nullptr;
-    const size_t blob_bytes = 8 * 256 + tbytes + cbytes + 2 * hbytes + (nseg1 + 1) * 8 + 64;
+    const size_t blob_bytes = 9 * 256 + tbytes + cbytes + 2 * hbytes + (nseg1 + 1) * 8 + 64 + lbytes + 64;
     e = cudaMallocAsync((void**)&blob, blob_bytes, s);
     if (e != cudaSuccess) return e;
     char* q = blob;
@@ -1439,12 +1467,15 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
     unsigned long long* d_offs = (unsigned long long*)take(hbytes);
     uint64_t* d_seg_start = (uint64_t*)take((nseg1 + 1) * 8);
     uint32_t* d_counter = (uint32_t*)take(64);
+    BatchTile* d_lists = (BatchTile*)take(lbytes);
+    uint32_t* d_cls = (uint32_t*)take(64);  // [kLocalClasses + 1] list lengths
     e = cudaMemcpyAsync(d_tiles, tiles.data(), tbytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_chunks, chunks.data(), cbytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_seg_start, seg_start.data(), (nseg1 + 1) * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_hist, 0, hbytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, 64, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cls, 0, 64, s);
     if (e != cudaSuccess) {
       cudaFreeAsync(blob, s);
       return e;
@@ -1456,18 +1487,9 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
     else
       k_seg_hist1<uint64_t><<<hgrid, 256, 0, s>>>((const uint64_t*)bk[cur], d_chunks, chunks.size(), s2, d_hist);
     k_batch_scan_hist<<<nseg1, 256, 0, s>>>(d_hist, d_offs, d_seg_start, 1);
-    count_launch(2);
-    // the level-2 counts come back while pass 2 runs (it is a correct stable
-    // scatter whatever they show); the host waits on this event only
-    e = cudaMemcpyAsync(host_h2, d_hist, hbytes, cudaMemcpyDeviceToHost, s);
-    cudaEvent_t ev = nullptr;
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(ev, s);
-    if (e != cudaSuccess) {
-      if (ev) cudaEventDestroy(ev);
-      cudaFreeAsync(blob, s);
-      return e;
-    }
+    // the level-2 buckets grouped by size class on the device: no host round trip
+    k_bucket_classes<<<(nbins + 255) / 256, 256, 0, s>>>(d_hist, d_offs, nbins, d_lists, d_cls);
+    count_launch(3);
     // pass 2: segmented on s2; tiles.size() <= tiles_for(n) + 256, which the
     // status array is sized for
     const int dst2 = 1 - cur;
@@ -1481,36 +1503,34 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
           d_offs, 0, 1, v.status, d_counter, 40u, dflags, nullptr, 0u, 0u, TileMap{}, 0u);
     count_launch();
     cur = dst2;
+    // every level-2 bucket sorted in shared memory and written into the final
+    // layout, one launch per size class (the list lengths read on the device; a
+    // launch whose list is empty returns at once).  A bucket too large for any
+    // class is left out and counted: the caller reads that count (copied to
+    // host_h2) once the stream is done and then falls back to the LSD sort from
+    // bk[*verify_src], the data after both scatters, which the bucket sort only read.
+    const int dst3 = 1 - cur;
+    for (int c = 0; c < kLocalClasses && e == cudaSuccess; ++c)
+      e = local_sort(bk[cur], bv[cur], bk[dst3], bv[dst3], d_lists + (size_t)c * nbins, nbins, d_cls + c,
+                     local_class_max(c), c, top_shift, lsd_mask, single, key_bytes, g, sorted_layout,
+                     key_off, dflags, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(host_h2, d_cls + kLocalClasses, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(blob, s);
-    e = cudaEventSynchronize(ev);
-    cudaEventDestroy(ev);
     if (e != cudaSuccess) return e;
-    const unsigned long long* h2 = host_h2;
-    uint64_t mx = 0;
-    for (size_t j = 0; j < (size_t)nseg1 * kRadix; ++j) mx = std::max<uint64_t>(mx, h2[j]);
-    if (mx > cap) {  // a bucket too large for one CTA: the caller runs the full LSD sort
-      *result = cur;  // the data after the stable scatters on both windows
-      return sort_reset_counters(scratch, key_bytes, s);
-    }
-    // level-2 buckets, built while pass 2 runs, grouped by size class
-    segs[0].reserve((size_t)nseg1 * kRadix);
-    for (uint32_t a = 0; a < nseg1; ++a) {
-      uint64_t at = seg_start[a];
-      for (int d = 0; d < kRadix; ++d) {
-        const uint64_t c = h2[(size_t)a * kRadix + d];
-        if (c) segs[local_sort_class(c)].push_back(BatchTile{at, 0, (uint32_t)c, 0, 0});
-        at += c;
-      }
-    }
+    *result = dst3;
+    *used = true;
+    *verify_src = cur;
+    return cudaGetLastError();
   } else {
     for (int d = 0; d < kRadix; ++d) {
       const uint64_t c = start1[d + 1] - start1[d];
       if (c) segs[local_sort_class(c)].push_back(BatchTile{start1[d], 0, (uint32_t)c, 0, 0});
     }
   }
-  // every bucket sorted in shared memory and written into the final layout, one
-  // launch per size class, so that a few large buckets do not put every bucket
-  // in the widest class (fewer CTAs per SM)
+  // one level: every bucket sorted in shared memory and written into the final
+  // layout, one launch per size class, so that a few large buckets do not put
+  // every bucket in the widest class (fewer CTAs per SM)
   if (!segs[kLocalClasses].empty()) return cudaErrorInvalidValue;  // no class fits
   size_t total = 0;
   for (int c = 0; c < kLocalClasses; ++c) total += segs[c].size();
@@ -1526,8 +1546,8 @@ cudaError_t hybrid_sort(const void* src_k, const uint32_t* src_v, void* bk[2], u
     for (const BatchTile& t : v) max_count = std::max<uint64_t>(max_count, t.count);
     e = cudaMemcpyAsync(d_segs + at, v.data(), v.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-      e = local_sort(bk[cur], bv[cur], bk[dst3], bv[dst3], d_segs + at, v.size(), max_count, top_shift,
-                     lsd_mask, single, key_bytes, g, sorted_layout, key_off, dflags, s);
+      e = local_sort(bk[cur], bv[cur], bk[dst3], bv[dst3], d_segs + at, v.size(), nullptr, max_count, -1,
+                     top_shift, lsd_mask, single, key_bytes, g, sorted_layout, key_off, dflags, s);
     at += v.size();
   }
   cudaFreeAsync(d_segs, s);

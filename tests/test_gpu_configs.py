@@ -121,7 +121,7 @@ def test_layout_at_2e28_hybrid_matches_inorder_fill():
     idx = gi.gi_build(kd, rd, gi.GI_EYTZINGER_KARY | gi.GI_KEY_U64, 5)
     launches = gi.gi_launch_count() - c0
     del kd, rd
-    assert launches <= 10, launches  # the LSD path takes at least 8 passes + 6 other launches
+    assert launches <= 13, launches  # the LSD path takes at least 8 passes + 6 other launches
     lk = torch.empty(n, dtype=torch.int64, device=DEV)
     lr = torch.empty(n, dtype=torch.int32, device=DEV)
     gi.gi_copy_layout(idx, lk, lr)

@@ -476,12 +476,13 @@ def test_default_build_takes_the_hybrid_sort_from_2e21_u64(layout, k, n):
     # the default path from the size where it starts to pay, 2^21 u64 keys.  The
     # launch count shows which sort ran (hybrid: the pass finding the differing
     # bits, the window's counts + scan, two MSD passes, one per-bucket histogram +
-    # scan, the bucket sort = 8 kernels; LSD: histogram, scan, 8 passes and the
-    # permutation or duplicate check = 11).
+    # scan, the bucket lists by size class, one bucket-sort launch per class =
+    # 13 kernels; LSD: histogram, scan, 8 passes and the permutation or duplicate
+    # check = 11).
     keys = W.unique_keys(n, 64, 77)
     rows = np.random.default_rng(3).permutation(n).astype(np.uint32)
     ok, orr = _oracle_layout(keys, rows, layout, k)
-    for flag, launches in ((0, 8), (gi.GI_BUILD_LSD, 11)):
+    for flag, launches in ((0, 13), (gi.GI_BUILD_LSD, 11)):
         c0 = gi.gi_launch_count()
         idx = build(keys, rows, layout | flag, k)
         assert gi.gi_launch_count() - c0 == launches, flag
@@ -513,10 +514,10 @@ def test_hybrid_buckets_above_4096_take_the_512_thread_sort(layout, k):
     keys = keys[rng.permutation(n)]
     rows = rng.permutation(n).astype(np.uint32)
     ok, orr = _oracle_layout(keys, rows, layout, k)
-    # hybrid: 7 launches before the bucket sort, then one per size class in use
-    # (the cluster's bucket in the 5120-pair class, the ~512-pair buckets in the
-    # smallest), 9 in all; LSD: 11
-    for flag, launches in ((gi.GI_BUILD_HYBRID, 9), (gi.GI_BUILD_LSD, 11)):
+    # hybrid: 8 launches before the bucket sort, then one per size class (the
+    # cluster's bucket in the 5120-pair class, the ~512-pair buckets in the
+    # smallest), 13 in all; LSD: 11
+    for flag, launches in ((gi.GI_BUILD_HYBRID, 13), (gi.GI_BUILD_LSD, 11)):
         c0 = gi.gi_launch_count()
         idx = build(keys, rows, layout | flag, k)
         assert gi.gi_launch_count() - c0 == launches, flag  # the hybrid sort did run

@@ -507,9 +507,10 @@ __global__ void __launch_bounds__(256) k_batch_bucket_lists(
 // SM), up to 4096 (256 x 16, 2 per SM), up to 5120 (512 x 10, 2 per SM).
 #define GI_LOCAL_CLASSES(X) X(12, 256, 3, 0u, 3072u) X(16, 256, 2, 3072u, 4096u) X(10, 512, 2, 4096u, 5120u)
 
-// Size classes of the single-index bucket sort (one launch takes the class of the
-// largest bucket): smaller buckets in narrower classes leave room for more CTAs
-// per SM.  Up to 1536 pairs: 256 threads x 6, 5 CTAs per SM; 2560: x 10, 4 per SM
+// Size classes of the single-index bucket sort (one launch per class, each bucket
+// in the narrowest class that holds it): smaller buckets in narrower classes
+// leave room for more CTAs per SM.  Up to 1536 pairs: 256 threads x 6, 5 CTAs
+// per SM; 2560: x 10, 4 per SM
 // (2.6% faster than the 3072 class on 2048-pair buckets); 4096: 512 threads x 8,
 // 2 per SM (twice the threads of the batch's 256 x 16 class); then as the batch.
 #define GI_LOCAL_CLASSES_SINGLE(X) \

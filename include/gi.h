@@ -58,8 +58,8 @@ typedef struct gi_index gi_index;
 /* Build flags, OR-ed into `layout` of gi_build (at most one).  Both give the same
  * index; they choose how the pairs are sorted.
  *   default          u64 keys with at least five non-trivial digits (bytes that
- *                    differ between keys) and 2^21 <= n <= 2^28 + 2^27 (about), and
- *                    u32 keys with four non-trivial digits and 2^26 <= n <= that
+ *                    differ between keys) and 2^18 <= n <= 2^28 + 2^27 (about), and
+ *                    u32 keys with four non-trivial digits and 2^23 <= n <= that
  *                    bound, take the hybrid sort: a stable scatter on the 8 bits just below the
  *                    highest bit in which two keys differ, then one on up to 8
  *                    further bits (as many as split the largest bucket into pieces

@@ -625,8 +625,8 @@ int gi_build(const void* keys, const uint32_t* rowids, uint64_t n, int layout, u
   // the host plans
   PinnedScratch& pin = pinned_scratch();
   GI_TRY2(pin.ensure(), "page-locked scratch");
-  // Where the hybrid sort will likely follow (u64 keys from 2^21 pairs up, u32
-  // keys from 2^26, or forced), the histogram pass also finds the bits in which keys differ and a
+  // Where the hybrid sort will likely follow (u64 keys from 2^18 pairs up, u32
+  // keys from 2^23, or forced), the histogram pass also finds the bits in which keys differ and a
   // second read counts the 8-bit window just below the highest of them; the first
   // MSD scatter on that window is queued at once, before the host has seen any
   // counts.  Up to 256 x 256 x 7/8 of the bucket capacity pairs: beyond, buckets

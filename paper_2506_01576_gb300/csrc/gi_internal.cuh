@@ -436,11 +436,12 @@ cudaError_t point_lookup_u64(const void* keys, const uint32_t* rows, const Geom&
   X(33, 4) X(33, 8) X(33, 16) X(33, 32)
 // Where the hybrid sort (MSD windows + shared-memory bucket sort) replaces the
 // LSD passes by default.  Measured on GB300, whole builds of unique keys, layouts
-// identical: u64 keys 2^20 0.258 vs 0.251 ms (LSD), 2^21 0.290 vs 0.370, 2^22
-// 0.362 vs 0.516, 2^23 0.511 vs 0.838; u32 keys 2^24 0.753 vs 0.738, 2^26 2.17 vs
-// 2.53.  Keys that differ in fewer bytes than hybrid_min_digits save too few LSD
-// passes to pay for the two MSD passes.
-inline uint64_t hybrid_min_pairs(int key_bytes) { return key_bytes == 8 ? (1ull << 21) : (1ull << 26); }
+// identical, with the bucket lists made on the device: u64 keys 2^18 0.10 vs
+// 0.17 ms (LSD), 2^19 0.18 vs 0.20, 2^20 0.20 vs 0.25, 2^21 0.24 vs 0.37; u32 keys
+// 2^23 0.40 vs 0.41, 2^24 0.67 vs 0.73, 2^26 2.09 vs 2.53 (smaller sizes were not
+// measured).  Keys that differ in fewer bytes than hybrid_min_digits save too few
+// LSD passes to pay for the two MSD passes.
+inline uint64_t hybrid_min_pairs(int key_bytes) { return key_bytes == 8 ? (1ull << 18) : (1ull << 23); }
 inline uint32_t hybrid_min_digits(int key_bytes) { return key_bytes == 8 ? 5u : 4u; }
 bool eks_group_supported(uint32_t k, int key_bytes, int group);
 int eks_default_group(uint32_t k, int key_bytes);

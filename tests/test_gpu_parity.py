@@ -470,19 +470,20 @@ def test_hybrid_build_writes_every_layout(dtype, layout, k):
         gi.gi_destroy(idx)
 
 
-@pytest.mark.parametrize("n", [(1 << 21) + 1000, 1 << 24])
+@pytest.mark.parametrize("n,hybrid_launches", [((1 << 18) + 1000, 5), ((1 << 21) + 1000, 13), (1 << 24, 13)])
 @pytest.mark.parametrize("layout,k", [(gi.GI_EYTZINGER_KARY, 5), (gi.GI_SORTED, 0)])
-def test_default_build_takes_the_hybrid_sort_from_2e21_u64(layout, k, n):
-    # the default path from the size where it starts to pay, 2^21 u64 keys.  The
-    # launch count shows which sort ran (hybrid: the pass finding the differing
-    # bits, the window's counts + scan, two MSD passes, one per-bucket histogram +
-    # scan, the bucket lists by size class, one bucket-sort launch per class =
-    # 13 kernels; LSD: histogram, scan, 8 passes and the permutation or duplicate
-    # check = 11).
+def test_default_build_takes_the_hybrid_sort_from_2e18_u64(layout, k, n, hybrid_launches):
+    # the default path from the size where it starts to pay, 2^18 u64 keys.  The
+    # launch count shows which sort ran.  Hybrid with two windows: the pass finding
+    # the differing bits, the window's counts + scan, two MSD passes, one
+    # per-bucket histogram + scan, the bucket lists by size class, one bucket-sort
+    # launch per class = 13 kernels; with one window (2^18 + 1000 keys: ~1030-pair
+    # buckets after the first scatter) 3 + 1 MSD pass + 1 bucket-sort launch = 5.
+    # LSD: histogram, scan, 8 passes and the permutation or duplicate check = 11.
     keys = W.unique_keys(n, 64, 77)
     rows = np.random.default_rng(3).permutation(n).astype(np.uint32)
     ok, orr = _oracle_layout(keys, rows, layout, k)
-    for flag, launches in ((0, 13), (gi.GI_BUILD_LSD, 11)):
+    for flag, launches in ((0, hybrid_launches), (gi.GI_BUILD_LSD, 11)):
         c0 = gi.gi_launch_count()
         idx = build(keys, rows, layout | flag, k)
         assert gi.gi_launch_count() - c0 == launches, flag

@@ -509,12 +509,14 @@ __global__ void __launch_bounds__(256) k_batch_bucket_lists(
 
 // Size classes of the single-index bucket sort (one launch per class, each bucket
 // in the narrowest class that holds it): smaller buckets in narrower classes
-// leave room for more CTAs per SM.  Up to 1536 pairs: 256 threads x 6, 5 CTAs
-// per SM; 2560: x 10, 4 per SM
+// leave room for more CTAs per SM.  Up to 1536 pairs: 256 threads x 6, 6 CTAs
+// per SM (40 registers, 32 KB of shared memory each; 3.4% faster whole builds at
+// 2^26 u64 keys than 5 CTAs with 48 registers, despite 72 bytes of spills);
+// 2560: x 10, 4 per SM
 // (2.6% faster than the 3072 class on 2048-pair buckets); 4096: 512 threads x 8,
 // 2 per SM (twice the threads of the batch's 256 x 16 class); then as the batch.
 #define GI_LOCAL_CLASSES_SINGLE(X) \
-  X(6, 256, 5, 0u, 1536u) X(10, 256, 4, 1536u, 2560u) X(12, 256, 3, 2560u, 3072u) \
+  X(6, 256, 6, 0u, 1536u) X(10, 256, 4, 1536u, 2560u) X(12, 256, 3, 2560u, 3072u) \
   X(8, 512, 2, 3072u, 4096u) X(10, 512, 2, 4096u, 5120u)
 
 // cls >= 0: that class's kernel; else the class of the largest bucket (max_count).

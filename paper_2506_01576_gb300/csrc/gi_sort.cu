@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(256) k_scan_hist(const unsigned long long* __r
 
 // ---------------------------------------------------------------- one onesweep pass
 template <class K>
-__global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
+__global__ void __launch_bounds__(kSortThreads, 5) k_sort_pass(
     const K* __restrict__ src_k, const uint32_t* __restrict__ src_v, K* __restrict__ dst_k,
     uint32_t* __restrict__ dst_v, uint64_t n, uint32_t shift,
     const unsigned long long* __restrict__ digit_off, uint64_t* __restrict__ status,
@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(256) k_batch_scan_hist(const unsigned long lon
 }
 
 template <class K>
-__global__ void __launch_bounds__(kSortThreads, 4) k_batch_sort_pass(
+__global__ void __launch_bounds__(kSortThreads, 5) k_batch_sort_pass(
     const K* __restrict__ src_k, const uint32_t* __restrict__ src_v, K* __restrict__ dst_k,
     uint32_t* __restrict__ dst_v, uint64_t n, uint32_t shift, const BatchTile* __restrict__ tiles,
     const unsigned long long* __restrict__ offs, int pass, int passes,
@@ -1219,8 +1219,8 @@ cudaError_t batch_sort(const void* keys, const uint32_t* vals, void* tmp_k[2], u
     return cudaSuccess;
   }
   const int hgrid = (int)std::min<uint64_t>(nchunks, (uint64_t)sm_count() * 8);
-  // persistent radix grids: the 4 CTAs per SM the pass fits
-  const unsigned pgrid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count() * 4);
+  // persistent radix grids: the 5 CTAs per SM the pass fits
+  const unsigned pgrid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count() * 5);
   const BatchPlan* plan = nullptr;
   if (!hy) {  // the plain segmented LSD sort: digit histograms of every index
     if (key_bytes == 4)

@@ -431,16 +431,22 @@ def extras(a, gi, torch, dev, kd, rd, qd, out, keys, q, n, m, pt_ms, configure, 
             gi.gi_destroy(idx)
             return int(hoff[-1])
 
-        e2e_step()
-        reps = 3
-        t0 = time.perf_counter()
+        for _ in range(2):  # warm-up: the first calls set up the staging buffers
+            e2e_step()
+        # each step timed on the host clock; the median of 5 (a step is ~15 ms, so
+        # one descheduled host thread would otherwise move a 3-step mean by 2x)
+        reps = 5
+        times = []
         for _ in range(reps):
+            t0 = time.perf_counter()
             total = e2e_step()
-        dt = (time.perf_counter() - t0) / reps
+            times.append(time.perf_counter() - t0)
+        dt = float(np.median(times))
         res["e2e"] = {"value": m / dt, "unit": UNIT,
                       "h2d_bytes_per_step": nk * 8 + nk * 4 + m * 8 + 2 * mr * 8,
                       "d2h_bytes_per_step": m * 4 + (mr + 1) * 8 + total * 4,
-                      "ms_per_step": dt * 1e3, "host_buffers": "pinned"}
+                      "ms_per_step": dt * 1e3, "ms_per_step_each": [round(x * 1e3, 3) for x in times],
+                      "stat": "median of %d steps after 2 warm-up steps" % reps, "host_buffers": "pinned"}
     # ---- the other forms of the path, each at a stated size (after the timed region)
     if not a.no_legs:
         res["ranges"] = ranges_leg(gi, torch, dev)
